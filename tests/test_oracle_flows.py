@@ -1,0 +1,216 @@
+"""Pins of whole oracle runs against the closed forms the paper uses:
+steady circular Couette flow (Appendix A, Eq. A.3) and its torque, the
+transient pipe flow (Eq. 20), the convergence orders stated in Sec. 3.1 and
+Sec. 3.3, and the strain rate from non-equilibrium moments (Eq. 27)."""
+import json
+import os
+
+import numpy as np
+import pytest
+
+from paper_1906_05445_gb300 import workloads as W
+
+GOLD = os.path.join(os.path.dirname(__file__), "golden")
+ORDERS = json.load(open(os.path.join(GOLD, "paper_orders.json")))
+C1 = json.load(open(os.path.join(GOLD, "couette_c1.json")))
+
+
+def couette_sim(oracle, p: W.Problem):
+    s = oracle.OracleSim(p.lattice, p.nx, p.ny, p.nz, p.tau, p.collision, g=p.g)
+    ids = [s.add_solid(b.kind, b.centre, b.radius, b.velocity, b.omega,
+                       b.fluid_inside) for b in p.solids]
+    s.set_scheme(p.scheme, p.ibm_iters, p.retraction, p.marker_density)
+    return s, ids
+
+
+def couette_exact(p: W.Problem):
+    (inner, outer) = p.solids
+    c = inner.centre
+    R1, R2, Om1 = inner.radius, outer.radius, inner.omega[2]
+    A = Om1 / (R1 ** -2 - R2 ** -2)
+    B = -Om1 * R1 ** 2 / (R2 ** 2 - R1 ** 2)
+    y, x = np.mgrid[0:p.ny, 0:p.nx]
+    rx, ry = x - c[0], y - c[1]
+    r = np.hypot(rx, ry)
+    return rx, ry, r, A, B
+
+
+def init_couette_profile(oracle, s, p):
+    """Start from the analytic steady profile (shortens the transient; the
+    steady state reached does not depend on the start)."""
+    e, w = oracle.lattice(0)
+    rx, ry, r, A, B = couette_exact(p)
+    R1, R2 = p.solids[0].radius, p.solids[1].radius
+    ex = A / r + B * r
+    ins = (r >= R1) & (r <= R2)
+    ux = np.where(ins, -ry / r * ex, 0)
+    uy = np.where(ins, rx / r * ex, 0)
+    eu = e[:, 0, None, None] * ux + e[:, 1, None, None] * uy
+    f = w[:, None, None] * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (ux ** 2 + uy ** 2))
+    s.set_f(f[:, None])
+
+
+def couette_errors(oracle, p, tol=1e-9, max_steps=60000):
+    s, (i1, i2) = couette_sim(oracle, p)
+    init_couette_profile(oracle, s, p)
+    s.run_to_steady(tol, max_steps, 200)
+    rx, ry, r, A, B = couette_exact(p)
+    u = s.velocity()[:, 0]
+    uth = (-ry * u[0] + rx * u[1]) / r
+    ex = A / r + B * r
+    R1, R2 = p.solids[0].radius, p.solids[1].radius
+    fl = (r > R1) & (r < R2) if p.scheme == W.IBM else ~s.solid_mask()[0]
+    err = np.sqrt(((uth - ex)[fl] ** 2).sum() / (ex[fl] ** 2).sum())
+    F, T = s.force_torque(i1)
+    nu = (p.tau - 0.5) / 3
+    Om1 = p.solids[0].omega[2]
+    T1 = -4 * np.pi * nu * Om1 * R1 ** 2 * R2 ** 2 / (R2 ** 2 - R1 ** 2)
+    return err, abs(T[2] - T1) / abs(T1), s
+
+
+def test_couette_c1_profile_and_torque(oracle):
+    """The 64x64 D2Q9 case run from rest for 5000 steps with linear Bouzidi
+    bounce-back reaches the Eq. A.3 profile and the analytic torque."""
+    p = W.couette_2d()
+    s, (i1, i2) = couette_sim(oracle, p)
+    s.step(p.steps)
+    rx, ry, r, A, B = couette_exact(p)
+    assert abs(A - C1["A"]) < 1e-15 and abs(B - C1["B"]) < 1e-18
+    u = s.velocity()[:, 0]
+    uth = (-ry * u[0] + rx * u[1]) / r
+    ex = C1["A"] / r + C1["B"] * r
+    fl = ~s.solid_mask()[0]
+    err = np.sqrt(((uth - ex)[fl] ** 2).sum() / (ex[fl] ** 2).sum())
+    assert err < 3e-3
+    ur = (rx * u[0] + ry * u[1]) / r
+    assert np.abs(ur[fl]).max() < 5e-3 * np.abs(ex[fl]).max()
+    F1, T1 = s.force_torque(i1)
+    F2, T2 = s.force_torque(i2)
+    assert abs(T1[2] / C1["torque_inner"] - 1) < 5e-3
+    # steady state: the outer wall carries the opposite torque
+    assert abs(T2[2] + T1[2]) < 5e-3 * abs(T1[2])
+    # no net force by symmetry, up to the staircase of the cut links
+    assert np.abs(F1[:2]).max() < 2e-3 * abs(T1[2]) / 10.0
+
+
+@pytest.mark.slow
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_LIN, W.BOUZIDI_QUAD, W.YU_LIN, W.YU_QUAD])
+def test_couette_ibb_second_order(oracle, scheme):
+    errs = []
+    for k in (0.5, 1.0):
+        n = int(round(64 * k))
+        p = W.couette_2d(n, 10 * k, 28 * k, (n / 2 + 0.3, n / 2 - 0.3), 0.01,
+                         0.8, scheme)
+        errs.append(couette_errors(oracle, p)[:2])
+    errs = np.array(errs)
+    vel_order = np.log2(errs[0, 0] / errs[1, 0])
+    assert abs(vel_order - ORDERS["couette_velocity"]["ibb"]) < 0.35
+    if scheme != W.YU_LIN:
+        tq_order = np.log2(errs[0, 1] / errs[1, 1])
+        assert abs(tq_order - ORDERS["couette_torque"]["ibb"]) < 0.35
+
+
+@pytest.mark.slow
+def test_couette_ibm_first_order(oracle):
+    errs = []
+    for k in (0.5, 1.0):
+        n = int(round(64 * k))
+        p = W.couette_2d(n, 10 * k, 28 * k, (n / 2 + 0.3, n / 2 - 0.3), 0.01,
+                         0.8, W.IBM).with_(ibm_iters=5)
+        errs.append(couette_errors(oracle, p, tol=1e-8)[:2])
+    errs = np.array(errs)
+    assert abs(np.log2(errs[0, 0] / errs[1, 0]) - ORDERS["couette_velocity"]["ibm"]) < 0.3
+    assert abs(np.log2(errs[0, 1] / errs[1, 1]) - ORDERS["couette_torque"]["ibm"]) < 0.3
+    # IBM errors are much larger than IBB errors at equal resolution
+    assert errs[1, 0] > 10 * couette_errors(oracle, W.couette_2d(
+        64, 10, 28, (32.3, 31.7), 0.01, 0.8, W.BOUZIDI_QUAD))[0]
+
+
+def pipe_error(oracle, scheme, R, steps, tau=0.8, g=1e-6, coll=1, nz=4):
+    from scipy.special import j0, j1, jn_zeros
+    n = int(2 * R + 6)
+    c = (n / 2 + 0.21, n / 2 - 0.13, 0.0)
+    s = oracle.OracleSim(1, n, n, nz, tau, coll, g=(0, 0, g))
+    s.add_solid(W.CYLINDER_Z, c, R, fluid_inside=True)
+    s.set_scheme(scheme)
+    s.step(steps)
+    u = s.velocity()[2, 0]
+    y, x = np.mgrid[0:n, 0:n]
+    r = np.hypot(x - c[0], y - c[1])
+    nu = (tau - 0.5) / 3
+    u0 = g * R * R / (4 * nu)
+    lam = jn_zeros(0, 60)
+    ex = u0 * ((1 - r ** 2 / R ** 2) - sum(
+        8 * j0(l * r / R) / (l ** 3 * j1(l)) * np.exp(-l * l * nu * steps / R ** 2)
+        for l in lam))
+    fl = ~s.solid_mask()[0]
+    return np.sqrt(((u - ex)[fl] ** 2).sum() / (ex[fl] ** 2).sum())
+
+
+def test_transient_pipe_flow(oracle):
+    """Eq. 20 (Bessel series) at an early time and at steady state."""
+    assert pipe_error(oracle, W.BOUZIDI_QUAD, 6.3, 150) < 1.5e-2
+    assert pipe_error(oracle, W.BOUZIDI_QUAD, 6.3, 2500) < 1e-2
+
+
+@pytest.mark.slow
+def test_pipe_ibb_second_order(oracle):
+    e1 = pipe_error(oracle, W.BOUZIDI_QUAD, 4.3, 1500)
+    e2 = pipe_error(oracle, W.BOUZIDI_QUAD, 8.6, 6000)
+    assert abs(np.log2(e1 / e2) - ORDERS["pipe_velocity"]["ibb"]) < 0.35
+
+
+def test_couette_strain_rate(oracle):
+    """S_xy etc. from non-equilibrium moments against the analytic strain of
+    Eq. A.3: S_r_theta = -A / r^2."""
+    p = W.couette_2d(scheme=W.BOUZIDI_QUAD)
+    err, _, s = couette_errors(oracle, p, tol=1e-10)
+    S = s.strain_rate()[:, 0]
+    rx, ry, r, A, B = couette_exact(p)
+    Srt = -A / r ** 2
+    # rotate the analytic polar tensor (only S_r_theta != 0) to x, y
+    c, sn = rx / r, ry / r
+    Sxx = -2 * c * sn * Srt
+    Syy = 2 * c * sn * Srt
+    Sxy = (c * c - sn * sn) * Srt
+    fl = ~s.solid_mask()[0]
+    for got, ref in ((S[0], Sxx), (S[1], Syy), (S[2], Sxy)):
+        rel = np.sqrt(((got - ref)[fl] ** 2).sum() / (ref[fl] ** 2).sum())
+        assert rel < 0.03
+
+
+def test_strain_rate_matches_d2q9_moment_form(oracle):
+    """For D2Q9 MRT without force, Eq. 27 expresses the strain rate through
+    the non-equilibrium energy (e), normal-stress (p_xx) and shear-stress
+    (p_xy) moments with their own rates; the oracle's tensor form must give
+    the same numbers for distinct s_e, s_n = s_c."""
+    rates = np.zeros(9)
+    rates[1] = 1.31      # s_e
+    rates[7] = rates[8] = 1 / 0.7
+    s = oracle.OracleSim(0, 7, 6, 1, 0.7, 1, rates=rates)
+    e, w = oracle.lattice(0)
+    r = W.population_noise(9, s.shape, seed=21, amplitude=0.02)
+    f = w[:, None, None, None] * (1 + r)
+    s.set_f(f)
+    S = s.strain_rate()
+    M = oracle.mrt_matrix(0)
+    fl = f.reshape(9, -1)
+    rho = fl.sum(0)
+    u = np.stack([(fl * e[:, a, None]).sum(0) for a in range(2)])
+    feq = np.stack([oracle.equilibrium(0, rho[n], [u[0, n], u[1, n], 0])
+                    for n in range(fl.shape[1])], axis=1)
+    mneq = M @ (fl - feq)
+    se, sn, sc = rates[1], rates[7], rates[8]
+    dudx = -se / 4 * mneq[1] - 3 * sn / 4 * mneq[7]
+    dvdy = -se / 4 * mneq[1] + 3 * sn / 4 * mneq[7]
+    sxy = -3 * sc / 2 * mneq[8]
+    got = S.reshape(3, -1)
+    for k, ref in enumerate((dudx, dvdy, sxy)):
+        assert np.abs(got[k] - ref).max() < 1e-14
+
+
+def test_run_to_steady_converges(oracle):
+    p = W.couette_2d(32, 5, 14, (16.3, 15.8), 0.01, 0.8, W.BOUZIDI_LIN)
+    s, _ = couette_sim(oracle, p)
+    done, r = s.run_to_steady(1e-8, 20000, 100)
+    assert r < 1e-8 and done < 20000 and done % 100 == 0

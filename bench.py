@@ -1,0 +1,378 @@
+"""Benchmark of the fused D3Q19 collide-stream sweep with curved no-slip walls.
+
+Workload (one "step" = one time step of the whole hot path on both lattices):
+the 128^3 periodic cube with a fixed sphere (R = 12 at a seeded sub-grid
+offset), D3Q19 MRT, tau = 0.6, uniform body force g_x = 3.4e-8, FP32
+arithmetic with f - w_i stored in FP32, run side by side with quadratic
+Bouzidi interpolated bounce-back (+ momentum exchange, FP64 reduction) and
+with direct-forcing IBM (Peskin 4-point kernel, one marker per unit area).
+
+Prints one JSON line: MLUPS over both lattices, the roofline of the dominant
+kernel (the bulk sweep, timed with CUDA events on its stream), the end-to-end
+figure through the C ABI with host buffers, the oracle on the host cores, the
+SM clocks sampled during the timed region and the kernel launch count.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun each rank runs its own replica of the workload (independent
+lattices, no data-path collective): value = all node updates / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import re
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+from paper_1906_05445_gb300 import workloads as W  # noqa: E402
+
+METRIC = "D3Q19 MLUPS"
+UNIT = "MLUPS"
+BYTES_PER_NODE = {W.FP64: 304, W.FP32: 152, W.FP32_BF16: 76, W.FP32_FP16: 76}
+SWEEP_SOURCES = ["paper_1906_05445_gb300/csrc/sweep_impl.cuh",
+                 "paper_1906_05445_gb300/csrc/lbm_device.cuh"]
+TRAFFIC_FILE = "profiles/bulk_sweep_d3q19_mrt_fp32_128.md"
+
+
+def workload(precision=W.FP32):
+    base = dict(n=128, radius=12.0, seed=1906, tau=0.6, g=3.4e-8,
+                precision=precision, collision=W.MRT)
+    return [W.fixed_sphere(scheme=W.BOUZIDI_QUAD, **base),
+            W.fixed_sphere(scheme=W.IBM, **base)]
+
+
+def workload_config(problems, precision):
+    p = problems[0]
+    return {"workload": f"sphere_{p.nx}^3_D3Q19_MRT_ibb_quadratic+ibm_side_by_side",
+            "lattice": "D3Q19", "collision": "MRT", "nodes_per_lattice": p.nodes,
+            "lattices": len(problems), "radius": p.solids[0].radius,
+            "centre": [round(c, 6) for c in p.solids[0].centre], "tau": p.tau,
+            "g": p.g[0], "storage": {W.FP32: "fp32 f-w", W.FP64: "fp64",
+                                     W.FP32_BF16: "bf16 f-w", W.FP32_FP16: "fp16 (f-w)*2^10"}[precision],
+            "schemes": ["bouzidi_quadratic", "ibm_direct_forcing(peskin4, n_it=1)"],
+            "l2": "inputs larger than L2: 2 x 159 MB read + 2 x 159 MB written per step"}
+
+
+def sweep_source_hash() -> str:
+    h = hashlib.sha256()
+    for f in SWEEP_SOURCES:
+        with open(os.path.join(ROOT, f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def recorded_traffic():
+    """DRAM bytes per bulk-sweep launch from the committed ncu summary, if it
+    was taken on the current sweep source."""
+    path = os.path.join(ROOT, TRAFFIC_FILE)
+    if not os.path.exists(path):
+        return None
+    txt = open(path).read()
+    m = re.search(r"traffic_bytes_per_launch:\s*([0-9.eE+]+)", txt)
+    s = re.search(r"sweep_source_sha256_16:\s*([0-9a-f]+)", txt)
+    if not m or not s or s.group(1) != sweep_source_hash():
+        return None
+    return float(m.group(1))
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as fh:
+            return json.load(fh), "measured"
+    return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if not self.proc:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=5)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                mx.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", 0))
+    world = int(os.environ.get("WORLD_SIZE", 1))
+    local = int(os.environ.get("LOCAL_RANK", 0))
+    return rank, world, local
+
+
+def reduce_max(value: float, world: int, device) -> float:
+    if world == 1:
+        return value
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def barrier(world: int):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def aggregate(per_rank_units: float, max_seconds: float, world: int) -> float:
+    """Whole-job MLUPS: node updates of all ranks / slowest rank's time."""
+    return per_rank_units * world / max_seconds / 1e6
+
+
+# ------------------------------------------------------------------ oracle
+def make_oracle(p):
+    import oracle as O
+    O.build()
+    s = O.OracleSim(p.lattice, p.nx, p.ny, p.nz, p.tau, p.collision, g=p.g,
+                    force_all=p.force_all)
+    for b in p.solids:
+        s.add_solid(b.kind, b.centre, b.radius, b.velocity, b.omega, b.fluid_inside)
+    s.set_scheme(p.scheme, p.ibm_iters, p.retraction, p.marker_density)
+    return s
+
+
+def oracle_sample(problems, steps_each=2):
+    """Time the FP64 C oracle on the host (one thread) on a bounded sample of
+    the workload: `steps_each` steps of each lattice at full size."""
+    units = 0
+    secs = 0.0
+    for p in problems:
+        o = make_oracle(p)
+        t0 = time.perf_counter()
+        o.step(steps_each)
+        secs += time.perf_counter() - t0
+        units += p.nodes * steps_each
+        o.close()
+    return {"value": units / secs / 1e6, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{steps_each} steps of each of the {len(problems)} lattices at full size "
+                      f"({units} node updates, {secs:.1f} s, FP64, single thread)"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    problems = workload()
+    cpu = oracle_sample(problems, steps_each=1)
+    # the timed reference arm: K steps, each a bounded sample of one step on
+    # one lattice (alternating IBB / IBM)
+    sims = [make_oracle(p) for p in problems]
+    for k in range(args.warmup):
+        sims[k % 2].step(1)
+    t0 = time.perf_counter()
+    units = 0
+    for k in range(args.steps):
+        sims[k % 2].step(1)
+        units += problems[k % 2].nodes
+    secs = time.perf_counter() - t0
+    value = units / secs / 1e6
+    cpu["value"] = value
+    cpu["sample"] = (f"{args.steps} timed steps alternating the two 128^3 lattices, one lattice "
+                     f"per step, FP64 oracle on one host thread")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(problems, W.FP64),
+            "cpu_baseline": cpu,
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local):
+    import torch
+    if not torch.cuda.is_available():
+        raise SystemExit("bench.py needs a CUDA device (the library has no CPU path)")
+    torch.cuda.set_device(local)
+    device = torch.device("cuda", local)
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=device)
+    from paper_1906_05445_gb300 import lbm
+    precision = {"fp32": W.FP32, "bf16": W.FP32_BF16, "fp16": W.FP32_FP16,
+                 "fp64": W.FP64}[args.precision]
+    problems = workload(precision)
+    stream = torch.cuda.current_stream(device)
+    lats = [lbm.Lattice.from_problem(p, stream=stream.cuda_stream) for p in problems]
+    for lt in lats:
+        lt.init_equilibrium()
+    for _ in range(args.warmup):
+        for lt in lats:
+            lt.step(1)
+    for lt in lats:
+        lt.set_timing(True)
+    launches0 = sum(lt.info().kernel_launches for lt in lats)
+    sampler = ClockSampler(local)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(world)
+    torch.cuda.synchronize(device)
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        for lt in lats:
+            lt.step(1)
+    ev1.record(stream)
+    torch.cuda.synchronize(device)
+    barrier(world)
+    clocks = sampler.stop()
+    secs = ev0.elapsed_time(ev1) / 1e3
+    launches = sum(lt.info().kernel_launches for lt in lats) - launches0
+    max_secs = reduce_max(secs, world, device)
+    units = sum(p.nodes for p in problems) * args.steps
+    value = aggregate(units, max_secs, world)
+
+    # dominant kernel: the bulk sweep of the bounce-back lattice
+    ms, nl, nodes = lats[0].kernel_time(lbm.TK_BULK)
+    bpn = BYTES_PER_NODE[precision]
+    per_launch_bytes = nodes / max(nl, 1) * bpn
+    achieved = per_launch_bytes / (ms / max(nl, 1) / 1e3) / 1e9
+    peaks, peak_kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    kt = {}
+    for name, k in (("bulk", lbm.TK_BULK), ("boundary_list", lbm.TK_LIST), ("ibm", lbm.TK_IBM)):
+        kt[name] = [round(lt.kernel_time(k)[0] / max(args.steps, 1), 5) for lt in lats]
+    for lt in lats:
+        lt.set_timing(False)
+    traffic = recorded_traffic() if precision == W.FP32 else None
+
+    # end to end through the C ABI with host buffers: upload the initial
+    # populations of both lattices from pinned memory, step, read the force
+    # and torque of every step, read the velocity field at the end
+    e2e_steps = max(args.steps // 2, 10)
+    # initial populations: the rest state f = w_i, written on the host
+    wq = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
+    pinned_f = []
+    for p in problems:
+        hf = torch.empty((p.Q, p.nodes), dtype=torch.float64, pin_memory=True)
+        hf.numpy()[:] = wq[:, None]
+        pinned_f.append(hf)
+    hu = [torch.empty((3, p.nodes), dtype=torch.float64, pin_memory=True) for p in problems]
+    torch.cuda.synchronize(device)
+    barrier(world)
+    t0 = time.perf_counter()
+    for lt, hf in zip(lats, pinned_f):
+        lt.set_f(hf.numpy())
+    for _ in range(e2e_steps):
+        for lt in lats:
+            lt.step(1)
+            lt.force_torque(0)
+    for lt, u in zip(lats, hu):
+        u.numpy()[:] = lt.velocity().reshape(3, -1)
+    e2e_secs = reduce_max(time.perf_counter() - t0, world, device)
+    e2e_units = sum(p.nodes for p in problems) * e2e_steps
+    h2d = sum(hf.numel() * 8 for hf in pinned_f) / e2e_steps
+    d2h = (48 * len(lats) * e2e_steps + sum(u.numel() * 8 for u in hu)) / e2e_steps
+    e2e = {"value": aggregate(e2e_units, e2e_secs, world), "unit": UNIT,
+           "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+           "steps": e2e_steps,
+           "path": "lbm_set_distributions (pinned FP64 host) + lbm_step(1) and "
+                   "lbm_get_force_torque per step per lattice + lbm_get_velocity at the end"}
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cpu = oracle_sample(problems, steps_each=1)
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+                "steps": args.steps, "warmup": args.warmup,
+                "ms_per_step": max_secs / args.steps * 1e3, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None,
+                "dtype": {W.FP32: "f32", W.FP64: "f64", W.FP32_BF16: "f32 (bf16 storage)",
+                          W.FP32_FP16: "f32 (fp16 storage)"}[precision],
+                "data": "synthetic", "config": workload_config(problems, precision),
+                "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                             "frac": achieved / peak, "traffic": traffic,
+                             "kernel": "k_bulk_sweep<D3Q19,MRT,float>",
+                             "bytes_per_node": bpn, "nodes_per_launch": nodes / max(nl, 1),
+                             "launch_ms": ms / max(nl, 1), "peak_kind": peak_kind + " hbm_gbs"},
+                "kernel_ms_per_step": kt,
+                "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
+                "gpu_launches": int(launches) * world}
+        print(json.dumps(line), flush=True)
+    for lt in lats:
+        lt.close()
+    if world > 1:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"])
+    ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    args = ap.parse_args(argv)
+    args.warmup = max(args.warmup, 3)
+    rank, world, local = dist_env()
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,236 @@
+/*
+ * lbm.h -- C ABI of the GB300 lattice Boltzmann library for curved no-slip
+ * walls: the fused collide-stream sweep with interpolated bounce-back or
+ * direct-forcing immersed boundary, after Peng, Ayala & Wang, "A comparative
+ * study of immersed boundary method and interpolated bounce-back scheme for
+ * no-slip boundary treatment in the lattice Boltzmann method" (arXiv
+ * 1906.05445).
+ *
+ * Units are lattice units throughout: dx = dt = h = 1, c_s^2 = 1/3 and the
+ * reference density rho0 = 1.  Arrays exchanged with the caller are FP64 in
+ * the layout [component][z][y][x] (x fastest; nz = 1 for D2Q9).  Directions
+ * are numbered as follows (e_i):
+ *   D2Q9 : 0 (0,0); 1 (1,0); 2 (0,1); 3 (-1,0); 4 (0,-1); 5 (1,1); 6 (-1,1);
+ *          7 (-1,-1); 8 (1,-1)
+ *   D3Q19: 0 rest; 1 +x; 2 -x; 3 +y; 4 -y; 5 +z; 6 -z; 7 (1,1,0);
+ *          8 (-1,-1,0); 9 (1,-1,0); 10 (-1,1,0); 11 (1,0,1); 12 (-1,0,-1);
+ *          13 (1,0,-1); 14 (-1,0,1); 15 (0,1,1); 16 (0,-1,-1); 17 (0,1,-1);
+ *          18 (0,-1,1)
+ *
+ * Conventions of every entry point:
+ *  - the return value is an lbm_status; on error the context is unchanged
+ *    and lbm_last_error() describes the failure;
+ *  - work is enqueued on the CUDA stream given to lbm_create; the calls
+ *    that return data to the host (queries, lbm_sync, lbm_save) synchronise
+ *    that stream and report any CUDA error raised by earlier work;
+ *  - host buffers belong to the caller and are only read or written during
+ *    the call; device memory belongs to the library;
+ *  - a context is not thread-safe; distinct contexts may share a stream;
+ *  - every simulation step runs in the library's CUDA kernels: there is no
+ *    CPU path, and a missing or unusable GPU is an error (LBM_ERR_CUDA).
+ */
+#ifndef LBM_H
+#define LBM_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lbm_ctx lbm_ctx;
+
+typedef enum {
+  LBM_OK = 0,
+  LBM_ERR_ARG = -1,         /* invalid argument or descriptor */
+  LBM_ERR_OOM = -2,         /* device or host allocation failed */
+  LBM_ERR_CUDA = -3,        /* CUDA runtime error (message in last_error) */
+  LBM_ERR_UNSUPPORTED = -4, /* valid but not implemented combination */
+  LBM_ERR_STATE = -5,       /* call not valid in the current state */
+  LBM_ERR_TIMEOUT = -6,     /* a bounded device wait gave up */
+  LBM_ERR_DIVERGED = -7,    /* non-finite residual */
+  LBM_ERR_CAPACITY = -8     /* a fixed-capacity device list overflowed */
+} lbm_status;
+
+/* lattice selectors */
+enum { LBM_D2Q9 = 0, LBM_D3Q19 = 1 };
+/* collision operators: Eq. 1 (BGK) and Eq. 3 (MRT) */
+enum { LBM_BGK = 0, LBM_MRT = 1 };
+/* storage / compute precision of the distributions */
+enum {
+  LBM_FP64 = 0,           /* FP64 storage and arithmetic (parity build) */
+  LBM_FP32 = 1,           /* FP32 storage of f - w_i, FP32 arithmetic */
+  LBM_FP32_BF16STORE = 2, /* BF16 storage of f - w_i, FP32 arithmetic */
+  LBM_FP32_FP16STORE = 3  /* FP16 storage of scaled f - w_i, FP32 arithmetic */
+};
+/* where the external body force acts */
+enum { LBM_FORCE_FLUID_ONLY = 0, LBM_FORCE_ALL = 1 };
+/* solid shapes */
+enum { LBM_SPHERE = 0, LBM_CYLINDER_Z = 1 };
+/* no-slip schemes (Sec. 2.1 and Sec. 2.2 of the paper) */
+enum {
+  LBM_SCHEME_NONE = 0,    /* solids ignored: periodic box */
+  LBM_BOUNCE_BACK = 1,    /* Eq. 9 */
+  LBM_BOUZIDI_LIN = 2,    /* two-point form of Eq. 11 */
+  LBM_BOUZIDI_QUAD = 3,   /* Eq. 11 */
+  LBM_YU_LIN = 4,         /* two-point form of Eqs. 12-14 */
+  LBM_YU_QUAD = 5,        /* Eqs. 12-14 (the combined Eq. 15) */
+  LBM_IBM_DIRECT = 6      /* direct-forcing IBM, Eqs. 5-10 */
+};
+/* fields for lbm_device_field */
+enum { LBM_FIELD_F_POST = 0, LBM_FIELD_FLAGS = 1 };
+
+/* Lattice: Eq. 1 / Eq. 3 with nu = (tau - 1/2)/3 (Eq. 2).
+ * mrt_rates: relaxation rate per moment (order of the Gram-Schmidt basis:
+ *   D2Q9  rho, e, eps, jx, qx, jy, qy, pxx, pxy;
+ *   D3Q19 rho, e, eps, jx, qx, jy, qy, jz, qz, 3pxx, 3pixx, pww, piww, pxy,
+ *         pyz, pxz, mx, my, mz);
+ *   0 selects the default: 1/tau, except the energy-flux moments q whose rate
+ *   satisfies (tau - 1/2)(1/s_q - 1/2) = 3/16.  The stress rates are always
+ *   1/tau and the conserved moments' rates have no effect.
+ * body_force: uniform force density g (acts on nodes outside every solid
+ *   unless force_region == LBM_FORCE_ALL). */
+typedef struct {
+  int lattice;
+  int nx, ny, nz;
+  double tau;
+  int collision;
+  double mrt_rates[19];
+  int precision;
+  double body_force[3];
+  int force_region;
+} lbm_lattice_desc;
+
+/* Solid: a sphere (a circle on D2Q9) or a cylinder along z.
+ * fluid_inside = 0: the solid is the ball |x - c| <= R;
+ * fluid_inside = 1: the solid is the outside |x - c| >= R (an enclosing
+ *   wall, e.g. the outer cylinder of a Couette cell or a pipe).
+ * velocity: translation speed; the centre moves by velocity per step.
+ * omega: angular velocity; the wall velocity is u_w = U + omega x (x_w - c).
+ * Distances use the nearest periodic image. */
+typedef struct {
+  int kind;
+  double centre[3];
+  double radius;
+  double velocity[3];
+  double omega[3];
+  int fluid_inside;
+} lbm_solid_desc;
+
+/* Scheme.  For LBM_IBM_DIRECT: ibm_iters >= 1 forcing iterations (Eq. 10
+ * applied to the spread force), ibm_retraction = R_d (markers at R - R_d, or
+ * R + R_d for an enclosing wall), ibm_marker_density = markers per unit
+ * surface area (per unit length in 2D), 0 -> 1. */
+typedef struct {
+  int scheme;
+  int ibm_iters;
+  double ibm_retraction;
+  double ibm_marker_density;
+} lbm_scheme_desc;
+
+typedef struct {
+  int64_t nodes;          /* nx * ny * nz */
+  int64_t fluid_nodes;    /* nodes carrying distributions */
+  int64_t list_nodes;     /* nodes handled by the boundary-node kernel */
+  int64_t cut_links;      /* interpolated bounce-back links */
+  int64_t markers;        /* IBM markers over all solids */
+  int64_t steps;          /* steps taken since create */
+  int64_t kernel_launches;/* kernels launched since create */
+  int64_t device_bytes;   /* device memory held */
+  int32_t num_solids;
+  int32_t precision;
+} lbm_info;
+
+/* Create a lattice at rest (f = w_i, no solids, scheme NONE) on the current
+ * CUDA device.  cuda_stream: a cudaStream_t (NULL = legacy default stream).
+ * Errors: LBM_ERR_ARG (bad sizes/tau/selectors), LBM_ERR_OOM, LBM_ERR_CUDA. */
+lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc,
+                      void *cuda_stream);
+void lbm_destroy(lbm_ctx *ctx);
+
+/* Add a solid (at most 8).  Geometry (Fig. 1: solid nodes, cut links, wall
+ * fractions q) is rebuilt before the next step. */
+lbm_status lbm_add_solid(lbm_ctx *ctx, const lbm_solid_desc *solid,
+                         int *solid_id);
+/* Replace the centre, velocity and angular velocity of a solid. */
+lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int solid_id,
+                                const double centre[3],
+                                const double velocity[3],
+                                const double omega[3]);
+lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme);
+
+/* Set the state to the equilibrium at (rho, u) on every fluid node. */
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, double rho, const double u[3]);
+/* Set / read the pre-collision distributions f(x, t) (full f, not f - w):
+ * host array of n = Q * nodes doubles, [Q][z][y][x].  Values at solid nodes
+ * are ignored on input and returned as 0. */
+lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *host_f, size_t n);
+lbm_status lbm_get_distributions(lbm_ctx *ctx, double *host_f, size_t n);
+
+/* Advance nsteps time steps (asynchronous).  One step: geometry of moving
+ * solids and refilling of uncovered nodes, IBM forcing (Sec. 2.1), the fused
+ * pull collide-stream sweep with interpolated bounce-back on cut links
+ * (Sec. 2.2) and the momentum exchange of Eq. 17. */
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
+/* Step in blocks of check_every until the velocity residual
+ * ||u^n - u^(n-K)||_2 / ||u^n||_2 over fluid nodes drops below tol or
+ * max_steps is reached.  LBM_ERR_DIVERGED on a non-finite residual. */
+lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, int check_every,
+                             int max_steps, int *steps_done, double *residual);
+
+/* Fields at the current time (synchronous), 0 at solid nodes:
+ * density [nodes]; velocity [d][nodes] with the half-force correction;
+ * strain rate [d(d+1)/2][nodes] from non-equilibrium moments (Sec. 3.1,
+ *   Eq. 27 generalised), order xx, yy, xy (2D) / xx, yy, zz, xy, yz, xz (3D);
+ * stress = -c_s^2 rho I + 2 rho0 nu S, same order. */
+lbm_status lbm_get_density(lbm_ctx *ctx, double *host_out, size_t n);
+lbm_status lbm_get_velocity(lbm_ctx *ctx, double *host_out, size_t n);
+lbm_status lbm_get_strain_rate(lbm_ctx *ctx, double *host_out, size_t n);
+lbm_status lbm_get_stress(lbm_ctx *ctx, double *host_out, size_t n);
+/* 1 where the node carries no distributions (solid under bounce-back). */
+lbm_status lbm_get_solid_mask(lbm_ctx *ctx, unsigned char *host_out, size_t n);
+
+/* Force and torque on a solid (FP64): under bounce-back the momentum
+ * exchange of Eq. 17 during the most recent streaming; under IBM minus the
+ * sum of marker forces times their control volume at the current time. */
+lbm_status lbm_get_force_torque(lbm_ctx *ctx, int solid_id, double F[3],
+                                double T[3]);
+/* The last min(max_steps, steps kept) records, oldest first, 6 doubles
+ * (Fx Fy Fz Tx Ty Tz) per step; *n receives the count. */
+lbm_status lbm_get_force_history(lbm_ctx *ctx, int solid_id, double *host_out,
+                                 size_t max_steps, size_t *n);
+lbm_status lbm_get_residual(lbm_ctx *ctx, double *residual);
+lbm_status lbm_get_solid_centre(lbm_ctx *ctx, int solid_id, double centre[3]);
+lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info);
+
+/* Borrowed device pointer to an internal field, valid until the next call
+ * that steps or rebuilds the context.  LBM_FIELD_F_POST: the post-collision
+ * deviations f* - w_i in the storage type, [Q][z][y][x] with *dir_stride
+ * elements between consecutive directions (>= nodes: the arrays are padded);
+ * LBM_FIELD_FLAGS: one byte per node.  bytes / dir_stride may be NULL. */
+lbm_status lbm_device_field(lbm_ctx *ctx, int which, void **dptr,
+                            size_t *bytes, size_t *dir_stride);
+
+/* Checkpoint: the full state (distributions, flags of the current geometry,
+ * solids, step count).  With host_buf == NULL *size receives the size. */
+lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size);
+lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size);
+
+/* Per-kernel device timing with CUDA events on the context's stream.
+ * kernel: 0 bulk sweep, 1 boundary-node sweep, 2 IBM (all kernels),
+ * 3 geometry.  Totals since the last reset, in ms, with launch counts and
+ * the number of node updates done by those launches. */
+lbm_status lbm_set_timing(lbm_ctx *ctx, int enable);
+lbm_status lbm_get_kernel_time(lbm_ctx *ctx, int kernel, double *total_ms,
+                               int64_t *launches, int64_t *node_updates);
+
+lbm_status lbm_sync(lbm_ctx *ctx);
+const char *lbm_last_error(const lbm_ctx *ctx);
+/* Library version string. */
+const char *lbm_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

@@ -1,0 +1,1223 @@
+// api.cu -- host side of the C ABI declared in include/lbm.h.
+//
+// The context owns every device buffer.  Its state is the post-collision
+// array f*(t) (`f[cur]`) plus, in `f[1-cur]`, either f*(t-1) (after a step:
+// gathering from it with the current geometry reproduces the pre-collision
+// f(t) for queries) or the pre-collision f(t) itself (after an
+// initialisation: `prev_local`).  One step (Sec. 2 of Peng, Ayala & Wang):
+//   bounce-back: geometry at X(t) (+ refilling) -> sweep -> X += U dt
+//   IBM        : X += U dt -> geometry at X(t+1) -> unforced velocity, force,
+//                spreading -> sweep
+#include <math.h>
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <string>
+#include <vector>
+
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+void launch_sweep_f64(SweepOp, int, int, const KArgs &, cudaStream_t);
+void launch_sweep_f32(SweepOp, int, int, const KArgs &, cudaStream_t);
+void launch_sweep_bf16(SweepOp, int, int, const KArgs &, cudaStream_t);
+void launch_sweep_f16(SweepOp, int, int, const KArgs &, cudaStream_t);
+
+void launch_sweep(SweepOp op, int lattice, int collision, int precision, const KArgs &a,
+                  cudaStream_t st) {
+  switch (precision) {
+  case LBM_FP64: launch_sweep_f64(op, lattice, collision, a, st); break;
+  case LBM_FP32: launch_sweep_f32(op, lattice, collision, a, st); break;
+  case LBM_FP32_BF16STORE: launch_sweep_bf16(op, lattice, collision, a, st); break;
+  default: launch_sweep_f16(op, lattice, collision, a, st); break;
+  }
+}
+}  // namespace lbm
+
+using namespace lbm;
+
+namespace {
+
+constexpr int kHistCap = 4096;          // force records kept (steps)
+constexpr double kFp16Scale = 1024.0;   // FP16 storage keeps (f - w) * 2^10
+constexpr int kGeomMargin = 7;          // box margin around a moving solid
+
+struct SolidHost {
+  lbm_solid_desc d;
+  double c[3];   // centre now
+  double cg[3];  // centre of the current geometry
+};
+
+const double PI = 3.14159265358979323846;
+
+}  // namespace
+
+struct lbm_ctx {
+  lbm_lattice_desc d;
+  int Q = 0, D = 0;
+  long long N = 0;
+  long long fs = 0;  // direction stride of the distribution arrays (elements)
+  int bulk_block = 128;
+  cudaStream_t st = 0;
+  // auxiliary high-priority stream: the boundary-node sweep and the IBM
+  // pre-pass run there, concurrently with the bulk sweep on `st`
+  cudaStream_t aux = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  int device = 0;
+  size_t ssz = 0;  // storage element size
+  size_t tsz = 0;  // compute element size
+  void *f[2] = {nullptr, nullptr};
+  int cur = 0;
+  bool prev_local = true, need_collide = true;
+  uint8_t *flags = nullptr, *sid = nullptr;
+  int *counts = nullptr;  // 16 ints
+  int *list_node = nullptr;
+  uint32_t *list_mask = nullptr;
+  int *list_link = nullptr;
+  double *list_cst = nullptr;
+  int list_cap = 0, link_cap = 0, refill_cap = 0;
+  int list_count = -1, link_count = -1;  // known after a static build
+  long long bulk_nodes = 0;              // plain fluid nodes at the last full build
+  void *link_mem = nullptr;
+  LinkArrays links{};
+  int *refill_node = nullptr;
+  uint8_t *refill_sid = nullptr;
+  // IBM
+  double *mk_dir = nullptr, *mk_dV = nullptr, *mk_F = nullptr;
+  uint8_t *mk_sid = nullptr;
+  int nmark = 0;
+  void *u_band = nullptr, *f_ibm = nullptr;
+  // forces
+  double *hist = nullptr;
+  int slot = 0;
+  long long records = 0;
+  // queries / residual
+  double *qbuf = nullptr;
+  size_t qbuf_elems = 0;
+  double *u_now = nullptr, *u_snap = nullptr, *red2 = nullptr;
+  double last_residual = NAN;
+  // host state
+  std::vector<SolidHost> solids;
+  lbm_scheme_desc scheme{};
+  bool geom_dirty = true, restore_geometry = false;
+  long long step = 0, launches = 0;
+  size_t dev_bytes = 0;
+  std::string err;
+  // collision constants
+  double omega = 0, ds[19] = {0}, s_bulk = 0, nu = 0, inv_scale = 1;
+  // timing
+  bool timing = false;
+  struct Pending {
+    cudaEvent_t a, b;
+    int kind;
+    long long nodes;
+  };
+  std::vector<Pending> pending;
+  std::vector<cudaEvent_t> free_events;
+  double tk_ms[TK_COUNT] = {0};
+  long long tk_launch[TK_COUNT] = {0}, tk_nodes[TK_COUNT] = {0};
+  std::vector<void *> allocs;
+};
+
+namespace {
+
+lbm_status fail(lbm_ctx *c, lbm_status s, const std::string &m) {
+  if (c) c->err = m;
+  return s;
+}
+
+lbm_status cuda_check(lbm_ctx *c, cudaError_t e, const char *what) {
+  if (e == cudaSuccess) return LBM_OK;
+  return fail(c, e == cudaErrorMemoryAllocation ? LBM_ERR_OOM : LBM_ERR_CUDA,
+              std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+#define CK(expr)                                              \
+  do {                                                        \
+    lbm_status _s = cuda_check(ctx, (expr), #expr);           \
+    if (_s != LBM_OK) return _s;                              \
+  } while (0)
+#define TRY(expr)                                             \
+  do {                                                        \
+    lbm_status _s = (expr);                                   \
+    if (_s != LBM_OK) return _s;                              \
+  } while (0)
+
+lbm_status dalloc(lbm_ctx *ctx, void **p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return LBM_OK;
+  cudaError_t e = cudaMalloc(p, bytes);
+  if (e != cudaSuccess) {
+    *p = nullptr;
+    cudaGetLastError();
+    return fail(ctx, LBM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) + " bytes failed");
+  }
+  ctx->dev_bytes += bytes;
+  ctx->allocs.push_back(*p);
+  return LBM_OK;
+}
+
+void dfree(lbm_ctx *ctx, void *p) {
+  if (!p) return;
+  auto it = std::find(ctx->allocs.begin(), ctx->allocs.end(), p);
+  if (it != ctx->allocs.end()) ctx->allocs.erase(it);
+  cudaFree(p);
+}
+
+bool is_ibb(int s) { return s >= LBM_BOUNCE_BACK && s <= LBM_YU_QUAD; }
+
+// ---- timing helpers (CUDA events on the context's stream)
+cudaEvent_t take_event(lbm_ctx *ctx) {
+  if (!ctx->free_events.empty()) {
+    cudaEvent_t e = ctx->free_events.back();
+    ctx->free_events.pop_back();
+    return e;
+  }
+  cudaEvent_t e;
+  cudaEventCreate(&e);
+  return e;
+}
+
+struct Timed {
+  lbm_ctx *ctx;
+  int kind;
+  long long nodes;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  Timed(lbm_ctx *c, int k, long long n, cudaStream_t stream) : ctx(c), kind(k), nodes(n), s(stream) {
+    if (ctx->timing) {
+      a = take_event(ctx);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~Timed() {
+    if (ctx->timing) {
+      cudaEvent_t b = take_event(ctx);
+      cudaEventRecord(b, s);
+      ctx->pending.push_back({a, b, kind, nodes});
+    }
+  }
+};
+
+void resolve_timing(lbm_ctx *ctx) {
+  for (auto &p : ctx->pending) {
+    float ms = 0;
+    if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) {
+      ctx->tk_ms[p.kind] += ms;
+      ctx->tk_launch[p.kind] += 1;
+      ctx->tk_nodes[p.kind] += p.nodes;
+    }
+    ctx->free_events.push_back(p.a);
+    ctx->free_events.push_back(p.b);
+  }
+  ctx->pending.clear();
+}
+
+// ---- kernel argument assembly
+SolidsDev solids_dev(const lbm_ctx *ctx, bool geometry_centres) {
+  SolidsDev s{};
+  s.n = (int)ctx->solids.size();
+  for (int k = 0; k < s.n; k++) {
+    const SolidHost &h = ctx->solids[k];
+    SolidDev &o = s.s[k];
+    o.kind = h.d.kind;
+    o.fluid_inside = h.d.fluid_inside;
+    o.R = h.d.radius;
+    for (int a = 0; a < 3; a++) {
+      o.c[a] = geometry_centres ? h.cg[a] : h.c[a];
+      o.U[a] = h.d.velocity[a];
+      o.Om[a] = h.d.omega[a];
+    }
+    if (ctx->D == 2) {
+      o.c[2] = 0;
+      o.U[2] = 0;
+      o.Om[0] = o.Om[1] = 0;
+    }
+    const double rd = ctx->scheme.ibm_retraction;
+    o.RL = h.d.fluid_inside ? h.d.radius + rd : h.d.radius - rd;
+  }
+  return s;
+}
+
+KArgs base_args(lbm_ctx *ctx) {
+  KArgs a;
+  memset(&a, 0, sizeof(a));
+  a.nx = ctx->d.nx;
+  a.ny = ctx->d.ny;
+  a.nz = ctx->D == 2 ? 1 : ctx->d.nz;
+  a.N = ctx->N;
+  a.fs = ctx->fs;
+  a.bulk_block = ctx->bulk_block;
+  a.flags = ctx->flags;
+  a.omega = ctx->omega;
+  for (int k = 0; k < 19; k++) a.ds[k] = ctx->ds[k];
+  a.s_bulk = ctx->s_bulk;
+  a.nu = ctx->nu;
+  for (int k = 0; k < 3; k++) a.g[k] = ctx->d.body_force[k];
+  if (ctx->D == 2) a.g[2] = 0;
+  a.inv_scale = ctx->inv_scale;
+  a.omega_f = (float)a.omega;
+  for (int k = 0; k < 19; k++) a.ds_f[k] = (float)a.ds[k];
+  for (int k = 0; k < 3; k++) a.g_f[k] = (float)a.g[k];
+  a.inv_scale_f = (float)a.inv_scale;
+  a.list_node = ctx->list_node;
+  a.list_mask = ctx->list_mask;
+  a.list_link = ctx->list_link;
+  a.list_cst = ctx->list_cst;
+  a.counts = ctx->counts;
+  a.list_cap = ctx->list_count >= 0 ? std::min(ctx->list_count, ctx->list_cap) : ctx->list_cap;
+  a.links = ctx->links;
+  a.f_ibm = ctx->f_ibm;
+  a.u_band = ctx->u_band;
+  a.nsolids = (int)ctx->solids.size();
+  a.refill_node = ctx->refill_node;
+  a.refill_sid = ctx->refill_sid;
+  a.refill_cap = ctx->refill_cap;
+  a.solids = solids_dev(ctx, true);
+  a.sid = ctx->sid;
+  return a;
+}
+
+void sweep(lbm_ctx *ctx, SweepOp op, const KArgs &a, cudaStream_t s) {
+  launch_sweep(op, ctx->d.lattice, ctx->d.collision, ctx->d.precision, a, s);
+  ctx->launches++;
+}
+void sweep(lbm_ctx *ctx, SweepOp op, const KArgs &a) { sweep(ctx, op, a, ctx->st); }
+
+// ---- geometry
+void solid_box(const lbm_ctx *ctx, const SolidHost &s, GeomBox &b) {
+  const int n[3] = {ctx->d.nx, ctx->d.ny, ctx->D == 2 ? 1 : ctx->d.nz};
+  int o[3], w[3];
+  for (int a = 0; a < 3; a++) {
+    const bool full = s.d.fluid_inside || (a == 2 && (ctx->D == 2 || s.d.kind == LBM_CYLINDER_Z));
+    const double ext = s.d.radius + kGeomMargin + fabs(ctx->scheme.ibm_retraction);
+    int lo = (int)floor(s.cg[a] - ext), hi = (int)ceil(s.cg[a] + ext);
+    if (full || hi - lo + 1 >= n[a]) {
+      o[a] = 0;
+      w[a] = n[a];
+    } else {
+      o[a] = lo;
+      w[a] = hi - lo + 1;
+    }
+  }
+  b = {o[0], o[1], o[2], w[0], w[1], w[2]};
+}
+
+bool any_moving(const lbm_ctx *ctx) {
+  for (auto &s : ctx->solids)
+    if (s.d.velocity[0] != 0 || s.d.velocity[1] != 0 || (ctx->D == 3 && s.d.velocity[2] != 0))
+      return true;
+  return false;
+}
+
+lbm_status ensure_list_capacity(lbm_ctx *ctx, int list_cap, int link_cap, int refill_cap) {
+  if (list_cap > ctx->list_cap || refill_cap > ctx->refill_cap) {
+    dfree(ctx, ctx->list_node);
+    dfree(ctx, ctx->list_mask);
+    dfree(ctx, ctx->list_link);
+    dfree(ctx, ctx->list_cst);
+    dfree(ctx, ctx->refill_node);
+    dfree(ctx, ctx->refill_sid);
+    ctx->list_node = nullptr;
+    ctx->list_mask = nullptr;
+    ctx->list_link = nullptr;
+    ctx->list_cst = nullptr;
+    ctx->refill_node = nullptr;
+    ctx->refill_sid = nullptr;
+    const int lc = std::max(list_cap, 1), rc = std::max(refill_cap, 1);
+    TRY(dalloc(ctx, (void **)&ctx->list_node, sizeof(int) * lc));
+    TRY(dalloc(ctx, (void **)&ctx->list_mask, sizeof(uint32_t) * lc));
+    TRY(dalloc(ctx, (void **)&ctx->list_link, sizeof(int) * lc));
+    TRY(dalloc(ctx, (void **)&ctx->list_cst, sizeof(double) * 6 * lc));
+    TRY(dalloc(ctx, (void **)&ctx->refill_node, sizeof(int) * rc));
+    TRY(dalloc(ctx, (void **)&ctx->refill_sid, rc));
+    ctx->list_cap = list_cap;
+    ctx->refill_cap = refill_cap;
+  }
+  if (link_cap > ctx->link_cap) {
+    dfree(ctx, ctx->link_mem);
+    ctx->link_mem = nullptr;
+    const size_t lk = std::max(link_cap, 1);
+    const size_t per = 12 * ctx->tsz + 1;
+    TRY(dalloc(ctx, &ctx->link_mem, per * lk + 64));
+    char *p = (char *)ctx->link_mem;
+    for (int k = 0; k < 5; k++) {
+      ctx->links.c[k] = p;
+      p += ctx->tsz * lk;
+    }
+    ctx->links.mw = p;
+    p += ctx->tsz * lk;
+    for (int k = 0; k < 3; k++) {
+      ctx->links.uw[k] = p;
+      p += ctx->tsz * lk;
+    }
+    for (int k = 0; k < 3; k++) {
+      ctx->links.arm[k] = p;
+      p += ctx->tsz * lk;
+    }
+    ctx->links.sid = (uint8_t *)p;
+    ctx->link_cap = link_cap;
+  }
+  return LBM_OK;
+}
+
+GeomArgs geom_args(lbm_ctx *ctx) {
+  GeomArgs g;
+  memset(&g, 0, sizeof(g));
+  g.nx = ctx->d.nx;
+  g.ny = ctx->d.ny;
+  g.nz = ctx->D == 2 ? 1 : ctx->d.nz;
+  g.N = ctx->N;
+  g.lattice = ctx->d.lattice;
+  g.scheme = ctx->scheme.scheme;
+  g.force_all = ctx->d.force_region == LBM_FORCE_ALL;
+  g.solids = solids_dev(ctx, true);
+  g.flags = ctx->flags;
+  g.sid = ctx->sid;
+  g.counts = ctx->counts;
+  g.list_node = ctx->list_node;
+  g.list_mask = ctx->list_mask;
+  g.list_link = ctx->list_link;
+  g.list_cst = ctx->list_cst;
+  g.list_cap = ctx->list_cap;
+  g.link_cap = ctx->link_cap;
+  g.links = ctx->links;
+  g.refill_node = ctx->refill_node;
+  g.refill_sid = ctx->refill_sid;
+  g.refill_cap = ctx->refill_cap;
+  g.band_w = 2.0 * sqrt((double)ctx->D) + 1e-6;
+  return g;
+}
+
+void set_boxes(lbm_ctx *ctx, GeomArgs &g, bool full) {
+  if (full || ctx->solids.empty()) {
+    g.nbox = 1;
+    g.box[0] = {0, 0, 0, g.nx, g.ny, g.nz};
+  } else {
+    g.nbox = (int)ctx->solids.size();
+    for (int k = 0; k < g.nbox; k++) solid_box(ctx, ctx->solids[k], g.box[k]);
+  }
+  g.box_offset[0] = 0;
+  for (int k = 0; k < g.nbox; k++)
+    g.box_offset[k + 1] = g.box_offset[k] + (long long)g.box[k].bx * g.box[k].by * g.box[k].bz;
+}
+
+lbm_status build_markers(lbm_ctx *ctx) {
+  dfree(ctx, ctx->mk_dir);
+  dfree(ctx, ctx->mk_dV);
+  dfree(ctx, ctx->mk_F);
+  dfree(ctx, ctx->mk_sid);
+  ctx->mk_dir = ctx->mk_dV = ctx->mk_F = nullptr;
+  ctx->mk_sid = nullptr;
+  ctx->nmark = 0;
+  if (ctx->scheme.scheme != LBM_IBM_DIRECT || ctx->solids.empty()) return LBM_OK;
+  std::vector<double> dx, dy, dz, dV;
+  std::vector<uint8_t> ms;
+  const double dens = ctx->scheme.ibm_marker_density > 0 ? ctx->scheme.ibm_marker_density : 1.0;
+  for (size_t k = 0; k < ctx->solids.size(); k++) {
+    const SolidHost &s = ctx->solids[k];
+    const double rd = ctx->scheme.ibm_retraction;
+    const double RL = s.d.fluid_inside ? s.d.radius + rd : s.d.radius - rd;
+    if (ctx->D == 3 && s.d.kind == LBM_SPHERE) {
+      // golden-angle points on the sphere, about `dens` per unit area
+      const double area = 4 * PI * RL * RL;
+      int n = (int)lround(dens * area);
+      if (n < 1) n = 1;
+      const double ga = PI * (3 - sqrt(5.0));
+      for (int m = 0; m < n; m++) {
+        const double z = 1 - (2.0 * m + 1) / n, r = sqrt(1 - z * z);
+        dx.push_back(r * cos(ga * m));
+        dy.push_back(r * sin(ga * m));
+        dz.push_back(z);
+        dV.push_back(area / n);
+        ms.push_back((uint8_t)k);
+      }
+    } else {
+      // uniform angles on a circle; one ring per z-plane for a cylinder on
+      // a 3D lattice (dz holds the plane)
+      const double circ = 2 * PI * RL;
+      int per = (int)lround(dens * circ);
+      if (per < 1) per = 1;
+      const int rings = ctx->D == 3 ? ctx->d.nz : 1;
+      for (int r = 0; r < rings; r++)
+        for (int m = 0; m < per; m++) {
+          const double th = 2 * PI * m / per;
+          dx.push_back(cos(th));
+          dy.push_back(sin(th));
+          dz.push_back((double)r);
+          dV.push_back(circ / per);
+          ms.push_back((uint8_t)k);
+        }
+    }
+  }
+  const int n = (int)dx.size();
+  std::vector<double> dir(3 * (size_t)n);
+  for (int m = 0; m < n; m++) {
+    dir[m] = dx[m];
+    dir[n + m] = dy[m];
+    dir[2 * n + m] = dz[m];
+  }
+  TRY(dalloc(ctx, (void **)&ctx->mk_dir, sizeof(double) * 3 * n));
+  TRY(dalloc(ctx, (void **)&ctx->mk_dV, sizeof(double) * n));
+  TRY(dalloc(ctx, (void **)&ctx->mk_F, sizeof(double) * 3 * n));
+  TRY(dalloc(ctx, (void **)&ctx->mk_sid, n));
+  CK(cudaMemcpyAsync(ctx->mk_dir, dir.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->mk_dV, dV.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->mk_sid, ms.data(), n, cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->nmark = n;
+  if (!ctx->u_band) {
+    TRY(dalloc(ctx, &ctx->u_band, 3 * ctx->tsz * ctx->N));
+    TRY(dalloc(ctx, &ctx->f_ibm, 3 * ctx->tsz * ctx->N));
+    CK(cudaMemsetAsync(ctx->u_band, 0, 3 * ctx->tsz * ctx->N, ctx->st));
+    CK(cudaMemsetAsync(ctx->f_ibm, 0, 3 * ctx->tsz * ctx->N, ctx->st));
+  }
+  return LBM_OK;
+}
+
+lbm_status read_counts(lbm_ctx *ctx, int out[16]) {
+  CK(cudaMemcpyAsync(out, ctx->counts, 16 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  return LBM_OK;
+}
+
+// Full rebuild over the whole lattice (solids or scheme changed): count the
+// boundary nodes and links first, size the lists exactly, then build.
+lbm_status rebuild_full(lbm_ctx *ctx) {
+  if (!ctx->restore_geometry)
+    for (auto &s : ctx->solids) memcpy(s.cg, s.c, sizeof(s.c));
+  ctx->restore_geometry = false;
+  TRY(build_markers(ctx));
+  GeomArgs g = geom_args(ctx);
+  set_boxes(ctx, g, true);
+  g.list_cap = g.link_cap = g.refill_cap = 0;
+  g.track_new = 0;
+  CK(cudaMemsetAsync(ctx->counts, 0, 16 * sizeof(int), ctx->st));
+  launch_geometry(g, ctx->d.precision, ctx->st);
+  ctx->launches += 3;
+  int cnt[16];
+  TRY(read_counts(ctx, cnt));
+  const bool moving = any_moving(ctx);
+  int list_cap = cnt[0], link_cap = cnt[1], refill_cap = 0;
+  if (moving) {
+    // per-step rebuilds over the solids' boxes: bound by the box volume
+    GeomArgs gb = g;
+    set_boxes(ctx, gb, false);
+    const long long vol = gb.box_offset[gb.nbox];
+    const long long lb = std::min<long long>(vol, 2LL * cnt[0] + 4096);
+    const long long kb = std::min<long long>((long long)(ctx->Q - 1) * vol, 2LL * cnt[1] + 4096LL * 8);
+    list_cap = (int)lb;
+    link_cap = (int)kb;
+    refill_cap = (int)std::min<long long>(vol, 1 << 20);
+  }
+  TRY(ensure_list_capacity(ctx, list_cap, link_cap, refill_cap));
+  g = geom_args(ctx);
+  set_boxes(ctx, g, true);
+  g.refill_cap = 0;
+  g.track_new = 0;
+  CK(cudaMemsetAsync(ctx->counts, 0, 16 * sizeof(int), ctx->st));
+  launch_geometry(g, ctx->d.precision, ctx->st);
+  ctx->launches += 3;
+  TRY(read_counts(ctx, cnt));
+  if (cnt[3]) return fail(ctx, LBM_ERR_CAPACITY, "boundary list overflow during rebuild");
+  ctx->list_count = moving ? -1 : cnt[0];
+  ctx->link_count = moving ? -1 : cnt[1];
+  {
+    std::vector<uint8_t> fl(ctx->N);
+    CK(cudaMemcpyAsync(fl.data(), ctx->flags, ctx->N, cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    long long b = 0;
+    for (long long k = 0; k < ctx->N; k++) b += fl[k] == 0;
+    ctx->bulk_nodes = b;
+  }
+  ctx->geom_dirty = false;
+  return LBM_OK;
+}
+
+// Per-step rebuild over the boxes of the solids (moving geometry).
+lbm_status rebuild_boxes(lbm_ctx *ctx) {
+  for (auto &s : ctx->solids) memcpy(s.cg, s.c, sizeof(s.c));
+  GeomArgs g = geom_args(ctx);
+  set_boxes(ctx, g, false);
+  g.track_new = is_ibb(ctx->scheme.scheme) ? 1 : 0;
+  CK(cudaMemsetAsync(ctx->counts, 0, 4 * sizeof(int), ctx->st));
+  Timed tm(ctx, TK_GEOM, 0, ctx->st);
+  launch_geometry(g, ctx->d.precision, ctx->st);
+  ctx->launches += 3;
+  return LBM_OK;
+}
+
+lbm_status ensure_geometry(lbm_ctx *ctx) {
+  if (ctx->geom_dirty) return rebuild_full(ctx);
+  return LBM_OK;
+}
+
+double *force_slot(lbm_ctx *ctx, int slot) {
+  return ctx->hist + (size_t)slot * kMaxSolids * 6;
+}
+
+// IBM: unforced velocity at the band, n_it interpolation/force iterations,
+// spreading, and the solid's force (into the given record slot).
+void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStream_t s) {
+  if (ctx->scheme.scheme != LBM_IBM_DIRECT || ctx->nmark == 0) return;
+  Timed tm(ctx, TK_IBM, 0, s);
+  KArgs a = base_args(ctx);
+  a.src = src;
+  a.local_gather = local ? 1 : 0;
+  sweep(ctx, OP_BAND_VEL, a, s);
+  IbmArgs ib;
+  memset(&ib, 0, sizeof(ib));
+  ib.nx = a.nx;
+  ib.ny = a.ny;
+  ib.nz = a.nz;
+  ib.dim = ctx->D;
+  ib.N = ctx->N;
+  ib.nmark = ctx->nmark;
+  ib.dir = ctx->mk_dir;
+  ib.dV = ctx->mk_dV;
+  ib.msid = ctx->mk_sid;
+  ib.Fm = ctx->mk_F;
+  ib.solids = solids_dev(ctx, true);
+  ib.u_band = ctx->u_band;
+  ib.f_ibm = ctx->f_ibm;
+  ib.force_acc = acc;
+  const int iters = std::max(1, ctx->scheme.ibm_iters);
+  for (int it = 0; it < iters; it++) {
+    ib.first = it == 0;
+    ib.use_f = it > 0;
+    launch_ibm_interp(ib, ctx->d.precision, s);
+    if (it > 0) {
+      launch_zero_band(a, ctx->d.precision, s);
+      ctx->launches++;
+    }
+    ib.reduce_force = it == iters - 1;
+    launch_ibm_spread(ib, ctx->d.precision, s);
+    ctx->launches += 2;
+  }
+}
+
+// Collide the pre-collision state held in f[1-cur] into f[cur].
+lbm_status init_collide(lbm_ctx *ctx) {
+  TRY(ensure_geometry(ctx));
+  const int prev = 1 - ctx->cur;
+  ctx->slot = (ctx->slot + 1) % kHistCap;
+  double *acc = force_slot(ctx, ctx->slot);
+  CK(cudaMemsetAsync(acc, 0, sizeof(double) * kMaxSolids * 6, ctx->st));
+  ibm_prepass(ctx, ctx->f[prev], true, acc, ctx->st);
+  KArgs a = base_args(ctx);
+  a.src = ctx->f[prev];
+  a.dst = ctx->f[ctx->cur];
+  sweep(ctx, OP_LOCAL_INIT, a);
+  ctx->need_collide = false;
+  ctx->prev_local = true;
+  ctx->records = std::min<long long>(ctx->records + 1, kHistCap);
+  return LBM_OK;
+}
+
+lbm_status prepare(lbm_ctx *ctx) {
+  TRY(ensure_geometry(ctx));
+  if (ctx->need_collide) TRY(init_collide(ctx));
+  return LBM_OK;
+}
+
+lbm_status step_once(lbm_ctx *ctx) {
+  const bool moving = any_moving(ctx);
+  const bool ibm = ctx->scheme.scheme == LBM_IBM_DIRECT;
+  if (ibm && moving)
+    for (auto &s : ctx->solids)
+      for (int a = 0; a < 3; a++) s.c[a] += s.d.velocity[a];
+  if (moving) TRY(rebuild_boxes(ctx));
+  const int cur = ctx->cur, nxt = 1 - ctx->cur;
+  KArgs a = base_args(ctx);
+  if (moving && is_ibb(ctx->scheme.scheme)) {
+    // refill nodes uncovered since the previous geometry (into f*(t))
+    a.src = ctx->f[cur];
+    a.dst = ctx->f[cur];
+    sweep(ctx, OP_REFILL, a);
+    launch_clear_new(ctx->flags, ctx->counts, ctx->refill_node, ctx->refill_cap, ctx->st);
+    ctx->launches++;
+  }
+  ctx->slot = (ctx->slot + 1) % kHistCap;
+  double *acc = force_slot(ctx, ctx->slot);
+  a = base_args(ctx);
+  a.src = ctx->f[cur];
+  a.dst = ctx->f[nxt];
+  a.force_acc = acc;
+  // fork: the boundary nodes (and the IBM pre-pass that feeds them) on the
+  // auxiliary stream, the bulk nodes on the main stream; they read the same
+  // f*(t) and write disjoint nodes of f*(t+1)
+  CK(cudaEventRecord(ctx->ev_fork, ctx->st));
+  CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
+  CK(cudaMemsetAsync(acc, 0, sizeof(double) * kMaxSolids * 6, ctx->aux));
+  ibm_prepass(ctx, ctx->f[cur], false, acc, ctx->aux);
+  {
+    Timed tm(ctx, TK_LIST, ctx->list_count >= 0 ? ctx->list_count : 0, ctx->aux);
+    sweep(ctx, OP_LIST_SWEEP, a, ctx->aux);
+  }
+  {
+    Timed tm(ctx, TK_BULK, ctx->bulk_nodes, ctx->st);
+    sweep(ctx, OP_BULK_SWEEP, a, ctx->st);
+  }
+  // join
+  CK(cudaEventRecord(ctx->ev_join, ctx->aux));
+  CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
+  ctx->cur = nxt;
+  ctx->prev_local = false;
+  if (!ibm && moving)
+    for (auto &s : ctx->solids)
+      for (int k = 0; k < 3; k++) s.c[k] += s.d.velocity[k];
+  ctx->records = std::min<long long>(ctx->records + 1, kHistCap);
+  ctx->step++;
+  return LBM_OK;
+}
+
+lbm_status qbuf_ensure(lbm_ctx *ctx, size_t elems) {
+  if (elems <= ctx->qbuf_elems) return LBM_OK;
+  dfree(ctx, ctx->qbuf);
+  ctx->qbuf = nullptr;
+  TRY(dalloc(ctx, (void **)&ctx->qbuf, elems * sizeof(double)));
+  ctx->qbuf_elems = elems;
+  return LBM_OK;
+}
+
+// Run the query kernels with the given FP64 device outputs (pre-zeroed).
+void run_query(lbm_ctx *ctx, KArgs a) {
+  a.src = ctx->f[1 - ctx->cur];
+  if (ctx->prev_local) {
+    a.local_gather = 1;
+    sweep(ctx, OP_LOCAL_QUERY, a);
+  } else {
+    a.local_gather = 0;
+    sweep(ctx, OP_BULK_QUERY, a);
+    sweep(ctx, OP_LIST_QUERY, a);
+  }
+}
+
+enum QueryKind { Q_RHO, Q_U, Q_S, Q_STRESS, Q_F };
+
+lbm_status query(lbm_ctx *ctx, QueryKind kind, double *host, size_t n) {
+  if (!ctx) return LBM_ERR_ARG;
+  const int nc = ctx->D == 2 ? 3 : 6;
+  size_t comps = kind == Q_RHO ? 1 : kind == Q_U ? ctx->D : kind == Q_F ? ctx->Q : nc;
+  const size_t need = comps * (size_t)ctx->N;
+  if (!host || n < need) return fail(ctx, LBM_ERR_ARG, "output buffer too small: need " + std::to_string(need));
+  TRY(prepare(ctx));
+  TRY(qbuf_ensure(ctx, need));
+  CK(cudaMemsetAsync(ctx->qbuf, 0, need * sizeof(double), ctx->st));
+  KArgs a = base_args(ctx);
+  switch (kind) {
+  case Q_RHO: a.out_rho = ctx->qbuf; break;
+  case Q_U: a.out_u = ctx->qbuf; break;
+  case Q_S: a.out_S = ctx->qbuf; break;
+  case Q_STRESS: a.out_stress = ctx->qbuf; break;
+  case Q_F: a.out_f = ctx->qbuf; break;
+  }
+  run_query(ctx, a);
+  CK(cudaMemcpyAsync(host, ctx->qbuf, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status velocity_to(lbm_ctx *ctx, double *dev) {
+  CK(cudaMemsetAsync(dev, 0, sizeof(double) * ctx->D * ctx->N, ctx->st));
+  KArgs a = base_args(ctx);
+  a.out_u = dev;
+  run_query(ctx, a);
+  return LBM_OK;
+}
+
+void set_collision_constants(lbm_ctx *ctx) {
+  const lbm_lattice_desc &d = ctx->d;
+  ctx->omega = 1.0 / d.tau;
+  ctx->nu = (d.tau - 0.5) / 3.0;
+  const double sq = 1.0 / (0.5 + (3.0 / 16.0) / (d.tau - 0.5));
+  // kinds of the moment rows (see include/lbm.h): c conserved, b energy,
+  // e energy square, q energy flux, v stress, p / m ghosts
+  const char *k9 = "cbecqcqvv", *k19 = "cbecqcqcqvpvpvvvmmm";
+  const char *kind = d.lattice == LBM_D2Q9 ? k9 : k19;
+  for (int k = 0; k < 19; k++) ctx->ds[k] = 0;
+  ctx->s_bulk = ctx->omega;
+  if (d.collision == LBM_MRT) {
+    for (int k = 0; k < ctx->Q; k++) {
+      double s = kind[k] == 'q' ? sq : ctx->omega;
+      if (kind[k] != 'v' && kind[k] != 'c' && d.mrt_rates[k] != 0) s = d.mrt_rates[k];
+      if (kind[k] != 'c') ctx->ds[k] = ctx->omega - s;
+      if (kind[k] == 'b') ctx->s_bulk = s;
+    }
+  }
+  ctx->inv_scale = d.precision == LBM_FP32_FP16STORE ? 1.0 / kFp16Scale : 1.0;
+}
+
+}  // namespace
+
+// ===================================================================== ABI
+extern "C" {
+
+const char *lbm_version(void) { return "lbm-gb300 0.1 (sm_103a)"; }
+
+const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
+
+lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_stream) {
+  if (!out || !desc) return LBM_ERR_ARG;
+  *out = nullptr;
+  const lbm_lattice_desc &d = *desc;
+  if (d.lattice != LBM_D2Q9 && d.lattice != LBM_D3Q19) return LBM_ERR_ARG;
+  if (d.nx < 1 || d.ny < 1 || (d.lattice == LBM_D3Q19 && d.nz < 1)) return LBM_ERR_ARG;
+  if (!(d.tau > 0.5) || !(d.tau < 1e6)) return LBM_ERR_ARG;
+  if (d.collision != LBM_BGK && d.collision != LBM_MRT) return LBM_ERR_ARG;
+  if (d.precision < LBM_FP64 || d.precision > LBM_FP32_FP16STORE) return LBM_ERR_ARG;
+  const long long N = (long long)d.nx * d.ny * (d.lattice == LBM_D2Q9 ? 1 : d.nz);
+  if (N > (1LL << 31) - 1) return LBM_ERR_UNSUPPORTED;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || ndev == 0) {
+    cudaGetLastError();
+    return LBM_ERR_CUDA;
+  }
+  lbm_ctx *ctx = new lbm_ctx();
+  ctx->d = d;
+  if (d.lattice == LBM_D2Q9) ctx->d.nz = 1;
+  ctx->Q = d.lattice == LBM_D2Q9 ? 9 : 19;
+  ctx->D = d.lattice == LBM_D2Q9 ? 2 : 3;
+  ctx->N = N;
+  ctx->st = (cudaStream_t)cuda_stream;
+  cudaGetDevice(&ctx->device);
+  {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      lbm_destroy(ctx);
+      return LBM_ERR_CUDA;
+    }
+  }
+  ctx->ssz = d.precision == LBM_FP64 ? 8 : d.precision == LBM_FP32 ? 4 : 2;
+  ctx->tsz = d.precision == LBM_FP64 ? 8 : 4;
+  set_collision_constants(ctx);
+  // Direction arrays are spaced by an odd number of 128-byte lines beyond a
+  // whole number of line pairs, so that the Q read and Q write streams of a
+  // warp do not fall on the same cache sets and memory channels when the
+  // node count is a power of two.  LBM_DIR_PAD_LINES overrides the padding
+  // (0: arrays back to back), LBM_BULK_BLOCK the bulk block width.
+  {
+    const long long line = 128 / (long long)ctx->ssz;
+    long long pad = 1;
+    if (const char *e = getenv("LBM_DIR_PAD_LINES")) pad = atoll(e);
+    ctx->fs = pad <= 0 ? N : ((N + 2 * line - 1) / (2 * line)) * (2 * line) + pad * line;
+    if (const char *e = getenv("LBM_BULK_BLOCK")) {
+      const int b = atoi(e);
+      if (b >= 32 && b <= 512 && b % 32 == 0) ctx->bulk_block = b;
+    }
+  }
+  lbm_status s = LBM_OK;
+  const size_t fbytes = (size_t)ctx->Q * ctx->fs * ctx->ssz;
+  const size_t padN = ((N + 15) / 16) * 16;
+  if ((s = dalloc(ctx, &ctx->f[0], fbytes)) != LBM_OK ||
+      (s = dalloc(ctx, &ctx->f[1], fbytes)) != LBM_OK ||
+      (s = dalloc(ctx, (void **)&ctx->flags, padN)) != LBM_OK ||
+      (s = dalloc(ctx, (void **)&ctx->sid, 2 * padN)) != LBM_OK ||
+      (s = dalloc(ctx, (void **)&ctx->counts, 16 * sizeof(int))) != LBM_OK ||
+      (s = dalloc(ctx, (void **)&ctx->hist, sizeof(double) * kHistCap * kMaxSolids * 6)) != LBM_OK ||
+      (s = dalloc(ctx, (void **)&ctx->red2, 2 * sizeof(double))) != LBM_OK) {
+    lbm_destroy(ctx);
+    return s;
+  }
+  cudaMemsetAsync(ctx->flags, 0, padN, ctx->st);
+  cudaMemsetAsync(ctx->sid, 0, 2 * padN, ctx->st);
+  cudaMemsetAsync(ctx->counts, 0, 16 * sizeof(int), ctx->st);
+  cudaMemsetAsync(ctx->hist, 0, sizeof(double) * kHistCap * kMaxSolids * 6, ctx->st);
+  // rest state f = w as a pre-collision state, collided on first use
+  KArgs a = base_args(ctx);
+  a.dst = ctx->f[1];
+  a.omega = 1.0;  // rho
+  a.g[0] = a.g[1] = a.g[2] = 0;
+  sweep(ctx, OP_FILL_EQ, a);
+  ctx->cur = 0;
+  ctx->need_collide = true;
+  ctx->prev_local = true;
+  cudaError_t e = cudaStreamSynchronize(ctx->st);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    lbm_destroy(ctx);
+    return LBM_ERR_CUDA;
+  }
+  *out = ctx;
+  return LBM_OK;
+}
+
+void lbm_destroy(lbm_ctx *ctx) {
+  if (!ctx) return;
+  cudaStreamSynchronize(ctx->st);
+  if (ctx->aux) {
+    cudaStreamSynchronize(ctx->aux);
+    cudaStreamDestroy(ctx->aux);
+  }
+  if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
+  if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  for (void *p : ctx->allocs) cudaFree(p);
+  for (auto &p : ctx->pending) {
+    cudaEventDestroy(p.a);
+    cudaEventDestroy(p.b);
+  }
+  for (auto e : ctx->free_events) cudaEventDestroy(e);
+  delete ctx;
+}
+
+lbm_status lbm_add_solid(lbm_ctx *ctx, const lbm_solid_desc *solid, int *solid_id) {
+  if (!ctx || !solid) return LBM_ERR_ARG;
+  if ((int)ctx->solids.size() >= kMaxSolids) return fail(ctx, LBM_ERR_CAPACITY, "at most 8 solids");
+  if (solid->kind != LBM_SPHERE && solid->kind != LBM_CYLINDER_Z)
+    return fail(ctx, LBM_ERR_ARG, "unknown solid kind");
+  if (!(solid->radius > 0)) return fail(ctx, LBM_ERR_ARG, "radius must be positive");
+  SolidHost h;
+  h.d = *solid;
+  if (ctx->D == 2) {
+    h.d.centre[2] = 0;
+    h.d.velocity[2] = 0;
+    h.d.omega[0] = h.d.omega[1] = 0;
+  }
+  memcpy(h.c, h.d.centre, sizeof(h.c));
+  memcpy(h.cg, h.d.centre, sizeof(h.cg));
+  ctx->solids.push_back(h);
+  if (solid_id) *solid_id = (int)ctx->solids.size() - 1;
+  ctx->geom_dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int id, const double centre[3], const double vel[3],
+                                const double omega[3]) {
+  if (!ctx || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
+  SolidHost &h = ctx->solids[id];
+  bool moved = false;
+  for (int a = 0; a < 3; a++) {
+    if (centre && centre[a] != h.c[a]) moved = true;
+    if (centre) h.c[a] = h.d.centre[a] = centre[a];
+    if (vel) h.d.velocity[a] = vel[a];
+    if (omega) h.d.omega[a] = omega[a];
+  }
+  if (ctx->D == 2) {
+    h.c[2] = h.d.centre[2] = 0;
+    h.d.velocity[2] = 0;
+    h.d.omega[0] = h.d.omega[1] = 0;
+  }
+  // wall velocities are stored with the links: rebuild
+  (void)moved;
+  ctx->geom_dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme) {
+  if (!ctx || !scheme) return LBM_ERR_ARG;
+  if (scheme->scheme < LBM_SCHEME_NONE || scheme->scheme > LBM_IBM_DIRECT)
+    return fail(ctx, LBM_ERR_ARG, "unknown scheme");
+  if (scheme->ibm_iters < 0 || scheme->ibm_retraction < 0 || scheme->ibm_marker_density < 0)
+    return fail(ctx, LBM_ERR_ARG, "negative IBM parameter");
+  ctx->scheme = *scheme;
+  ctx->geom_dirty = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_init_equilibrium(lbm_ctx *ctx, double rho, const double u[3]) {
+  if (!ctx || !(rho > 0)) return LBM_ERR_ARG;
+  TRY(ensure_geometry(ctx));
+  KArgs a = base_args(ctx);
+  a.dst = ctx->f[1 - ctx->cur];
+  a.omega = rho;
+  for (int k = 0; k < 3; k++) a.g[k] = u ? u[k] : 0.0;
+  if (ctx->D == 2) a.g[2] = 0;
+  sweep(ctx, OP_FILL_EQ, a);
+  ctx->need_collide = true;
+  ctx->prev_local = true;
+  return LBM_OK;
+}
+
+lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *host_f, size_t n) {
+  if (!ctx || !host_f) return LBM_ERR_ARG;
+  const size_t need = (size_t)ctx->Q * ctx->N;
+  if (n < need) return fail(ctx, LBM_ERR_ARG, "input must hold Q * nodes doubles");
+  TRY(ensure_geometry(ctx));
+  TRY(qbuf_ensure(ctx, need));
+  CK(cudaMemcpyAsync(ctx->qbuf, host_f, need * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
+  KArgs a = base_args(ctx);
+  a.dst = ctx->f[1 - ctx->cur];
+  a.out_f = ctx->qbuf;
+  sweep(ctx, OP_FROM_DOUBLE, a);
+  ctx->need_collide = true;
+  ctx->prev_local = true;
+  CK(cudaStreamSynchronize(ctx->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_distributions(lbm_ctx *ctx, double *host_f, size_t n) {
+  return query(ctx, Q_F, host_f, n);
+}
+
+lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
+  if (!ctx || nsteps < 0) return LBM_ERR_ARG;
+  TRY(prepare(ctx));
+  for (int k = 0; k < nsteps; k++) TRY(step_once(ctx));
+  CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, int check_every, int max_steps,
+                             int *steps_done, double *residual) {
+  if (!ctx || check_every < 1 || max_steps < 0) return LBM_ERR_ARG;
+  TRY(prepare(ctx));
+  if (!ctx->u_now) {
+    TRY(dalloc(ctx, (void **)&ctx->u_now, sizeof(double) * ctx->D * ctx->N));
+    TRY(dalloc(ctx, (void **)&ctx->u_snap, sizeof(double) * ctx->D * ctx->N));
+  }
+  TRY(velocity_to(ctx, ctx->u_snap));
+  int done = 0;
+  double r = INFINITY;
+  lbm_status st = LBM_OK;
+  while (done < max_steps) {
+    const int k = std::min(check_every, max_steps - done);
+    for (int j = 0; j < k; j++) TRY(step_once(ctx));
+    done += k;
+    TRY(velocity_to(ctx, ctx->u_now));
+    launch_residual(ctx->u_now, ctx->u_snap, 0, ctx->flags, ctx->N, ctx->D, ctx->red2, ctx->st);
+    ctx->launches++;
+    double h[2];
+    CK(cudaMemcpyAsync(h, ctx->red2, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+    CK(cudaStreamSynchronize(ctx->st));
+    r = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+    ctx->last_residual = r;
+    if (!std::isfinite(r)) {
+      st = fail(ctx, LBM_ERR_DIVERGED, "non-finite residual");
+      break;
+    }
+    if (r < tol) break;
+    std::swap(ctx->u_now, ctx->u_snap);
+  }
+  if (steps_done) *steps_done = done;
+  if (residual) *residual = r;
+  return st;
+}
+
+lbm_status lbm_get_density(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_RHO, o, n); }
+lbm_status lbm_get_velocity(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_U, o, n); }
+lbm_status lbm_get_strain_rate(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_S, o, n); }
+lbm_status lbm_get_stress(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_STRESS, o, n); }
+
+lbm_status lbm_get_solid_mask(lbm_ctx *ctx, unsigned char *host_out, size_t n) {
+  if (!ctx || !host_out || n < (size_t)ctx->N) return LBM_ERR_ARG;
+  TRY(prepare(ctx));
+  std::vector<uint8_t> fl(ctx->N);
+  CK(cudaMemcpyAsync(fl.data(), ctx->flags, ctx->N, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (long long k = 0; k < ctx->N; k++) host_out[k] = (fl[k] & FL_SOLID) ? 1 : 0;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_force_torque(lbm_ctx *ctx, int id, double F[3], double T[3]) {
+  if (!ctx || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
+  TRY(prepare(ctx));
+  double h[6];
+  CK(cudaMemcpyAsync(h, force_slot(ctx, ctx->slot) + 6 * id, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaGetLastError());
+  for (int a = 0; a < 3; a++) {
+    if (F) F[a] = h[a];
+    if (T) T[a] = h[3 + a];
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_force_history(lbm_ctx *ctx, int id, double *host_out, size_t max_steps, size_t *n) {
+  if (!ctx || id < 0 || id >= (int)ctx->solids.size() || !n) return LBM_ERR_ARG;
+  TRY(prepare(ctx));
+  const long long have = std::min<long long>(ctx->records, (long long)max_steps);
+  std::vector<double> all((size_t)kHistCap * kMaxSolids * 6);
+  CK(cudaMemcpyAsync(all.data(), ctx->hist, all.size() * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (long long k = 0; k < have; k++) {
+    const int slot = (int)(((ctx->slot - (have - 1 - k)) % kHistCap + kHistCap) % kHistCap);
+    if (host_out) memcpy(host_out + 6 * k, &all[((size_t)slot * kMaxSolids + id) * 6], 6 * sizeof(double));
+  }
+  *n = (size_t)have;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_residual(lbm_ctx *ctx, double *r) {
+  if (!ctx || !r) return LBM_ERR_ARG;
+  *r = ctx->last_residual;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_solid_centre(lbm_ctx *ctx, int id, double c[3]) {
+  if (!ctx || id < 0 || id >= (int)ctx->solids.size() || !c) return LBM_ERR_ARG;
+  memcpy(c, ctx->solids[id].c, 3 * sizeof(double));
+  return LBM_OK;
+}
+
+lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
+  if (!ctx || !info) return LBM_ERR_ARG;
+  TRY(prepare(ctx));
+  int cnt[16];
+  TRY(read_counts(ctx, cnt));
+  std::vector<uint8_t> fl(ctx->N);
+  CK(cudaMemcpy(fl.data(), ctx->flags, ctx->N, cudaMemcpyDeviceToHost));
+  long long fluid = 0;
+  for (long long k = 0; k < ctx->N; k++) fluid += !(fl[k] & FL_SOLID);
+  memset(info, 0, sizeof(*info));
+  info->nodes = ctx->N;
+  info->fluid_nodes = fluid;
+  info->list_nodes = cnt[0];
+  info->cut_links = cnt[1];
+  info->markers = ctx->nmark;
+  info->steps = ctx->step;
+  info->kernel_launches = ctx->launches;
+  info->device_bytes = (int64_t)ctx->dev_bytes;
+  info->num_solids = (int)ctx->solids.size();
+  info->precision = ctx->d.precision;
+  return LBM_OK;
+}
+
+lbm_status lbm_device_field(lbm_ctx *ctx, int which, void **dptr, size_t *bytes,
+                            size_t *dir_stride) {
+  if (!ctx || !dptr) return LBM_ERR_ARG;
+  TRY(prepare(ctx));
+  if (dir_stride) *dir_stride = which == LBM_FIELD_F_POST ? (size_t)ctx->fs : 0;
+  if (which == LBM_FIELD_F_POST) {
+    *dptr = ctx->f[ctx->cur];
+    if (bytes) *bytes = (size_t)ctx->Q * ctx->fs * ctx->ssz;
+  } else if (which == LBM_FIELD_FLAGS) {
+    *dptr = ctx->flags;
+    if (bytes) *bytes = (size_t)ctx->N;
+  } else {
+    return LBM_ERR_ARG;
+  }
+  return LBM_OK;
+}
+
+// ---- checkpoint
+namespace {
+struct SaveHeader {
+  char magic[8];
+  int version, lattice, nx, ny, nz, precision, nsolids, prev_local, need_collide, scheme;
+  long long step, fs;
+  lbm_scheme_desc sch;
+};
+}  // namespace
+
+lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size) {
+  if (!ctx || !size) return LBM_ERR_ARG;
+  const size_t fb = (size_t)ctx->Q * ctx->fs * ctx->ssz;
+  const size_t total = sizeof(SaveHeader) + sizeof(SolidHost) * ctx->solids.size() + 2 * fb + ctx->N;
+  if (!host_buf) {
+    *size = total;
+    return LBM_OK;
+  }
+  if (*size < total) return fail(ctx, LBM_ERR_ARG, "checkpoint buffer too small");
+  TRY(ensure_geometry(ctx));
+  SaveHeader h;
+  memset(&h, 0, sizeof(h));
+  memcpy(h.magic, "LBMGB300", 8);
+  h.version = 1;
+  h.lattice = ctx->d.lattice;
+  h.nx = ctx->d.nx;
+  h.ny = ctx->d.ny;
+  h.nz = ctx->d.nz;
+  h.precision = ctx->d.precision;
+  h.nsolids = (int)ctx->solids.size();
+  h.prev_local = ctx->prev_local;
+  h.need_collide = ctx->need_collide;
+  h.step = ctx->step;
+  h.fs = ctx->fs;
+  h.sch = ctx->scheme;
+  char *p = (char *)host_buf;
+  memcpy(p, &h, sizeof(h));
+  p += sizeof(h);
+  memcpy(p, ctx->solids.data(), sizeof(SolidHost) * ctx->solids.size());
+  p += sizeof(SolidHost) * ctx->solids.size();
+  CK(cudaMemcpyAsync(p, ctx->f[ctx->cur], fb, cudaMemcpyDeviceToHost, ctx->st));
+  p += fb;
+  CK(cudaMemcpyAsync(p, ctx->f[1 - ctx->cur], fb, cudaMemcpyDeviceToHost, ctx->st));
+  p += fb;
+  CK(cudaMemcpyAsync(p, ctx->sid, ctx->N, cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  *size = total;
+  return LBM_OK;
+}
+
+lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size) {
+  if (!ctx || !host_buf || size < sizeof(SaveHeader)) return LBM_ERR_ARG;
+  SaveHeader h;
+  memcpy(&h, host_buf, sizeof(h));
+  if (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) return fail(ctx, LBM_ERR_ARG, "not a checkpoint");
+  if (h.lattice != ctx->d.lattice || h.nx != ctx->d.nx || h.ny != ctx->d.ny || h.nz != ctx->d.nz ||
+      h.precision != ctx->d.precision || h.nsolids < 0 || h.nsolids > kMaxSolids ||
+      h.fs != ctx->fs)
+    return fail(ctx, LBM_ERR_ARG, "checkpoint does not match this lattice");
+  const size_t fb = (size_t)ctx->Q * ctx->fs * ctx->ssz;
+  const size_t total = sizeof(SaveHeader) + sizeof(SolidHost) * h.nsolids + 2 * fb + ctx->N;
+  if (size < total) return fail(ctx, LBM_ERR_ARG, "checkpoint truncated");
+  const char *p = (const char *)host_buf + sizeof(h);
+  ctx->solids.assign((const SolidHost *)p, (const SolidHost *)p + h.nsolids);
+  p += sizeof(SolidHost) * h.nsolids;
+  ctx->scheme = h.sch;
+  ctx->cur = 0;
+  CK(cudaMemcpyAsync(ctx->f[0], p, fb, cudaMemcpyHostToDevice, ctx->st));
+  p += fb;
+  CK(cudaMemcpyAsync(ctx->f[1], p, fb, cudaMemcpyHostToDevice, ctx->st));
+  p += fb;
+  CK(cudaMemcpyAsync(ctx->sid, p, ctx->N, cudaMemcpyHostToDevice, ctx->st));
+  const size_t padN = ((ctx->N + 15) / 16) * 16;
+  CK(cudaMemcpyAsync(ctx->sid + padN, p, ctx->N, cudaMemcpyHostToDevice, ctx->st));
+  ctx->prev_local = h.prev_local;
+  ctx->need_collide = h.need_collide;
+  ctx->step = h.step;
+  ctx->geom_dirty = true;
+  ctx->restore_geometry = true;
+  TRY(rebuild_full(ctx));
+  if (!ctx->need_collide && ctx->scheme.scheme == LBM_IBM_DIRECT) {
+    // the IBM force of the current time is recomputed from the restored state
+    ctx->slot = (ctx->slot + 1) % kHistCap;
+    double *acc = force_slot(ctx, ctx->slot);
+    CK(cudaMemsetAsync(acc, 0, sizeof(double) * kMaxSolids * 6, ctx->st));
+    ibm_prepass(ctx, ctx->f[1], ctx->prev_local, acc, ctx->st);
+  }
+  CK(cudaStreamSynchronize(ctx->st));
+  return LBM_OK;
+}
+
+lbm_status lbm_set_timing(lbm_ctx *ctx, int enable) {
+  if (!ctx) return LBM_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
+  ctx->timing = enable != 0;
+  for (int k = 0; k < TK_COUNT; k++) {
+    ctx->tk_ms[k] = 0;
+    ctx->tk_launch[k] = ctx->tk_nodes[k] = 0;
+  }
+  return LBM_OK;
+}
+
+lbm_status lbm_get_kernel_time(lbm_ctx *ctx, int kernel, double *ms, int64_t *launches, int64_t *nodes) {
+  if (!ctx || kernel < 0 || kernel >= TK_COUNT) return LBM_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  resolve_timing(ctx);
+  if (ms) *ms = ctx->tk_ms[kernel];
+  if (launches) *launches = ctx->tk_launch[kernel];
+  if (nodes) *nodes = ctx->tk_nodes[kernel];
+  return LBM_OK;
+}
+
+lbm_status lbm_sync(lbm_ctx *ctx) {
+  if (!ctx) return LBM_ERR_ARG;
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaGetLastError());
+  int cnt[16];
+  TRY(read_counts(ctx, cnt));
+  if (cnt[3]) return fail(ctx, LBM_ERR_CAPACITY, "a boundary or refill list overflowed its capacity");
+  return LBM_OK;
+}
+
+}  // extern "C"

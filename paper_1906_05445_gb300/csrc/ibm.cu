@@ -1,0 +1,210 @@
+// ibm.cu -- direct-forcing immersed boundary (Sec. 2.1 of Peng, Ayala &
+// Wang): interpolation of the unforced velocity to the Lagrangian markers
+// with Peskin's 4-point delta function (Eqs. 5-6), the direct force
+// F = rho0 (U^d - U~)/dt (Eq. 7), and its spreading back to the lattice as a
+// body force (Eq. 8) with atomic accumulation.  One warp per marker: its 4^d
+// stencil points are split over the lanes and the interpolated velocity is
+// reduced with warp shuffles; the solid's force and torque are reduced per
+// block in FP64.
+#include "lbm_device.cuh"
+#include "lbm_internal.h"
+
+namespace lbm {
+
+namespace {
+
+// Peskin's 4-point kernel (Eq. 6)
+template <typename T>
+__device__ __forceinline__ T phi4(T r) {
+  const T a = fabs(r);
+  if (a >= (T)2) return (T)0;
+  if (a >= (T)1) return ((T)5 - (T)2 * a - sqrt((T)-7 + (T)12 * a - (T)4 * a * a)) / (T)8;
+  return ((T)3 - (T)2 * a + sqrt((T)1 + (T)4 * a - (T)4 * a * a)) / (T)8;
+}
+
+struct Marker {
+  double X[3];   // position
+  double r[3];   // X - centre (z dropped for cylinders and 2D)
+  int s;
+};
+
+__device__ __forceinline__ Marker marker(const IbmArgs &a, int m) {
+  Marker k;
+  k.s = a.msid[m];
+  const SolidDev &b = a.solids.s[k.s];
+  const double dx = a.dir[m], dy = a.dir[a.nmark + m], dz = a.dir[2 * a.nmark + m];
+  k.X[0] = b.c[0] + b.RL * dx;
+  k.X[1] = b.c[1] + b.RL * dy;
+  if (a.dim == 2)
+    k.X[2] = 0.0;
+  else if (b.kind == LBM_CYLINDER_Z)
+    k.X[2] = dz;  // plane of the ring
+  else
+    k.X[2] = b.c[2] + b.RL * dz;
+  k.r[0] = k.X[0] - b.c[0];
+  k.r[1] = k.X[1] - b.c[1];
+  k.r[2] = (a.dim == 2 || b.kind == LBM_CYLINDER_Z) ? 0.0 : k.X[2] - b.c[2];
+  return k;
+}
+
+// Stencil of a marker: the 4^d nodes from floor(X) - 1; the marker position
+// is FP64, the offsets of the stencil points from it are formed once and the
+// per-point arithmetic runs in the compute type.
+template <typename T> struct Stencil {
+  int ix, iy, iz;  // first stencil node (unwrapped)
+  T dx, dy, dz;    // first node - X
+};
+
+template <typename T>
+__device__ __forceinline__ Stencil<T> stencil_of(const IbmArgs &a, const Marker &k) {
+  Stencil<T> st;
+  const double bx = floor(k.X[0]) - 1.0, by = floor(k.X[1]) - 1.0;
+  const double bz = a.dim == 3 ? floor(k.X[2]) - 1.0 : 0.0;
+  st.ix = (int)bx;
+  st.iy = (int)by;
+  st.iz = (int)bz;
+  st.dx = (T)(bx - k.X[0]);
+  st.dy = (T)(by - k.X[1]);
+  st.dz = a.dim == 3 ? (T)(bz - k.X[2]) : (T)0;
+  return st;
+}
+
+template <typename T>
+__device__ __forceinline__ long long stencil_point(const IbmArgs &a, const Stencil<T> &st,
+                                                   int p, T &wgt) {
+  const int kx = p & 3, ky = (p >> 2) & 3, kz = p >> 4;
+  wgt = phi4<T>(st.dx + (T)kx) * phi4<T>(st.dy + (T)ky);
+  if (a.dim == 3) wgt *= phi4<T>(st.dz + (T)kz);
+  const int x = wrap(st.ix + kx, a.nx), y = wrap(st.iy + ky, a.ny);
+  const int z = a.dim == 3 ? wrap(st.iz + kz, a.nz) : 0;
+  return x + (long long)a.nx * (y + (long long)a.ny * z);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_interp(const IbmArgs a) {
+  const int m = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (m >= a.nmark) return;  // whole warp exits together
+  const Marker k = marker(a, m);
+  const Stencil<T> stc = stencil_of<T>(a, k);
+  const int npts = a.dim == 3 ? 64 : 16;
+  const T *ub = (const T *)a.u_band, *fi = (const T *)a.f_ibm;
+  T U[3] = {0, 0, 0};
+  for (int p = lane; p < npts; p += 32) {
+    T wgt;
+    const long long n = stencil_point<T>(a, stc, p, wgt);
+    for (int c = 0; c < a.dim; c++) {
+      T v = ub[c * a.N + n];
+      if (a.use_f) v += fi[c * a.N + n];  // u~ + f dt / rho0, rho0 = 1
+      U[c] += wgt * v;
+    }
+  }
+  for (int c = 0; c < 3; c++)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) U[c] += __shfl_down_sync(0xffffffffu, U[c], o);
+  if (lane == 0) {
+    const SolidDev &b = a.solids.s[k.s];
+    // desired velocity U + Omega x (X - c)
+    double Ud[3] = {b.U[0] + b.Om[1] * k.r[2] - b.Om[2] * k.r[1],
+                    b.U[1] + b.Om[2] * k.r[0] - b.Om[0] * k.r[2],
+                    b.U[2] + b.Om[0] * k.r[1] - b.Om[1] * k.r[0]};
+    for (int c = 0; c < 3; c++) {
+      const double F = c < a.dim ? (Ud[c] - (double)U[c]) : 0.0;  // rho0 (U^d - U~)/dt
+      a.Fm[c * a.nmark + m] = (a.first ? 0.0 : a.Fm[c * a.nmark + m]) + F;
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_spread(const IbmArgs a) {
+  __shared__ double part[4][6];
+  __shared__ int psid[4];
+  const int warp = threadIdx.x >> 5;
+  const int m = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool active = m < a.nmark;
+  if (lane == 0) psid[warp] = -1;
+  if (active) {
+    const Marker k = marker(a, m);
+    const Stencil<T> stc = stencil_of<T>(a, k);
+    const double dV = a.dV[m];
+    const double F[3] = {a.Fm[m], a.Fm[a.nmark + m], a.Fm[2 * a.nmark + m]};
+    const T FdV[3] = {(T)(F[0] * dV), (T)(F[1] * dV), (T)(F[2] * dV)};
+    const int npts = a.dim == 3 ? 64 : 16;
+    T *fi = (T *)a.f_ibm;
+    for (int p = lane; p < npts; p += 32) {
+      T wgt;
+      const long long n = stencil_point<T>(a, stc, p, wgt);
+      for (int c = 0; c < a.dim; c++) atomicAdd(fi + c * a.N + n, FdV[c] * wgt);
+    }
+    if (lane == 0 && a.reduce_force) {
+      // force on the solid: minus the marker forces (Sec. 3.1, Eq. B.7)
+      const double Fs[3] = {-F[0] * dV, -F[1] * dV, -F[2] * dV};
+      part[warp][0] = Fs[0];
+      part[warp][1] = Fs[1];
+      part[warp][2] = Fs[2];
+      part[warp][3] = k.r[1] * Fs[2] - k.r[2] * Fs[1];
+      part[warp][4] = k.r[2] * Fs[0] - k.r[0] * Fs[2];
+      part[warp][5] = k.r[0] * Fs[1] - k.r[1] * Fs[0];
+      psid[warp] = k.s;
+    }
+  }
+  if (!a.reduce_force) return;
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int c = threadIdx.x;
+    double acc = 0;
+    const int s0 = psid[0];
+    for (int wi = 0; wi < 4; wi++) {
+      if (psid[wi] < 0) continue;
+      if (psid[wi] == s0)
+        acc += part[wi][c];
+      else
+        atomicAdd(a.force_acc + 6 * psid[wi] + c, part[wi][c]);
+    }
+    if (s0 >= 0) atomicAdd(a.force_acc + 6 * s0 + c, acc);
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_zero_band(const KArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = a.counts[0];
+  if (cnt > a.list_cap) cnt = a.list_cap;
+  if (t >= cnt) return;
+  const long long n = a.list_node[t];
+  if (!(a.flags[n] & FL_BAND)) return;
+  T *fi = (T *)a.f_ibm;
+  for (int c = 0; c < 3; c++) fi[c * a.N + n] = (T)0;
+}
+
+}  // namespace
+
+void launch_ibm_interp(const IbmArgs &a, int precision, cudaStream_t st) {
+  if (a.nmark <= 0) return;
+  const unsigned grid = (unsigned)((32LL * a.nmark + 127) / 128);
+  if (precision == LBM_FP64)
+    k_interp<double><<<grid, 128, 0, st>>>(a);
+  else
+    k_interp<float><<<grid, 128, 0, st>>>(a);
+}
+
+void launch_ibm_spread(const IbmArgs &a, int precision, cudaStream_t st) {
+  if (a.nmark <= 0) return;
+  const unsigned grid = (unsigned)((32LL * a.nmark + 127) / 128);
+  if (precision == LBM_FP64)
+    k_spread<double><<<grid, 128, 0, st>>>(a);
+  else
+    k_spread<float><<<grid, 128, 0, st>>>(a);
+}
+
+void launch_zero_band(const KArgs &a, int precision, cudaStream_t st) {
+  if (a.list_cap <= 0) return;
+  const unsigned grid = (unsigned)((a.list_cap + 127) / 128);
+  if (precision == LBM_FP64)
+    k_zero_band<double><<<grid, 128, 0, st>>>(a);
+  else
+    k_zero_band<float><<<grid, 128, 0, st>>>(a);
+}
+
+}  // namespace lbm

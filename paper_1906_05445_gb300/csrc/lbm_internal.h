@@ -1,0 +1,159 @@
+// lbm_internal.h -- structures shared by the host API and the kernel
+// translation units of the library (not part of the public ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/lbm.h"
+
+namespace lbm {
+
+constexpr int kMaxSolids = 8;
+
+// Solid state passed to kernels by value (FP64 geometry).
+struct SolidDev {
+  int kind, fluid_inside;
+  double c[3], R, U[3], Om[3];
+  double RL;            // marker radius (IBM)
+};
+
+struct SolidsDev {
+  int n;
+  SolidDev s[kMaxSolids];
+};
+
+// Cut-link records (SoA, type T = compute type): coefficients c0..c4 of the
+// bounce-back rule, the moving-wall term mw = c5 * 6 w_i (e_i.u_w), the wall
+// velocity, the lever arm x_w - Y_c, and the solid id.
+struct LinkArrays {
+  void *c[5];
+  void *mw;
+  void *uw[3];
+  void *arm[3];
+  uint8_t *sid;
+};
+
+// Arguments of every sweep-like kernel (passed by value).
+struct KArgs {
+  // lattice
+  int nx, ny, nz;
+  long long N;
+  long long fs;     // stride between direction arrays (elements, >= N)
+  const void *src;  // distributions read
+  void *dst;        // distributions written
+  const uint8_t *flags;
+  // collision constants in FP64 (FP64 kernels, queries) and the same
+  // constants rounded once to FP32 on the host (FP32 kernels never touch
+  // FP64 values per node: GB300's FP64 rate is a small fraction of FP32)
+  double omega, ds[19], s_bulk, nu;
+  double g[3];
+  double inv_scale;  // storage scale^-1 (1 except FP16 storage)
+  float omega_f, ds_f[19], g_f[3], inv_scale_f;
+  // boundary-node list
+  const int *list_node;
+  const uint32_t *list_mask;
+  const int *list_link;
+  const int *counts;  // device counters: [0] list nodes, [1] links, [2] refill
+  int list_cap;
+  const double *list_cst;  // [6][list_cap] state-independent part of Eq. 17
+  LinkArrays links;
+  // IBM dense fields (type T, [3][N]) and flags
+  const void *f_ibm;
+  void *u_band;
+  // momentum exchange accumulators: [solid][6] doubles (F, T)
+  double *force_acc;
+  int nsolids;
+  // refill
+  const int *refill_node;
+  const uint8_t *refill_sid;
+  int refill_cap;
+  SolidsDev solids;
+  const uint8_t *sid;
+  // query outputs (FP64); unused pointers are null
+  double *out_rho, *out_u, *out_S, *out_stress, *out_f;
+  int local_gather;  // 1: read src locally (pre-collision state), 0: pull
+  int bulk_block;    // threads per block of the bulk sweep (multiple of 32)
+};
+
+// kernel families timed by lbm_set_timing
+enum TimedKernel { TK_BULK = 0, TK_LIST = 1, TK_IBM = 2, TK_GEOM = 3, TK_COUNT = 4 };
+
+// Operations of the precision-specific translation units.
+enum SweepOp {
+  OP_BULK_SWEEP,   // pull + collide + store, plain fluid nodes
+  OP_LIST_SWEEP,   // pull + bounce-back + collide + store + Eq. 17
+  OP_BULK_QUERY,   // pull, fields to FP64 outputs
+  OP_LIST_QUERY,
+  OP_LOCAL_INIT,   // local read of a pre-collision state + collide + store
+  OP_LOCAL_QUERY,  // local read of a pre-collision state, fields
+  OP_REFILL,       // equilibrium refill of uncovered nodes (+ collide)
+  OP_BAND_VEL,     // IBM: unforced velocity at band nodes, zero the IBM force
+  OP_FROM_DOUBLE,  // convert a full-f FP64 array (out_f) into deviations (dst)
+  OP_FILL_EQ       // fill dst with equilibrium deviations (g[] = u, omega = rho)
+};
+
+// Launch one operation for the given lattice/collision/precision.  grid
+// sizes are chosen by the launcher; counts on the device bound list work.
+void launch_sweep(SweepOp op, int lattice, int collision, int precision,
+                  const KArgs &a, cudaStream_t st);
+
+// geometry (geometry.cu)
+struct GeomBox {
+  int x0, y0, z0, bx, by, bz;
+};
+struct GeomArgs {
+  int nx, ny, nz, lattice, scheme, force_all;
+  long long N;
+  SolidsDev solids;
+  uint8_t *flags;
+  uint8_t *sid;
+  int *counts;  // [0] list nodes, [1] links, [2] refill nodes, [3] overflow
+  int *list_node;
+  uint32_t *list_mask;
+  int *list_link;
+  double *list_cst;
+  int list_cap, link_cap;
+  LinkArrays links;
+  int *refill_node;
+  uint8_t *refill_sid;
+  int refill_cap;
+  int track_new;  // mark nodes uncovered since the previous geometry
+  double band_w;  // IBM band half width
+  GeomBox box[kMaxSolids];
+  int nbox;
+  long long box_offset[kMaxSolids + 1];
+};
+void launch_geometry(const GeomArgs &g, int precision, cudaStream_t st);
+void launch_clear_new(uint8_t *flags, const int *counts, const int *node, int cap,
+                      cudaStream_t st);
+
+// IBM (ibm.cu)
+struct IbmArgs {
+  int nx, ny, nz, dim, nmark;
+  long long N;
+  const double *dir;  // [3][nmark]
+  const double *dV;   // [nmark]
+  const uint8_t *msid;
+  double *Fm;         // [3][nmark] accumulated marker force density
+  SolidsDev solids;
+  void *u_band;       // T [3][N]
+  void *f_ibm;        // T [3][N]
+  int use_f;          // interpolate u_band + f_ibm (iterations > 1)
+  int first;          // first iteration: Fm = 0 before adding
+  double *force_acc;  // [solid][6]
+  int reduce_force;   // accumulate -sum F dV and the torque
+};
+void launch_ibm_interp(const IbmArgs &a, int precision, cudaStream_t st);
+void launch_ibm_spread(const IbmArgs &a, int precision, cudaStream_t st);
+void launch_zero_band(const KArgs &a, int precision, cudaStream_t st);
+
+// reductions (reduce.cu)
+void launch_residual(const double *u, const double *usnap, long long n,
+                     const uint8_t *flags, long long N, int d, double *out2,
+                     cudaStream_t st);
+
+}  // namespace lbm

@@ -1,0 +1,9 @@
+// sweep_f32.cu -- sweep kernels with float storage and float arithmetic.
+#include "sweep_impl.cuh"
+
+namespace lbm {
+void launch_sweep_f32(SweepOp op, int lattice, int collision, const KArgs &a,
+                        cudaStream_t st) {
+  launch_precision<float, float>(op, lattice, collision, a, st);
+}
+}  // namespace lbm

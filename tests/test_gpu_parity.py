@@ -1,0 +1,263 @@
+"""GPU parity: the CUDA library (through the C ABI) against the FP64 CPU
+oracle on the same seeded inputs, element by element.
+
+Tolerances: the FP64 build must match to 1e-12 relative L2 on velocity; the
+FP32 build to 1e-5 relative L2 on velocity and 1e-4 on the drag.  The oracle
+keeps full populations, so its own absolute rounding is about ulp(1/3) per
+value; the FP64 cases therefore run at flow speeds of order 1e-2 (those of
+the paper's runs), where that floor is far below 1e-12 of the velocity.  Sizes span
+several thread blocks and leave ragged tails (nx not a multiple of the block
+width), and the edge cases cover spheres across the periodic wrap, tiny
+lattices and every fallback of the bounce-back rules."""
+import numpy as np
+import pytest
+
+from paper_1906_05445_gb300 import workloads as W
+
+from .parity import compare, make_gpu, make_oracle, random_populations, rel_l2
+
+pytestmark = pytest.mark.gpu
+
+FP64_TOL = 1e-12
+FP32_U_TOL = 1e-5
+FP32_F_TOL = 1e-4
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _gpu():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import oracle
+    oracle.build()
+    from paper_1906_05445_gb300 import build
+    build.build()
+
+
+def periodic(lat, coll, prec, nx, ny, nz, tau=0.7, g=(1e-5, -2e-5, 3e-5)):
+    return W.Problem("periodic", lat, nx, ny, nz, tau, coll, prec, g, [], W.NONE, 0)
+
+
+@pytest.mark.parametrize("lat,shape", [(W.D2Q9, (150, 37, 1)), (W.D3Q19, (37, 23, 19))])
+@pytest.mark.parametrize("coll", [W.BGK, W.MRT])
+def test_periodic_sweep_fp64_from_random_state(lat, shape, coll):
+    """Eq. 1 / Eq. 3 with Guo forcing on a periodic box from random
+    populations: every population after 7 steps."""
+    p = periodic(lat, coll, W.FP64, *shape)
+    f0 = random_populations(p, seed=3)
+    g, o = make_gpu(p), make_oracle(p)
+    g.set_f(f0)
+    o.set_f(f0)
+    compare(g, o, FP64_TOL, what=("u", "rho", "f"))    # initial state round trip
+    g.step(7)
+    o.step(7)
+    compare(g, o, FP64_TOL, what=("u", "rho", "f"))
+
+
+@pytest.mark.parametrize("lat,shape", [(W.D2Q9, (150, 37, 1)), (W.D3Q19, (37, 23, 19))])
+@pytest.mark.parametrize("coll", [W.BGK, W.MRT])
+def test_periodic_sweep_fp32(lat, shape, coll):
+    p = periodic(lat, coll, W.FP32, *shape)
+    f0 = random_populations(p, seed=4, amplitude=0.005)
+    g, o = make_gpu(p), make_oracle(p)
+    g.set_f(f0)
+    o.set_f(f0)
+    g.step(20)
+    o.step(20)
+    compare(g, o, FP32_U_TOL, what=("u", "rho"), rho_tol=1e-7)
+
+
+@pytest.mark.parametrize("scheme", [W.BB, W.BOUZIDI_LIN, W.BOUZIDI_QUAD, W.YU_LIN, W.YU_QUAD])
+def test_fixed_sphere_ibb_fp64(scheme):
+    """Sec. 2.2 rules and Eq. 17 on a fixed sphere (MRT, body force), from a
+    random state so that every link carries a distinct value."""
+    p = W.fixed_sphere(29, 6.3, seed=11, tau=0.65, g=2e-4, scheme=scheme,
+                       precision=W.FP64, collision=W.MRT, steps=25)
+    g, o = make_gpu(p), make_oracle(p)
+    f0 = random_populations(p, seed=5, amplitude=0.03)
+    g.set_f(f0)
+    o.set_f(f0)
+    g.step(p.steps)
+    o.step(p.steps)
+    r = compare(g, o, FP64_TOL, tol_F=1e-11, what=("u", "rho", "f"))
+    assert g.info().cut_links == sum(o.link_stats()) // p.steps
+
+
+def test_couette_c1_fp64():
+    """The 64x64 D2Q9 circular Couette configuration for its full 5000
+    steps (two cylinders, rotating inner wall, linear Bouzidi)."""
+    p = W.couette_2d()
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    r = compare(g, o, FP64_TOL, tol_F=1e-9, sids=(0, 1), what=("u", "rho"))
+    for sid in (0, 1):
+        Tg = g.force_torque(sid)[1][2]
+        To = o.force_torque(sid)[1][2]
+        assert abs(Tg - To) <= FP64_TOL * abs(To)
+    # strain rate and stress queries
+    assert rel_l2(g.strain_rate(), o.strain_rate(), o.solid_mask()) < 1e-10
+
+
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.YU_LIN])
+def test_couette_fp64_other_rules(scheme):
+    p = W.couette_2d(48, 7.5, 21.0, (24.4, 23.7), 0.01, 0.9, scheme, 400)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-9, sids=(0, 1))
+
+
+@pytest.mark.parametrize("iters,rd", [(1, 0.0), (3, 0.3)])
+def test_fixed_sphere_ibm_fp64(iters, rd):
+    """Direct-forcing IBM (Eqs. 5-10): band velocity, interpolation with
+    Peskin's kernel, force, spreading, forced sweep; force on the solid."""
+    p = W.fixed_sphere(26, 6.1, seed=13, tau=0.7, g=2e-4, scheme=W.IBM,
+                       precision=W.FP64, collision=W.MRT, steps=20,
+                       ibm_iters=iters, retraction=rd)
+    g, o = make_gpu(p), make_oracle(p)
+    f0 = random_populations(p, seed=6, amplitude=0.03)
+    g.set_f(f0)
+    o.set_f(f0)
+    compare(g, o, FP64_TOL, tol_F=1e-10, what=("u", "rho"))   # forces at t0
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10, what=("u", "rho", "f"))
+    assert g.info().markers == o.num_markers(0)
+
+
+def test_couette_ibm_fp64():
+    p = W.couette_2d(48, 7.5, 21.0, (24.4, 23.7), 0.01, 0.9, W.IBM, 300).with_(
+        ibm_iters=2, retraction=0.3)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10, sids=(0, 1))
+
+
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.YU_QUAD, W.BB])
+def test_moving_sphere_ibb_refill_fp64(scheme):
+    """A sphere translating across grid lines: geometry rebuilt every step,
+    uncovered nodes refilled, moving-wall term in the bounce-back."""
+    p = W.translating_sphere(40, 24, 22, 5.2, seed=17, u=0.07, tau=0.7,
+                             scheme=scheme, precision=W.FP64, steps=40)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10, what=("u", "rho"))
+    assert np.allclose(g.solid_centre(0), o.solid_centre(0), rtol=0, atol=1e-12)
+    hist = g.force_history(0)
+    assert hist.shape[0] >= p.steps
+
+
+def test_moving_sphere_ibm_fp64():
+    p = W.translating_sphere(40, 24, 22, 5.2, seed=19, u=0.07, tau=0.7,
+                             scheme=W.IBM, precision=W.FP64, steps=30)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10, what=("u", "rho"))
+
+
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])
+def test_sphere_fp32(scheme):
+    """FP32 storage of f - w_i and FP32 arithmetic against the FP64 oracle."""
+    p = W.fixed_sphere(48, 8.0, seed=1906, tau=0.6, g=1e-6, scheme=scheme,
+                       precision=W.FP32, collision=W.MRT, steps=300)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP32_U_TOL, tol_F=FP32_F_TOL)
+
+
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])
+def test_full_size_sphere_fp32(scheme):
+    """The 128^3 D3Q19 MRT sphere (R = 12, seeded offset) in the launch
+    configuration of the benchmark, a few steps from rest against the
+    oracle on every node."""
+    p = W.fixed_sphere(128, 12.0, seed=1906, scheme=scheme, precision=W.FP32,
+                       g=3.4e-5, steps=3)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP32_U_TOL, tol_F=FP32_F_TOL)
+
+
+def test_sphere_across_periodic_wrap_and_tiny_lattices():
+    # sphere centred near a corner: its solid nodes wrap through all faces
+    p = W.Problem("wrap", W.D3Q19, 17, 15, 13, 0.8, W.MRT, W.FP64, (3e-4, 0, 0),
+                  [W.Solid(W.SPHERE, (0.3, 14.6, 12.8), 4.4)], W.BOUZIDI_QUAD, 15)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10)
+    # a 4x4x4 box whose sphere leaves interpolation neighbours missing
+    p = W.Problem("tiny", W.D3Q19, 4, 4, 4, 0.8, W.BGK, W.FP64, (3e-4, 0, 0),
+                  [W.Solid(W.SPHERE, (1.7, 1.4, 2.1), 0.9)], W.YU_QUAD, 10)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10)
+    # a single periodic node
+    p = periodic(W.D3Q19, W.MRT, W.FP64, 1, 1, 1)
+    g, o = make_gpu(p), make_oracle(p)
+    f0 = random_populations(p, seed=9)
+    g.set_f(f0)
+    o.set_f(f0)
+    g.step(3)
+    o.step(3)
+    compare(g, o, FP64_TOL, what=("f",))
+
+
+def test_fallback_rules_and_link_counts():
+    """Two close spheres leave links whose x_ff / x_fff are solid: the
+    rules fall back to linear and to Eq. 9 exactly as in the oracle."""
+    p = W.Problem("gap", W.D3Q19, 30, 20, 20, 0.75, W.MRT, W.FP64, (3e-4, 0, 0),
+                  [W.Solid(W.SPHERE, (9.3, 10.2, 9.7), 5.1),
+                   W.Solid(W.SPHERE, (20.6, 9.9, 10.3), 5.2)], W.BOUZIDI_QUAD, 12)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10, sids=(0, 1))
+    st = o.link_stats()
+    assert st[W.BOUZIDI_LIN] > 0 and st[W.BB] > 0
+
+
+def test_run_to_steady_matches_oracle():
+    p = W.couette_2d(32, 5.0, 14.0, (16.3, 15.8), 0.01, 0.8, W.BOUZIDI_LIN)
+    g, o = make_gpu(p), make_oracle(p)
+    done_g, r_g = g.run_to_steady(1e-7, 100, 20000)
+    done_o, r_o = o.run_to_steady(1e-7, 20000, 100)
+    assert done_g == done_o
+    assert abs(r_g - r_o) <= 1e-6 * r_o
+    compare(g, o, FP64_TOL)
+
+
+def test_checkpoint_split_run_equals_straight_run():
+    p = W.translating_sphere(36, 20, 20, 4.3, seed=23, u=0.06, tau=0.7,
+                             scheme=W.BOUZIDI_QUAD, precision=W.FP64, steps=30)
+    a = make_gpu(p)
+    a.step(30)
+    b = make_gpu(p)
+    b.step(15)
+    blob = b.save()
+    c = make_gpu(p)
+    c.load(blob)
+    c.step(15)
+    assert rel_l2(c.velocity(), a.velocity()) < 1e-14
+    # forces are FP64 sums whose atomic order varies from run to run
+    assert np.allclose(c.force_torque(0)[0], a.force_torque(0)[0], rtol=1e-12, atol=1e-13)
+
+
+@pytest.mark.parametrize("prec", [W.FP32_BF16, W.FP32_FP16])
+def test_low_precision_storage_tracks_oracle(prec):
+    """BF16 / FP16 storage with FP32 arithmetic: the error against the FP64
+    oracle is reported and bounded (acceptance against the discretisation
+    error is measured by the benchmark)."""
+    p = W.fixed_sphere(40, 7.0, seed=29, tau=0.7, g=5e-6, scheme=W.BOUZIDI_QUAD,
+                       precision=prec, collision=W.MRT, steps=200)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    err = rel_l2(g.velocity(), o.velocity(), o.solid_mask())
+    assert err < (5e-2 if prec == W.FP32_BF16 else 5e-3), err

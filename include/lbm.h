@@ -225,6 +225,31 @@ lbm_status lbm_set_timing(lbm_ctx *ctx, int enable);
 lbm_status lbm_get_kernel_time(lbm_ctx *ctx, int kernel, double *total_ms,
                                int64_t *launches, int64_t *node_updates);
 
+/* Velocity query that allocates no device memory.  The paper has no
+ * counterpart: this is an operational variant of lbm_get_velocity for
+ * callers that must not allocate GPU memory once they are set up -- for
+ * example a host application that has handed the remaining device memory to
+ * its own pool allocator, or a time-critical loop where a cudaMalloc would
+ * synchronise the device.  lbm_get_velocity allocates its FP64 staging
+ * buffer the first time it is called; this variant stages the field through
+ * a fixed array compiled into the library instead: 2^20 doubles (8 MiB),
+ * held on every GPU that loads the library until the process exits.
+ *  - Output: as lbm_get_velocity, [d][z][y][x] FP64 into host_out (n >= d *
+ *    nodes); 0 at solid nodes.
+ *  - d * nodes above 2^20 is rejected with LBM_ERR_CAPACITY.
+ *  - The context must not hold a pending geometry change (rebuilding it
+ *    would allocate): call lbm_step or lbm_sync after add_solid / set_scheme
+ *    / set_solid_motion, otherwise LBM_ERR_STATE.  The context's device must
+ *    be current (LBM_ERR_STATE otherwise).
+ *  - The first call on a device looks up the array's device address once
+ *    (cudaGetSymbolAddress); make that first call before any stream capture.
+ *  - All calls, from every context, share the one array and it keeps the
+ *    previous call's contents (the call clears the part it uses).  Calls
+ *    whose work overlaps on the GPU (contexts on different streams, or
+ *    several host threads) race on it: serialise them.
+ *  - Synchronous, like the other queries. */
+lbm_status lbm_get_velocity_noalloc(lbm_ctx *ctx, double *host_out, size_t n);
+
 lbm_status lbm_sync(lbm_ctx *ctx);
 const char *lbm_last_error(const lbm_ctx *ctx);
 /* Library version string. */

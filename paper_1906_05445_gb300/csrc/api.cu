@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <mutex>
 #include <string>
 #include <vector>
 
@@ -1207,6 +1208,64 @@ lbm_status lbm_get_kernel_time(lbm_ctx *ctx, int kernel, double *ms, int64_t *la
   if (ms) *ms = ctx->tk_ms[kernel];
   if (launches) *launches = ctx->tk_launch[kernel];
   if (nodes) *nodes = ctx->tk_nodes[kernel];
+  return LBM_OK;
+}
+
+// ---- velocity query without device allocation
+//
+// Staging buffer compiled into the library: 2^20 doubles (8 MiB) on every
+// device that loads it, shared by all contexts and all calls.
+static constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+
+// Device address of the staging buffer, looked up once per device (host code
+// may not take the address of a __device__ variable directly).
+static constexpr int kNoAllocMaxDevices = 64;
+static double *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+lbm_status lbm_get_velocity_noalloc(lbm_ctx *ctx, double *host_out, size_t n) {
+  if (!ctx || !host_out) return LBM_ERR_ARG;
+  const size_t need = (size_t)ctx->D * (size_t)ctx->N;
+  if (n < need) return fail(ctx, LBM_ERR_ARG, "output buffer too small: need " + std::to_string(need));
+  if (need > kNoAllocScratchDoubles)
+    return fail(ctx, LBM_ERR_CAPACITY,
+                "lbm_get_velocity_noalloc stages at most " + std::to_string(kNoAllocScratchDoubles) +
+                    " doubles (d * nodes); this lattice needs " + std::to_string(need) +
+                    ": use lbm_get_velocity");
+  // rebuilding the geometry would allocate: the caller must have stepped or
+  // queried the context since its last change
+  if (ctx->geom_dirty)
+    return fail(ctx, LBM_ERR_STATE,
+                "geometry changed since the last step: call lbm_step or lbm_sync first");
+  int dev = -1;
+  CK(cudaGetDevice(&dev));
+  if (dev != ctx->device)
+    return fail(ctx, LBM_ERR_STATE, "make the context's device current before this call");
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(ctx, LBM_ERR_UNSUPPORTED, "device index too large");
+  double *scratch = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void *p = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        return fail(ctx, LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
+      }
+      g_noalloc_addr[dev] = (double *)p;
+    }
+    scratch = g_noalloc_addr[dev];
+  }
+  if (ctx->need_collide) TRY(init_collide(ctx));  // kernels only, no allocation
+  // the array keeps the previous call's values: solid nodes must read 0
+  CK(cudaMemsetAsync(scratch, 0, need * sizeof(double), ctx->st));
+  KArgs a = base_args(ctx);
+  a.out_u = scratch;
+  run_query(ctx, a);
+  CK(cudaMemcpyAsync(host_out, scratch, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  CK(cudaGetLastError());
   return LBM_OK;
 }
 

@@ -92,6 +92,7 @@ def _load():
         "lbm_load": (st, [vp, vp, sz]),
         "lbm_set_timing": (st, [vp, i]),
         "lbm_get_kernel_time": (st, [vp, i, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
+        "lbm_get_velocity_noalloc": (st, [vp, dp, sz]),
         "lbm_sync": (st, [vp]),
         "lbm_last_error": (C.c_char_p, [vp]),
         "lbm_version": (C.c_char_p, []),
@@ -112,7 +113,8 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
     "lbm_get_residual", "lbm_get_solid_centre", "lbm_get_info",
     "lbm_device_field", "lbm_save", "lbm_load", "lbm_set_timing",
-    "lbm_get_kernel_time", "lbm_sync", "lbm_last_error", "lbm_version")})
+    "lbm_get_kernel_time", "lbm_get_velocity_noalloc", "lbm_sync", "lbm_last_error",
+    "lbm_version")})
 
 
 class LbmError(RuntimeError):

@@ -1,0 +1,80 @@
+"""Host-side logic of bench.py, on CPU: the whole-job aggregation over
+ranks (max-over-ranks time, weak scaling) with a 2-rank gloo group, the
+nvidia-smi sample parser and the traffic/roofline bookkeeping."""
+import os
+import socket
+
+import pytest
+import torch.multiprocessing as mp
+
+import bench
+
+
+def _free_port():
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        return s.getsockname()[1]
+
+
+def _rank(rank, world, port, secs, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    bench.barrier(world)
+    m = bench.reduce_max(secs[rank], world, None)
+    out[rank] = bench.aggregate(1_000_000, m, world)
+    dist.destroy_process_group()
+
+
+def test_two_rank_aggregation_uses_slowest_rank():
+    port = _free_port()
+    secs = [0.5, 2.0]
+    out = mp.Manager().dict()
+    mp.start_processes(_rank, args=(2, port, secs, out), nprocs=2, join=True,
+                       start_method="spawn")
+    # value = node updates of all ranks / slowest rank's time
+    assert out[0] == out[1] == pytest.approx(2 * 1_000_000 / 2.0 / 1e6)
+
+
+def test_single_rank_aggregate():
+    assert bench.aggregate(4_000_000, 0.5, 1) == pytest.approx(8.0)
+
+
+def test_clock_parser():
+    c = bench.ClockSampler(0)
+    c.proc = None
+    c.lines = ["0, 2070, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+               "0, 1980, 2070, 1300.0, 0x4, Not Active, Not Active, Not Active, Active"]
+
+    class P:  # stands in for the finished nvidia-smi process
+        def terminate(self):
+            pass
+
+        def wait(self, timeout=None):
+            return 0
+
+    class T:
+        def join(self, timeout=None):
+            pass
+
+    c.proc, c.thread = P(), T()
+    r = c.stop()
+    assert r["sm_max_mhz"] == 2070 and r["reasons"] == ["sw_power_cap"]
+    assert r["sm_mhz"] == pytest.approx(2025)
+
+
+def test_traffic_only_for_current_sweep_source():
+    t = bench.recorded_traffic()
+    txt = open(os.path.join(bench.ROOT, bench.TRAFFIC_FILE)).read()
+    if bench.sweep_source_hash() in txt:
+        assert t and t > 1e8
+    else:
+        assert t is None
+
+
+def test_workload_is_the_128_cube_sphere():
+    p = bench.workload()
+    assert len(p) == 2 and p[0].nx == p[0].ny == p[0].nz == 128
+    assert p[0].solids[0].radius == 12.0 and p[0].collision == 1
+    cfg = bench.workload_config(p, p[0].precision)
+    assert "128^3" in cfg["workload"] and cfg["lattices"] == 2

@@ -16,6 +16,11 @@ SM clocks sampled during the timed region and the kernel launch count.
 
 Under torchrun each rank runs its own replica of the workload (independent
 lattices, no data-path collective): value = all node updates / max time.
+
+At N = 1 the line also carries "batch" (a grid-convergence batch of sphere
+lattices run to steady state in one graph-captured batch vs one at a time)
+and "serve" (a Poisson stream of solves under continuous batching vs one at
+a time, with p50/p99 latency); --no-batch skips them.
 """
 from __future__ import annotations
 
@@ -240,6 +245,69 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------------------ batch / serve
+BATCH_CFG = dict(count=8, r_min=3.0, r_max=8.0, tau=0.8, re_p=2.0, tol=1e-6,
+                 check_every=200, max_steps=100000)
+SERVE_CFG = dict(count=24, seed=11, rate_hz=40.0, min_2d=48, max_2d=160, min_3d=24,
+                 max_3d=48, tau_range=(0.7, 1.0), tol=1e-5, check_every=200)
+
+
+def run_batch_leg(lbm, stream):
+    """Grid-convergence batch (spheres R = 3..8, cube edge 8R, alternating
+    quadratic Bouzidi / IBM, FP32), every lattice to its own residual < tol:
+    one batch (graph-captured, autotuned) vs the same solves one at a time."""
+    c = BATCH_CFG
+    ps = W.convergence_batch(c["count"], tau=c["tau"], re_p=c["re_p"], r_min=c["r_min"],
+                             r_max=c["r_max"])
+    t0 = time.perf_counter()
+    seq_steps = []
+    for p in ps:
+        lt = lbm.Lattice.from_problem(p, stream=stream)
+        lt.init_equilibrium()
+        seq_steps.append(lt.run_to_steady(c["tol"], c["check_every"], c["max_steps"])[0])
+        lt.close()
+    t_seq = time.perf_counter() - t0
+    lats = [lbm.Lattice.from_problem(p, stream=stream) for p in ps]
+    for lt in lats:
+        lt.init_equilibrium()
+    t0 = time.perf_counter()
+    b = lbm.Batch(lats, stream=stream, autotune=True)
+    steps, res = b.run_to_steady(c["tol"], c["check_every"], c["max_steps"])
+    t_batch = time.perf_counter() - t0
+    blocks = [list(b.info(i)[:2]) for i in range(len(ps))]
+    b.close()
+    for lt in lats:
+        lt.close()
+    return {"metric": "batched solves/s", "value": len(ps) / t_batch, "unit": "solves/s",
+            "sequential_value": len(ps) / t_seq, "speedup": t_seq / t_batch,
+            "batch_s": t_batch, "sequential_s": t_seq,
+            "steps": [int(x) for x in steps], "sequential_steps": [int(x) for x in seq_steps],
+            "converged": bool(all(r < c["tol"] for r in res)),
+            "blocks_bulk_list": blocks,
+            "stated_error": f"steady-state residual < {c['tol']} (every {c['check_every']} steps); "
+                            "FP32 within 1e-5 (velocity) / 1e-4 (drag) of the FP64 oracle",
+            "config": {"lattices": len(ps), "radii": [p.solids[0].radius for p in ps],
+                       "edges": [p.nx for p in ps], "tau": c["tau"], "re_p": c["re_p"],
+                       "schemes": "even: bouzidi_quadratic, odd: ibm", "dtype": "f32"}}
+
+
+def run_serve_leg(stream):
+    """Poisson stream of mixed 2D Couette / 3D sphere solves (FP32, random
+    tau and scheme): continuous batching vs one solve at a time."""
+    from paper_1906_05445_gb300 import serve
+    c = SERVE_CFG
+    reqs = W.request_stream(count=c["count"], seed=c["seed"], rate_hz=c["rate_hz"],
+                            min_2d=c["min_2d"], max_2d=c["max_2d"], min_3d=c["min_3d"],
+                            max_3d=c["max_3d"], tau_range=c["tau_range"])
+    a = serve.summarize(serve.serve_batched(reqs, c["tol"], c["check_every"], stream=stream))
+    s = serve.summarize(serve.serve_sequential(reqs, c["tol"], c["check_every"], stream=stream))
+    return {"metric": "served solves/s", "value": a["solves_per_s"], "unit": "solves/s",
+            "p50_s": a["p50_s"], "p99_s": a["p99_s"],
+            "sequential": {"value": s["solves_per_s"], "p50_s": s["p50_s"], "p99_s": s["p99_s"]},
+            "stated_error": f"each solve to steady-state residual < {c['tol']}",
+            "config": {k: v for k, v in c.items()}}
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args, rank, world, local):
     import torch
@@ -335,6 +403,10 @@ def run_ours(args, rank, world, local):
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(problems, steps_each=1)
+    batch = serve_leg = None
+    if rank == 0 and world == 1 and not args.no_batch:
+        batch = run_batch_leg(lbm, stream.cuda_stream)
+        serve_leg = run_serve_leg(stream.cuda_stream)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -351,7 +423,8 @@ def run_ours(args, rank, world, local):
                              "launch_ms": ms / max(nl, 1), "peak_kind": peak_kind + " hbm_gbs"},
                 "kernel_ms_per_step": kt,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
-                "gpu_launches": int(launches) * world}
+                "gpu_launches": int(launches) * world,
+                "batch": batch, "serve": serve_leg}
         print(json.dumps(line), flush=True)
     for lt in lats:
         lt.close()
@@ -368,6 +441,8 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--no-batch", action="store_true",
+                    help="skip the batched-solve and served-stream legs")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()

@@ -252,6 +252,39 @@ lbm_status lbm_get_velocity_noalloc(lbm_ctx *ctx, double *host_out, size_t n);
 
 lbm_status lbm_sync(lbm_ctx *ctx);
 const char *lbm_last_error(const lbm_ctx *ctx);
+
+/* ---- batches: many lattices of uneven size advanced together ----
+ * (workload shaped like a grid-convergence sweep: one solve per resolution).
+ * lbm_batch_create takes n distinct, configured and initialised contexts
+ * on one device.  It prepares them (geometry, initial collision), gives
+ * each a private stream and, when autotune_blocks != 0, picks the bulk and
+ * boundary-node block widths per lattice shape by timing the kernels into a
+ * scratch buffer (the simulation state is untouched).  While in a batch the
+ * contexts must be stepped only through the batch; their queries remain
+ * valid.  lbm_batch_destroy gives the contexts their streams back (it does
+ * not destroy them).  cuda_stream is kept for reference only: the batch runs
+ * on private streams, so lbm_batch_step returns with work in flight and the
+ * contexts' queries (which synchronise their streams) wait for it.
+ * Stepping captures one step pair of every lattice with static solids into
+ * a CUDA graph whose per-lattice chains are independent branches, and
+ * replays it: two steps of the whole batch per launch.  Lattices with
+ * moving solids step directly.  Under graph replay the force history keeps
+ * only the last two records per lattice (lbm_get_force_torque is exact).
+ * lbm_batch_run_to_steady runs every lattice to its own residual < tol
+ * (checked every check_every steps, as lbm_run_to_steady), drops converged
+ * lattices from the graph, and reports steps_done[i] and residual[i]. */
+typedef struct lbm_batch lbm_batch;
+lbm_status lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int n,
+                            void *cuda_stream, int autotune_blocks);
+void lbm_batch_destroy(lbm_batch *batch);
+lbm_status lbm_batch_step(lbm_batch *batch, int nsteps);
+lbm_status lbm_batch_run_to_steady(lbm_batch *batch, double tol,
+                                   int check_every, int max_steps,
+                                   int64_t *steps_done, double *residual);
+/* block widths chosen for lattice i and the number of graph launches */
+lbm_status lbm_batch_info(lbm_batch *batch, int i, int *bulk_block,
+                          int *list_block, int64_t *graph_launches);
+const char *lbm_batch_last_error(const lbm_batch *batch);
 /* Library version string. */
 const char *lbm_version(void);
 

@@ -62,6 +62,9 @@ struct lbm_ctx {
   long long N = 0;
   long long fs = 0;  // direction stride of the distribution arrays (elements)
   int bulk_block = 128;
+  int list_block = 256;
+  int cache_hints = 0;
+  int coll_mode = 0;  // CM_BGK, CM_MRT or CM_MRT_Q
   cudaStream_t st = 0;
   // auxiliary high-priority stream: the boundary-node sweep and the IBM
   // pre-pass run there, concurrently with the bulk sweep on `st`
@@ -252,6 +255,8 @@ KArgs base_args(lbm_ctx *ctx) {
   a.N = ctx->N;
   a.fs = ctx->fs;
   a.bulk_block = ctx->bulk_block;
+  a.cache_hints = ctx->cache_hints;
+  a.list_block = ctx->list_block;
   a.flags = ctx->flags;
   a.omega = ctx->omega;
   for (int k = 0; k < 19; k++) a.ds[k] = ctx->ds[k];
@@ -283,7 +288,7 @@ KArgs base_args(lbm_ctx *ctx) {
 }
 
 void sweep(lbm_ctx *ctx, SweepOp op, const KArgs &a, cudaStream_t s) {
-  launch_sweep(op, ctx->d.lattice, ctx->d.collision, ctx->d.precision, a, s);
+  launch_sweep(op, ctx->d.lattice, ctx->coll_mode, ctx->d.precision, a, s);
   ctx->launches++;
 }
 void sweep(lbm_ctx *ctx, SweepOp op, const KArgs &a) { sweep(ctx, op, a, ctx->st); }
@@ -751,6 +756,27 @@ void set_collision_constants(lbm_ctx *ctx) {
     }
   }
   ctx->inv_scale = d.precision == LBM_FP32_FP16STORE ? 1.0 / kFp16Scale : 1.0;
+  // kernel variant: MRT whose only non-BGK moments are the q moments (one
+  // common rate, the default) runs a cheaper in-place correction
+  ctx->coll_mode = CM_BGK;
+  if (d.collision == LBM_MRT) {
+    bool q_only = true;
+    double dq = 0;
+    bool have_q = false;
+    for (int k = 0; k < ctx->Q; k++) {
+      if (kind[k] == 'q') {
+        if (!have_q) {
+          dq = ctx->ds[k];
+          have_q = true;
+        } else if (ctx->ds[k] != dq) {
+          q_only = false;
+        }
+      } else if (ctx->ds[k] != 0) {
+        q_only = false;
+      }
+    }
+    ctx->coll_mode = q_only ? (dq != 0 ? CM_MRT_Q : CM_BGK) : CM_MRT;
+  }
 }
 
 }  // namespace
@@ -814,6 +840,9 @@ lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_st
       const int b = atoi(e);
       if (b >= 32 && b <= 512 && b % 32 == 0) ctx->bulk_block = b;
     }
+    if (const char *e = getenv("LBM_CACHE_HINTS")) ctx->cache_hints = atoi(e) & 3;
+    if (const char *e = getenv("LBM_MRT_GENERAL"))
+      if (atoi(e) && ctx->coll_mode == CM_MRT_Q) ctx->coll_mode = CM_MRT;
   }
   lbm_status s = LBM_OK;
   const size_t fbytes = (size_t)ctx->Q * ctx->fs * ctx->ssz;
@@ -1278,5 +1307,434 @@ lbm_status lbm_sync(lbm_ctx *ctx) {
   if (cnt[3]) return fail(ctx, LBM_ERR_CAPACITY, "a boundary or refill list overflowed its capacity");
   return LBM_OK;
 }
+
+}  // extern "C"
+
+// ===================================================================== batch
+//
+// Many lattices advanced together.  Each lattice keeps its own context; the
+// batch gives every context a private stream and captures one step pair
+// (even + odd, so that the ping-pong buffers return to their places) of all
+// active lattices into a single CUDA graph whose per-lattice chains are
+// independent branches.  Replaying the graph advances every lattice two
+// steps with one launch; small lattices overlap on the GPU instead of
+// queueing behind each other.  Residuals are checked every `check_every`
+// steps and converged lattices leave the graph.  Solids that move need a
+// geometry rebuild with host-side centres every step: such lattices are
+// stepped directly, outside the graph.
+struct lbm_batch {
+  std::vector<lbm_ctx *> ctx;
+  std::vector<cudaStream_t> user_st;   // restored on destroy
+  std::vector<cudaStream_t> own_st;    // private stream per lattice
+  std::vector<cudaEvent_t> ev_done;
+  cudaEvent_t ev_origin = nullptr;
+  cudaStream_t origin = nullptr;       // private stream the graph runs on
+  cudaStream_t user = nullptr;         // stream given at creation
+  std::vector<char> active;
+  std::vector<long long> steps_done;
+  std::vector<double> residual;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> graph_cur;          // cur of each lattice when captured
+  std::vector<long long> pair_launches;  // kernels of one captured step pair
+  std::vector<int> graph_slot;           // force-record slot of the pair's 2nd step
+  std::vector<char> in_graph;
+  long long graph_launches = 0;
+  std::string err;
+};
+
+namespace {
+
+lbm_status bfail(lbm_batch *b, lbm_status s, const std::string &m) {
+  if (b) b->err = m;
+  return s;
+}
+
+#define BCK(expr)                                                          \
+  do {                                                                     \
+    cudaError_t _e = (expr);                                               \
+    if (_e != cudaSuccess)                                                 \
+      return bfail(b, LBM_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(_e)); \
+  } while (0)
+
+// Time the bulk sweep of one lattice for a few block widths and keep the
+// fastest (writes go to a scratch buffer: the simulation state is untouched).
+lbm_status autotune(lbm_ctx *ctx, void *scratch) {
+  const int cand_bulk[3] = {64, 128, 256};
+  const int cand_list[3] = {64, 128, 256};
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  KArgs a = base_args(ctx);
+  a.src = ctx->f[ctx->cur];
+  a.dst = scratch;
+  a.force_acc = force_slot(ctx, (ctx->slot + kHistCap / 2) % kHistCap);
+  float best = 1e30f;
+  int best_b = ctx->bulk_block;
+  for (int c : cand_bulk) {
+    a.bulk_block = c;
+    sweep(ctx, OP_BULK_SWEEP, a);  // warm
+    cudaEventRecord(e0, ctx->st);
+    for (int r = 0; r < 3; r++) sweep(ctx, OP_BULK_SWEEP, a);
+    cudaEventRecord(e1, ctx->st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) {
+      best = ms;
+      best_b = c;
+    }
+  }
+  ctx->bulk_block = best_b;
+  best = 1e30f;
+  int best_l = ctx->list_block;
+  if (a.list_cap > 0)
+    for (int c : cand_list) {
+      a.list_block = c;
+      sweep(ctx, OP_LIST_SWEEP, a);
+      cudaEventRecord(e0, ctx->st);
+      for (int r = 0; r < 3; r++) sweep(ctx, OP_LIST_SWEEP, a);
+      cudaEventRecord(e1, ctx->st);
+      cudaEventSynchronize(e1);
+      float ms = 0;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (ms < best) {
+        best = ms;
+        best_l = c;
+      }
+    }
+  ctx->list_block = best_l;
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  // forget the scratch force record written while tuning
+  cudaMemsetAsync(a.force_acc, 0, sizeof(double) * kMaxSolids * 6, ctx->st);
+  return cudaGetLastError() == cudaSuccess ? LBM_OK : LBM_ERR_CUDA;
+}
+
+void drop_graph(lbm_batch *b) {
+  if (b->exec) cudaGraphExecDestroy(b->exec);
+  b->exec = nullptr;
+}
+
+// Capture two steps of every active lattice with static geometry.
+lbm_status capture(lbm_batch *b) {
+  drop_graph(b);
+  const int n = (int)b->ctx.size();
+  b->in_graph.assign(n, 0);
+  b->graph_cur.assign(n, 0);
+  b->pair_launches.assign(n, 0);
+  b->graph_slot.assign(n, 0);
+  struct Saved {
+    int cur, slot;
+    bool prev_local, timing;
+    long long step, launches, records;
+  };
+  std::vector<Saved> saved(n);
+  BCK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
+  BCK(cudaEventRecord(b->ev_origin, b->origin));
+  lbm_status st = LBM_OK;
+  int members = 0;
+  for (int i = 0; i < n && st == LBM_OK; i++) {
+    lbm_ctx *c = b->ctx[i];
+    if (!b->active[i] || any_moving(c)) continue;
+    saved[i] = {c->cur, c->slot, c->prev_local, c->timing, c->step, c->launches, c->records};
+    c->timing = false;
+    b->graph_cur[i] = c->cur;
+    cudaStreamWaitEvent(c->st, b->ev_origin, 0);
+    st = step_once(c);
+    if (st == LBM_OK) st = step_once(c);
+    cudaEventRecord(b->ev_done[i], c->st);
+    cudaStreamWaitEvent(b->origin, b->ev_done[i], 0);
+    b->in_graph[i] = 1;
+    members++;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e = cudaStreamEndCapture(b->origin, &g);
+  // capture only recorded the work: put the host-side state back
+  for (int i = 0; i < n; i++) {
+    if (!b->in_graph[i]) continue;
+    lbm_ctx *c = b->ctx[i];
+    b->pair_launches[i] = c->launches - saved[i].launches;
+    b->graph_slot[i] = c->slot;  // after two captured steps
+    c->cur = saved[i].cur;
+    c->slot = saved[i].slot;
+    c->prev_local = saved[i].prev_local;
+    c->timing = saved[i].timing;
+    c->step = saved[i].step;
+    c->records = saved[i].records;
+    c->launches = saved[i].launches;
+  }
+  if (st != LBM_OK) {
+    if (g) cudaGraphDestroy(g);
+    return st;
+  }
+  if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("graph capture: ") + cudaGetErrorString(e));
+  if (members == 0) {
+    cudaGraphDestroy(g);
+    return LBM_OK;
+  }
+  e = cudaGraphInstantiate(&b->exec, g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+  return LBM_OK;
+}
+
+// Host bookkeeping of one replayed step pair.  The replay writes the two
+// force-record slots that followed the capture-time slot, so the context's
+// current slot is the second of them after every replay.
+void after_replay(lbm_batch *b) {
+  for (size_t i = 0; i < b->ctx.size(); i++) {
+    if (!b->in_graph[i]) continue;
+    lbm_ctx *c = b->ctx[i];
+    c->slot = b->graph_slot[i];
+    c->step += 2;
+    c->prev_local = false;
+    c->records = std::min<long long>(c->records + 2, kHistCap);
+    c->launches += b->pair_launches[i];
+    b->steps_done[i] += 2;
+  }
+}
+
+bool graph_valid(const lbm_batch *b) {
+  if (!b->exec) return false;
+  for (size_t i = 0; i < b->ctx.size(); i++) {
+    const bool want = b->active[i] && !any_moving(b->ctx[i]);
+    if (want != (bool)b->in_graph[i]) return false;
+    if (want && b->ctx[i]->cur != b->graph_cur[i]) return false;
+  }
+  return true;
+}
+
+lbm_status batch_advance(lbm_batch *b, int nsteps) {
+  const int n = (int)b->ctx.size();
+  int done = 0;
+  while (done < nsteps) {
+    const bool pair = nsteps - done >= 2;
+    bool any_static = false;
+    for (int i = 0; i < n; i++) any_static |= b->active[i] && !any_moving(b->ctx[i]);
+    if (pair && any_static) {
+      if (!graph_valid(b)) {
+        // the per-slot bookkeeping in after_replay assumes the capture-time
+        // slots; capture again whenever membership or buffer parity changed
+        lbm_status s = capture(b);
+        if (s != LBM_OK) return s;
+      }
+      if (b->exec) {
+        // the replay follows each lattice's earlier work on its own stream,
+        // and later work on those streams (queries, residuals) follows it
+        for (int i = 0; i < n; i++) {
+          if (!b->in_graph[i]) continue;
+          BCK(cudaEventRecord(b->ev_done[i], b->ctx[i]->st));
+          BCK(cudaStreamWaitEvent(b->origin, b->ev_done[i], 0));
+        }
+        BCK(cudaGraphLaunch(b->exec, b->origin));
+        BCK(cudaEventRecord(b->ev_origin, b->origin));
+        for (int i = 0; i < n; i++)
+          if (b->in_graph[i]) BCK(cudaStreamWaitEvent(b->ctx[i]->st, b->ev_origin, 0));
+        b->graph_launches++;
+        after_replay(b);
+      }
+      // lattices outside the graph (moving solids) step directly
+      for (int i = 0; i < n; i++) {
+        if (!b->active[i] || b->in_graph[i]) continue;
+        for (int k = 0; k < 2; k++) {
+          lbm_status s = step_once(b->ctx[i]);
+          if (s != LBM_OK) return bfail(b, s, lbm_last_error(b->ctx[i]));
+        }
+        b->steps_done[i] += 2;
+      }
+      done += 2;
+    } else {
+      for (int i = 0; i < n; i++) {
+        if (!b->active[i]) continue;
+        lbm_status s = step_once(b->ctx[i]);
+        if (s != LBM_OK) return bfail(b, s, lbm_last_error(b->ctx[i]));
+        b->steps_done[i] += 1;
+      }
+      done += 1;
+    }
+  }
+  return LBM_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+lbm_status lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int n, void *cuda_stream,
+                            int autotune_blocks) {
+  if (!out || !ctxs || n <= 0) return LBM_ERR_ARG;
+  *out = nullptr;
+  lbm_batch *b = new lbm_batch();
+  b->user = (cudaStream_t)cuda_stream;
+  int dev0 = ctxs[0] ? ctxs[0]->device : -1;
+  size_t scratch_bytes = 0;
+  for (int i = 0; i < n; i++) {
+    lbm_ctx *c = ctxs[i];
+    if (!c || c->device != dev0) {
+      delete b;
+      return LBM_ERR_ARG;
+    }
+    for (int j = 0; j < i; j++)
+      if (ctxs[j] == c) {
+        delete b;
+        return LBM_ERR_ARG;
+      }
+    lbm_status s = prepare(c);
+    if (s != LBM_OK) {
+      delete b;
+      return s;
+    }
+    scratch_bytes = std::max<size_t>(scratch_bytes, (size_t)c->Q * c->fs * c->ssz);
+  }
+  b->ctx.assign(ctxs, ctxs + n);
+  b->active.assign(n, 1);
+  b->steps_done.assign(n, 0);
+  b->residual.assign(n, NAN);
+  b->in_graph.assign(n, 0);
+  b->graph_cur.assign(n, 0);
+  cudaError_t e = cudaEventCreateWithFlags(&b->ev_origin, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
+  for (int i = 0; i < n && e == cudaSuccess; i++) {
+    lbm_ctx *c = b->ctx[i];
+    cudaStreamSynchronize(c->st);
+    cudaStream_t s = nullptr;
+    cudaEvent_t ev = nullptr;
+    e = cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming);
+    b->user_st.push_back(c->st);
+    b->own_st.push_back(s);
+    b->ev_done.push_back(ev);
+    c->st = s;
+  }
+  if (e == cudaSuccess && autotune_blocks) {
+    void *scratch = nullptr;
+    e = cudaMalloc(&scratch, scratch_bytes);
+    if (e == cudaSuccess) {
+      for (int i = 0; i < n; i++) {
+        // lattices of the same shape share the result
+        int same = -1;
+        for (int j = 0; j < i; j++)
+          if (b->ctx[j]->d.nx == b->ctx[i]->d.nx && b->ctx[j]->d.ny == b->ctx[i]->d.ny &&
+              b->ctx[j]->d.nz == b->ctx[i]->d.nz && b->ctx[j]->d.precision == b->ctx[i]->d.precision)
+            same = j;
+        if (same >= 0) {
+          b->ctx[i]->bulk_block = b->ctx[same]->bulk_block;
+          b->ctx[i]->list_block = b->ctx[same]->list_block;
+        } else if (autotune(b->ctx[i], scratch) != LBM_OK) {
+          e = cudaErrorUnknown;
+          break;
+        }
+      }
+      for (int i = 0; i < n; i++) cudaStreamSynchronize(b->ctx[i]->st);
+      cudaFree(scratch);
+    }
+  }
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    lbm_batch_destroy(b);
+    return LBM_ERR_CUDA;
+  }
+  *out = b;
+  return LBM_OK;
+}
+
+void lbm_batch_destroy(lbm_batch *b) {
+  if (!b) return;
+  drop_graph(b);
+  for (size_t i = 0; i < b->ctx.size(); i++) {
+    if (i < b->own_st.size() && b->own_st[i]) {
+      cudaStreamSynchronize(b->own_st[i]);
+      b->ctx[i]->st = b->user_st[i];
+      cudaStreamDestroy(b->own_st[i]);
+    }
+    if (i < b->ev_done.size() && b->ev_done[i]) cudaEventDestroy(b->ev_done[i]);
+  }
+  if (b->ev_origin) cudaEventDestroy(b->ev_origin);
+  if (b->origin) {
+    cudaStreamSynchronize(b->origin);
+    cudaStreamDestroy(b->origin);
+  }
+  delete b;
+}
+
+lbm_status lbm_batch_step(lbm_batch *b, int nsteps) {
+  if (!b || nsteps < 0) return LBM_ERR_ARG;
+  lbm_status s = batch_advance(b, nsteps);
+  if (s != LBM_OK) return s;
+  BCK(cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int check_every, int max_steps,
+                                   int64_t *steps_done, double *residual) {
+  if (!b || check_every < 1 || max_steps < 0) return LBM_ERR_ARG;
+  const int n = (int)b->ctx.size();
+  for (int i = 0; i < n; i++) {
+    lbm_ctx *c = b->ctx[i];
+    if (!c->u_now) {
+      lbm_ctx *ctx = c;
+      TRY(dalloc(ctx, (void **)&c->u_now, sizeof(double) * c->D * c->N));
+      TRY(dalloc(ctx, (void **)&c->u_snap, sizeof(double) * c->D * c->N));
+    }
+    b->active[i] = 1;
+    b->steps_done[i] = 0;
+    b->residual[i] = INFINITY;
+    TRY(velocity_to(c, c->u_snap));
+  }
+  int left = n;
+  lbm_status result = LBM_OK;
+  while (left > 0) {
+    int k = check_every;
+    long long most = 0;
+    for (int i = 0; i < n; i++)
+      if (b->active[i]) most = std::max(most, b->steps_done[i]);
+    if (most + k > max_steps) k = (int)(max_steps - most);
+    if (k <= 0) break;
+    lbm_status s = batch_advance(b, k);
+    if (s != LBM_OK) return s;
+    for (int i = 0; i < n; i++) {
+      if (!b->active[i]) continue;
+      lbm_ctx *c = b->ctx[i];
+      TRY(velocity_to(c, c->u_now));
+      launch_residual(c->u_now, c->u_snap, 0, c->flags, c->N, c->D, c->red2, c->st);
+      c->launches++;
+    }
+    for (int i = 0; i < n; i++) {
+      if (!b->active[i]) continue;
+      lbm_ctx *c = b->ctx[i];
+      double h[2];
+      BCK(cudaMemcpyAsync(h, c->red2, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+      BCK(cudaStreamSynchronize(c->st));
+      const double r = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+      b->residual[i] = r;
+      c->last_residual = r;
+      if (!std::isfinite(r)) {
+        b->active[i] = 0;
+        left--;
+        result = bfail(b, LBM_ERR_DIVERGED, "lattice " + std::to_string(i) + " diverged");
+      } else if (r < tol) {
+        b->active[i] = 0;
+        left--;
+      } else {
+        std::swap(c->u_now, c->u_snap);
+      }
+    }
+  }
+  for (int i = 0; i < n; i++) {
+    if (steps_done) steps_done[i] = b->steps_done[i];
+    if (residual) residual[i] = b->residual[i];
+  }
+  return result;
+}
+
+lbm_status lbm_batch_info(lbm_batch *b, int i, int *bulk_block, int *list_block, int64_t *graph_launches) {
+  if (!b || i < 0 || i >= (int)b->ctx.size()) return LBM_ERR_ARG;
+  if (bulk_block) *bulk_block = b->ctx[i]->bulk_block;
+  if (list_block) *list_block = b->ctx[i]->list_block;
+  if (graph_launches) *graph_launches = b->graph_launches;
+  return LBM_OK;
+}
+
+const char *lbm_batch_last_error(const lbm_batch *b) { return b ? b->err.c_str() : "null batch"; }
 
 }  // extern "C"

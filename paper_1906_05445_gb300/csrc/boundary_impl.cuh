@@ -1,0 +1,603 @@
+// boundary_impl.cuh -- the kernels around the bulk sweep: boundary nodes
+// (interpolated bounce-back + Eq. 17), queries, local (initial) collisions,
+// refilling, the IBM band velocity, conversions, and the launcher of every
+// sweep-like operation.  Instantiated once per storage type by
+// sweep_<precision>.cu.
+#pragma once
+
+#include "sweep_impl.cuh"
+
+namespace lbm {
+
+// Interpolated bounce-back value of cut link (x_f, i) from post-collision
+// deviations (coefficients of Sec. 2.2, precomputed per link):
+//   f_i(x_f,t+1) = c0 f*_ib(x_f) + c1 f*_ib(x_ff) + c2 f*_ib(x_fff)
+//                + c3 f*_i(x_f) + c4 f*_i(x_ff) + mw.
+template <int LAT, typename S, typename T, typename LT>
+__device__ __forceinline__ T ibb_value(const KArgs &a, const S *__restrict__ src,
+                                       int i, int x, int y, int z, long long n,
+                                       int link, T isc, T &fs) {
+  using L = Lat<LAT>;
+  const int ib = L::opp(i);
+  const LT *c0 = (const LT *)a.links.c[0], *c1 = (const LT *)a.links.c[1],
+           *c2 = (const LT *)a.links.c[2], *c3 = (const LT *)a.links.c[3],
+           *c4 = (const LT *)a.links.c[4], *mw = (const LT *)a.links.mw;
+  const long long N = a.fs;
+  const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+  fs = Store<S>::ld(src + (long long)ib * N + n, isc);
+  T v = (T)c0[link] * fs + (T)mw[link];
+  const T k1 = (T)c1[link], k2 = (T)c2[link], k3 = (T)c3[link], k4 = (T)c4[link];
+  if (k1 != (T)0 || k2 != (T)0 || k4 != (T)0) {
+    const long long nff = wrap(x + ex, a.nx) +
+                          (long long)a.nx * (wrap(y + ey, a.ny) + (long long)a.ny * wrap(z + ez, a.nz));
+    if (k1 != (T)0) v += k1 * Store<S>::ld(src + (long long)ib * N + nff, isc);
+    if (k4 != (T)0) v += k4 * Store<S>::ld(src + (long long)i * N + nff, isc);
+    if (k2 != (T)0) {
+      const long long nfff = wrap(x + 2 * ex, a.nx) +
+                             (long long)a.nx * (wrap(y + 2 * ey, a.ny) +
+                                                (long long)a.ny * wrap(z + 2 * ez, a.nz));
+      v += k2 * Store<S>::ld(src + (long long)ib * N + nfff, isc);
+    }
+  }
+  if (k3 != (T)0) v += k3 * Store<S>::ld(src + (long long)i * N + n, isc);
+  return v;
+}
+
+// FP64 outputs of a query at one node from pre-collision deviations f.
+template <int LAT, typename T>
+__device__ __forceinline__ void write_fields(const KArgs &a, long long n,
+                                             const T (&f)[Lat<LAT>::Q], T Fx,
+                                             T Fy, T Fz) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q, D = L::D;
+  double fd[Q];
+  double drho = 0, j[3] = {0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < Q; i++) {
+    fd[i] = (double)f[i];
+    drho += fd[i];
+    j[0] += L::ex(i) * fd[i];
+    j[1] += L::ey(i) * fd[i];
+    j[2] += L::ez(i) * fd[i];
+  }
+  const double F[3] = {(double)Fx, (double)Fy, (double)Fz};
+  const double u[3] = {j[0] + 0.5 * F[0], j[1] + 0.5 * F[1], j[2] + 0.5 * F[2]};
+  if (a.out_rho) a.out_rho[n] = 1.0 + drho;
+  if (a.out_u)
+    for (int c = 0; c < D; c++) a.out_u[c * a.N + n] = u[c];
+  if (a.out_f)
+#pragma unroll
+    for (int i = 0; i < Q; i++) a.out_f[(long long)i * a.N + n] = L::w(i) + fd[i];
+  if (a.out_S || a.out_stress) {
+    const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
+    double P[3][3];
+    for (int p = 0; p < 3; p++)
+      for (int q = 0; q < 3; q++) P[p][q] = 0.5 * (F[p] * u[q] + u[p] * F[q]);
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const double neq = fd[i] - feq_dev<LAT, double>(i, drho, u[0], u[1], u[2], uu);
+      const int e[3] = {L::ex(i), L::ey(i), L::ez(i)};
+      for (int p = 0; p < 3; p++)
+        for (int q = 0; q < 3; q++) P[p][q] += neq * e[p] * e[q];
+    }
+    double tr = 0;
+    for (int p = 0; p < D; p++) tr += P[p][p];
+    const int nc = D == 2 ? 3 : 6;
+    const int ca[6] = {0, 1, D == 2 ? 0 : 2, 0, 1, 0};
+    const int cb[6] = {0, 1, D == 2 ? 1 : 2, 1, 2, 2};
+    for (int c = 0; c < nc; c++) {
+      const int p = ca[c], q = cb[c];
+      const double iso = p == q ? tr / D : 0.0;
+      const double S = -1.5 * (a.omega * (P[p][q] - iso) + a.s_bulk * iso);
+      if (a.out_S) a.out_S[c * a.N + n] = S;
+      if (a.out_stress)
+        a.out_stress[c * a.N + n] = (p == q ? -(1.0 + drho) / 3.0 : 0.0) + 2.0 * a.nu * S;
+    }
+  }
+}
+
+// ---------------------------------------------------------------- kernels
+template <int LAT, typename S>
+__global__ void __launch_bounds__(512) k_bulk_query(const KArgs a) {
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= a.nx) return;
+  const long long n = x + (long long)a.nx * (y + (long long)a.ny * z);
+  if (a.flags[n] != 0) return;
+  double f[Lat<LAT>::Q];
+  gather_pull<LAT, S, double>((const S *)a.src, a.fs, x, y, z, a.nx, a.ny, a.nz,
+                              a.inv_scale, f);
+  write_fields<LAT, double>(a, n, f, a.g[0], a.g[1], a.g[2]);
+}
+
+// Warp-sum of a double.
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Boundary-node sweep (MODE 0) or query (MODE 1): one thread per list node.
+template <int LAT, int CM, typename S, typename T, typename LT, int MODE>
+__global__ void __launch_bounds__(128) k_list(const KArgs a) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = a.counts[0];
+  if (cnt > a.list_cap) cnt = a.list_cap;
+  const bool active = t < cnt;
+  const T isc = kisc<T>(a);
+  const S *__restrict__ src = (const S *)a.src;
+  // momentum exchange (Eq. 17) of this thread for solid `sa` (the solid of
+  // its first cut link): the state-independent part -2 w_i e_i of every
+  // link was summed per node in FP64 when the geometry was built; the part
+  // linear in the deviations is formed here in the compute type and the
+  // sums are reduced in FP64
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  T dacc[6] = {0, 0, 0, 0, 0, 0};
+  int sa = -1;
+  if (active) {
+    const long long n = a.list_node[t];
+    const uint32_t mask = a.list_mask[t];
+    int link = a.list_link[t];
+    int x, y, z;
+    node_xyz(n, a.nx, a.ny, x, y, z);
+    T f[Q];
+    if (a.local_gather)
+      gather_local<LAT, S, T>(src, a.fs, n, isc, f);
+    else
+      gather_pull<LAT, S, T>(src, a.fs, x, y, z, a.nx, a.ny, a.nz, isc, f);
+    if (mask && !a.local_gather) {
+#pragma unroll
+      for (int i = 1; i < Q; i++) {
+        if (!((mask >> i) & 1u)) continue;
+        T fs;
+        const T v = ibb_value<LAT, S, T, LT>(a, src, i, x, y, z, n, link, isc, fs);
+        f[i] = v;
+        if (MODE == 0) {
+          const int s = a.links.sid[link];
+          if (sa < 0) sa = s;
+          const T e[3] = {(T)L::ex(i), (T)L::ey(i), (T)L::ez(i)};
+          const LT *uw0 = (const LT *)a.links.uw[0], *uw1 = (const LT *)a.links.uw[1],
+                   *uw2 = (const LT *)a.links.uw[2];
+          const LT *ar0 = (const LT *)a.links.arm[0], *ar1 = (const LT *)a.links.arm[1],
+                   *ar2 = (const LT *)a.links.arm[2];
+          const T uw[3] = {(T)uw0[link], (T)uw1[link], (T)uw2[link]};
+          const T r[3] = {(T)ar0[link], (T)ar1[link], (T)ar2[link]};
+          if (s == sa) {
+            // f*_ib(e_ib - u_w) - f_i(e_i - u_w) = -2 w_i e_i
+            //   - d*_ib (e_i + u_w) - d_i (e_i - u_w)   (d: deviations)
+            T dp[3];
+            for (int c = 0; c < 3; c++) dp[c] = -fs * (e[c] + uw[c]) - v * (e[c] - uw[c]);
+            dacc[0] += dp[0];
+            dacc[1] += dp[1];
+            dacc[2] += dp[2];
+            dacc[3] += r[1] * dp[2] - r[2] * dp[1];
+            dacc[4] += r[2] * dp[0] - r[0] * dp[2];
+            dacc[5] += r[0] * dp[1] - r[1] * dp[0];
+          } else {
+            // a second solid seen from the same node (narrow gap): full FP64
+            const double wi = L::w(i);
+            const double fsd = wi + (double)fs, fid = wi + (double)v;
+            double dp[3];
+            for (int c = 0; c < 3; c++)
+              dp[c] = fsd * (-(double)e[c] - (double)uw[c]) - fid * ((double)e[c] - (double)uw[c]);
+            const double rr[3] = {(double)r[0], (double)r[1], (double)r[2]};
+            atomicAdd(a.force_acc + 6 * s + 0, dp[0]);
+            atomicAdd(a.force_acc + 6 * s + 1, dp[1]);
+            atomicAdd(a.force_acc + 6 * s + 2, dp[2]);
+            atomicAdd(a.force_acc + 6 * s + 3, rr[1] * dp[2] - rr[2] * dp[1]);
+            atomicAdd(a.force_acc + 6 * s + 4, rr[2] * dp[0] - rr[0] * dp[2]);
+            atomicAdd(a.force_acc + 6 * s + 5, rr[0] * dp[1] - rr[1] * dp[0]);
+          }
+        }
+        link++;
+      }
+      if (MODE == 0 && sa >= 0)
+        for (int c = 0; c < 6; c++) acc[c] = a.list_cst[c * a.list_cap + t] + (double)dacc[c];
+    }
+    const uint8_t fl = a.flags[n];
+    T Fx, Fy, Fz;
+    node_force<T, LT>(a, n, fl, Fx, Fy, Fz);
+    if (MODE == 0) {
+      const Coll<T> c = make_coll<LAT, T>(a);
+      collide<LAT, CM, T>(f, Fx, Fy, Fz, c);
+      scatter<LAT, S, T>((S *)a.dst, a.fs, n, isc, f);
+    } else {
+      write_fields<LAT, T>(a, n, f, Fx, Fy, Fz);
+    }
+  }
+  if (MODE == 0 && a.force_acc) {
+    const int lane = threadIdx.x & 31;
+    for (int s = 0; s < a.nsolids; s++) {
+      if (!__any_sync(0xffffffffu, sa == s)) continue;
+      for (int c = 0; c < 6; c++) {
+        const double v = warp_sum(sa == s ? acc[c] : 0.0);
+        if (lane == 0) atomicAdd(a.force_acc + 6 * s + c, v);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- warp per
+// boundary node.  Lane i (< Q) owns direction i: it pulls f_i or rebuilds it
+// with the bounce-back rule, the moments and the q-moment correction are
+// warp reductions, and each lane writes its own f*_i.  Compared with a thread
+// per node this puts Q times more independent loads in flight for the few
+// thousand boundary nodes, which otherwise sit on the critical path.
+
+// per-lane direction tables packed into compile-time integers
+template <int LAT> __host__ __device__ constexpr unsigned long long pack_dir(int comp) {
+  unsigned long long r = 0;
+  for (int i = 0; i < Lat<LAT>::Q; i++) {
+    const int e = comp == 0 ? Lat<LAT>::ex(i) : comp == 1 ? Lat<LAT>::ey(i) : Lat<LAT>::ez(i);
+    r |= (unsigned long long)(e + 1) << (2 * i);
+  }
+  return r;
+}
+template <int LAT> __host__ __device__ constexpr unsigned long long pack_opp() {
+  unsigned long long r = 0;
+  for (int i = 0; i < Lat<LAT>::Q; i++) r |= (unsigned long long)Lat<LAT>::opp(i) << (5 * (i % 12));
+  return r;
+}
+template <int LAT> __host__ __device__ constexpr unsigned long long pack_opp_hi() {
+  unsigned long long r = 0;
+  for (int i = 12; i < Lat<LAT>::Q; i++) r |= (unsigned long long)Lat<LAT>::opp(i) << (5 * (i - 12));
+  return r;
+}
+
+template <typename T> __device__ __forceinline__ T wsum(T v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+template <int LAT, int CM, typename S, typename T>
+__global__ void __launch_bounds__(256) k_list_warp(const KArgs a) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  constexpr unsigned long long PX = pack_dir<LAT>(0), PY = pack_dir<LAT>(1), PZ = pack_dir<LAT>(2);
+  constexpr unsigned long long PO = pack_opp<LAT>(), POH = pack_opp_hi<LAT>();
+  __shared__ double part[8][6];
+  __shared__ int psid[8];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = blockIdx.x * (blockDim.x >> 5) + warp;  // list entry of this warp
+  int cnt = a.counts[0];
+  if (cnt > a.list_cap) cnt = a.list_cap;
+  const bool active = t < cnt;
+  const bool dir = lane < Q;
+  const T isc = kisc<T>(a);
+  const S *__restrict__ src = (const S *)a.src;
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  int sa = -1;
+  if (active) {
+    const long long n = a.list_node[t];
+    const uint32_t mask = a.list_mask[t];
+    const int lo = a.list_link[t];
+    int x, y, z;
+    node_xyz(n, a.nx, a.ny, x, y, z);
+    const int ex = (int)((PX >> (2 * lane)) & 3ull) - 1;
+    const int ey = (int)((PY >> (2 * lane)) & 3ull) - 1;
+    const int ez = (int)((PZ >> (2 * lane)) & 3ull) - 1;
+    const int cls = ex * ex + ey * ey + ez * ez;
+    const T w = cls == 0 ? (T)L::w(0) : (cls == 1 ? (T)L::w(1) : (T)L::w(Q - 1));
+    const int ib = lane < 12 ? (int)((PO >> (5 * lane)) & 31ull) : (int)((POH >> (5 * (lane - 12))) & 31ull);
+    const bool cut = dir && ((mask >> lane) & 1u);
+    T fi = 0, fs = 0;
+    int link = 0;
+    if (cut) {
+      link = lo + __popc(mask & ((1u << lane) - 1u));
+      fi = ibb_value<LAT, S, T, T>(a, src, lane, x, y, z, n, link, isc, fs);
+      (void)ib;
+    } else if (dir) {
+      const long long sn = wrap(x - ex, a.nx) +
+                           (long long)a.nx * (wrap(y - ey, a.ny) + (long long)a.ny * wrap(z - ez, a.nz));
+      fi = Store<S>::ld(src + (long long)lane * a.fs + sn, isc);
+    }
+    const uint8_t fl = a.flags[n];
+    T Fx, Fy, Fz;
+    node_force<T, T>(a, n, fl, Fx, Fy, Fz);
+    const T drho = wsum<T>(fi);
+    const T jx = wsum<T>((T)ex * fi), jy = wsum<T>((T)ey * fi), jz = wsum<T>((T)ez * fi);
+    const T ux = jx + (T)0.5 * Fx, uy = jy + (T)0.5 * Fy, uz = jz + (T)0.5 * Fz;
+    const T uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
+    const T eu = (T)ex * ux + (T)ey * uy + (T)ez * uz;
+    const T eF = (T)ex * Fx + (T)ey * Fy + (T)ez * Fz;
+    const T feq = w * (drho + (T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * uu);
+    const T fb = w * ((T)3 * (eF - uF) + (T)9 * eu * eF);
+    const Coll<T> c = make_coll<LAT, T>(a);
+    T out = c.omc * fi + c.omega * feq + c.cforce * fb;
+    if constexpr (CM == CM_MRT_Q) {
+      const T v = dir ? fi - feq + (T)0.5 * fb : (T)0;
+      const T qf = L::D == 3 ? (T)(5 * cls - 9) : (T)(3 * cls - 5);
+      const T kq = c.ds[4] * (T)(1.0 / mnorm<LAT>(4));
+      const T mx = wsum<T>(qf * (T)ex * v), my = wsum<T>(qf * (T)ey * v);
+      T corr = qf * ((T)ex * mx + (T)ey * my);
+      if (L::D == 3) corr += qf * (T)ez * wsum<T>(qf * (T)ez * v);
+      out += kq * corr;
+    }
+    if (dir) Store<S>::st((S *)a.dst + (long long)lane * a.fs + n, out, isc);
+    // Eq. 17 on this node's cut links (first solid: deviation part here,
+    // state-independent part from the geometry build)
+    const int first = mask ? __ffs(mask) - 1 : -1;
+    if (first >= 0) {
+      sa = a.links.sid[lo];
+      T dp[3] = {0, 0, 0}, tq[3] = {0, 0, 0};
+      if (cut) {
+        const int s = a.links.sid[link];
+        const T *uw0 = (const T *)a.links.uw[0], *uw1 = (const T *)a.links.uw[1],
+                *uw2 = (const T *)a.links.uw[2];
+        const T *ar0 = (const T *)a.links.arm[0], *ar1 = (const T *)a.links.arm[1],
+                *ar2 = (const T *)a.links.arm[2];
+        const T uw[3] = {uw0[link], uw1[link], uw2[link]};
+        const T r[3] = {ar0[link], ar1[link], ar2[link]};
+        const T e[3] = {(T)ex, (T)ey, (T)ez};
+        T d[3];
+        for (int k = 0; k < 3; k++) d[k] = -fs * (e[k] + uw[k]) - fi * (e[k] - uw[k]);
+        if (s == sa) {
+          for (int k = 0; k < 3; k++) dp[k] = d[k];
+          tq[0] = r[1] * d[2] - r[2] * d[1];
+          tq[1] = r[2] * d[0] - r[0] * d[2];
+          tq[2] = r[0] * d[1] - r[1] * d[0];
+        } else {
+          // a second solid seen from this node: full FP64 contribution
+          const double wi = (double)w;
+          const double fsd = wi + (double)fs, fid = wi + (double)fi;
+          double q[3];
+          for (int k = 0; k < 3; k++)
+            q[k] = fsd * (-(double)e[k] - (double)uw[k]) - fid * ((double)e[k] - (double)uw[k]);
+          const double rr[3] = {(double)r[0], (double)r[1], (double)r[2]};
+          atomicAdd(a.force_acc + 6 * s + 0, q[0]);
+          atomicAdd(a.force_acc + 6 * s + 1, q[1]);
+          atomicAdd(a.force_acc + 6 * s + 2, q[2]);
+          atomicAdd(a.force_acc + 6 * s + 3, rr[1] * q[2] - rr[2] * q[1]);
+          atomicAdd(a.force_acc + 6 * s + 4, rr[2] * q[0] - rr[0] * q[2]);
+          atomicAdd(a.force_acc + 6 * s + 5, rr[0] * q[1] - rr[1] * q[0]);
+        }
+      }
+      for (int k = 0; k < 3; k++) {
+        acc[k] = a.list_cst[k * a.list_cap + t] + (double)wsum<T>(dp[k]);
+        acc[3 + k] = a.list_cst[(3 + k) * a.list_cap + t] + (double)wsum<T>(tq[k]);
+      }
+    }
+  }
+  // block reduction of the per-node sums, one FP64 atomic per component
+  if (lane == 0) {
+    psid[warp] = sa;
+    for (int k = 0; k < 6; k++) part[warp][k] = acc[k];
+  }
+  __syncthreads();
+  if (threadIdx.x < 6) {
+    const int k = threadIdx.x, nw = blockDim.x >> 5;
+    int s0 = -1;
+    for (int wi = 0; wi < nw; wi++)
+      if (psid[wi] >= 0) {
+        s0 = psid[wi];
+        break;
+      }
+    double sum = 0;
+    for (int wi = 0; wi < nw; wi++) {
+      if (psid[wi] < 0) continue;
+      if (psid[wi] == s0)
+        sum += part[wi][k];
+      else
+        atomicAdd(a.force_acc + 6 * psid[wi] + k, part[wi][k]);
+    }
+    if (s0 >= 0) atomicAdd(a.force_acc + 6 * s0 + k, sum);
+  }
+}
+
+// Local read of a pre-collision state: collide into dst (MODE 0) or write
+// fields (MODE 1).  One thread per node.
+template <int LAT, int CM, typename S, typename T, typename LT, int MODE>
+__global__ void __launch_bounds__(256) k_local(const KArgs a) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  const uint8_t fl = a.flags[n];
+  if (fl & FL_SOLID) return;
+  const T isc = kisc<T>(a);
+  T f[Lat<LAT>::Q];
+  gather_local<LAT, S, T>((const S *)a.src, a.fs, n, isc, f);
+  T Fx, Fy, Fz;
+  node_force<T, LT>(a, n, fl, Fx, Fy, Fz);
+  if (MODE == 0) {
+    const Coll<T> c = make_coll<LAT, T>(a);
+    collide<LAT, CM, T>(f, Fx, Fy, Fz, c);
+    scatter<LAT, S, T>((S *)a.dst, a.fs, n, isc, f);
+  } else {
+    write_fields<LAT, T>(a, n, f, Fx, Fy, Fz);
+  }
+}
+
+// Refill of nodes uncovered by a moving solid: equilibrium at the mean
+// density of neighbours fluid before and after the move and at the local
+// wall velocity, then the node's collision, written into the current
+// post-collision array (src == dst).
+template <int LAT, int CM, typename S, typename T>
+__global__ void __launch_bounds__(128) k_refill(const KArgs a) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = a.counts[2];
+  if (cnt > a.refill_cap) cnt = a.refill_cap;
+  if (t >= cnt) return;
+  const long long n = a.refill_node[t];
+  const int sidx = a.refill_sid[t];
+  int x, y, z;
+  node_xyz(n, a.nx, a.ny, x, y, z);
+  const S *src = (const S *)a.src;
+  const T isc = kisc<T>(a);
+  double rs = 0;
+  int cntn = 0;
+#pragma unroll
+  for (int j = 1; j < Q; j++) {
+    const long long nb = wrap(x + L::ex(j), a.nx) +
+                         (long long)a.nx * (wrap(y + L::ey(j), a.ny) +
+                                            (long long)a.ny * wrap(z + L::ez(j), a.nz));
+    if (a.sid[nb] != 0 || (a.flags[nb] & FL_NEW)) continue;
+    double r = 1.0;
+    for (int k = 0; k < Q; k++) r += (double)Store<S>::ld(src + (long long)k * a.fs + nb, isc);
+    rs += r;
+    cntn++;
+  }
+  const double rho = cntn ? rs / cntn : 1.0;
+  const SolidDev &b = a.solids.s[sidx];
+  double r[3] = {x - b.c[0], y - b.c[1], z - b.c[2]};
+  r[0] -= a.nx * round(r[0] / a.nx);
+  r[1] -= a.ny * round(r[1] / a.ny);
+  r[2] = (L::D == 2 || b.kind == 1) ? 0.0 : r[2] - a.nz * round(r[2] / a.nz);
+  double uw[3] = {b.U[0] + b.Om[1] * r[2] - b.Om[2] * r[1],
+                  b.U[1] + b.Om[2] * r[0] - b.Om[0] * r[2],
+                  b.U[2] + b.Om[0] * r[1] - b.Om[1] * r[0]};
+  if (L::D == 2) uw[2] = 0;
+  const double uu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+  T f[Q];
+#pragma unroll
+  for (int i = 0; i < Q; i++) f[i] = (T)feq_dev<LAT, double>(i, rho - 1.0, uw[0], uw[1], uw[2], uu);
+  T Fx, Fy, Fz;
+  node_force<T, T>(a, n, a.flags[n], Fx, Fy, Fz);
+  const Coll<T> c = make_coll<LAT, T>(a);
+  collide<LAT, CM, T>(f, Fx, Fy, Fz, c);
+  scatter<LAT, S, T>((S *)a.dst, a.fs, n, isc, f);
+}
+
+// IBM: unforced velocity u~ = (sum f e + g/2)/rho0 at band nodes (the
+// external half force only, no IBM half force) and zero the IBM force there.
+template <int LAT, typename S, typename T>
+__global__ void __launch_bounds__(64) k_band_vel(const KArgs a) {
+  using L = Lat<LAT>;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = a.counts[0];
+  if (cnt > a.list_cap) cnt = a.list_cap;
+  if (t >= cnt) return;
+  const long long n = a.list_node[t];
+  const uint8_t fl = a.flags[n];
+  if (!(fl & FL_BAND)) return;
+  int x, y, z;
+  node_xyz(n, a.nx, a.ny, x, y, z);
+  T f[L::Q];
+  const T isc = kisc<T>(a);
+  if (a.local_gather)
+    gather_local<LAT, S, T>((const S *)a.src, a.fs, n, isc, f);
+  else
+    gather_pull<LAT, S, T>((const S *)a.src, a.fs, x, y, z, a.nx, a.ny, a.nz, isc, f);
+  T j[3] = {0, 0, 0};
+#pragma unroll
+  for (int i = 0; i < L::Q; i++) {
+    j[0] += (T)L::ex(i) * f[i];
+    j[1] += (T)L::ey(i) * f[i];
+    j[2] += (T)L::ez(i) * f[i];
+  }
+  const bool g = !(fl & FL_NOG);
+  T *ub = (T *)a.u_band;
+  T *fi = (T *)a.f_ibm;
+  for (int c = 0; c < 3; c++) {
+    ub[c * a.N + n] = j[c] + (g ? (T)0.5 * kg<T>(a, c) : (T)0);
+    fi[c * a.N + n] = (T)0;
+  }
+}
+
+// Full FP64 f -> stored deviations (solid nodes get 0).
+template <int LAT, typename S, typename T>
+__global__ void __launch_bounds__(256) k_from_double(const KArgs a) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  const bool solid = a.flags[n] & FL_SOLID;
+  const T isc = kisc<T>(a);
+#pragma unroll
+  for (int i = 0; i < Lat<LAT>::Q; i++) {
+    const double v = solid ? 0.0 : a.out_f[(long long)i * a.N + n] - Lat<LAT>::w(i);
+    Store<S>::st((S *)a.dst + (long long)i * a.fs + n, (T)v, isc);
+  }
+}
+
+// Equilibrium deviations at (rho, u): rho in omega, u in g[].
+template <int LAT, typename S, typename T>
+__global__ void __launch_bounds__(256) k_fill_eq(const KArgs a) {
+  const long long n = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (n >= a.N) return;
+  const double ux = a.g[0], uy = a.g[1], uz = a.g[2];
+  const double uu = ux * ux + uy * uy + uz * uz;
+  const T isc = kisc<T>(a);
+#pragma unroll
+  for (int i = 0; i < Lat<LAT>::Q; i++)
+    Store<S>::st((S *)a.dst + (long long)i * a.fs + n,
+                 (T)feq_dev<LAT, double>(i, a.omega - 1.0, ux, uy, uz, uu), isc);
+}
+
+// ---------------------------------------------------------------- launch
+inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
+
+template <int LAT, int CM, typename S, typename T>
+void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
+  const int want = a.bulk_block > 0 ? a.bulk_block : 128;
+  const int bx = a.nx >= want ? want : ((a.nx + 31) / 32) * 32;
+  const dim3 gbulk(div_up(a.nx, bx), a.ny, a.nz);
+  const int lc = a.list_cap > 0 ? a.list_cap : 1;
+  switch (op) {
+  case OP_BULK_SWEEP:
+    switch (a.cache_hints & 3) {
+    case 1: k_bulk_sweep<LAT, CM, S, T, 1><<<div_up(a.N, want), want, 0, st>>>(a); break;
+    case 2: k_bulk_sweep<LAT, CM, S, T, 2><<<div_up(a.N, want), want, 0, st>>>(a); break;
+    case 3: k_bulk_sweep<LAT, CM, S, T, 3><<<div_up(a.N, want), want, 0, st>>>(a); break;
+    default: k_bulk_sweep<LAT, CM, S, T, 0><<<div_up(a.N, want), want, 0, st>>>(a);
+    }
+    break;
+  case OP_BULK_QUERY:
+    k_bulk_query<LAT, S><<<gbulk, bx, 0, st>>>(a);
+    break;
+  case OP_LIST_SWEEP:
+    if (a.list_cap > 0) {
+      if constexpr (CM != CM_MRT) {
+        // a warp per boundary node, list_block / 32 nodes per block
+        const int lb = a.list_block >= 64 ? (a.list_block > 256 ? 256 : a.list_block) : 256;
+        k_list_warp<LAT, CM, S, T><<<div_up(lc, lb / 32), lb, 0, st>>>(a);
+      } else {
+        // general MRT rates: a thread per node (small blocks spread the few
+        // boundary nodes over many SMs)
+        const int lb = a.list_block > 0 && a.list_block <= 128 ? a.list_block : 64;
+        k_list<LAT, CM, S, T, T, 0><<<div_up(lc, lb), lb, 0, st>>>(a);
+      }
+    }
+    break;
+  case OP_LIST_QUERY:
+    if (a.list_cap > 0) k_list<LAT, CM, S, double, T, 1><<<div_up(lc, 64), 64, 0, st>>>(a);
+    break;
+  case OP_LOCAL_INIT:
+    k_local<LAT, CM, S, T, T, 0><<<div_up(a.N, 256), 256, 0, st>>>(a);
+    break;
+  case OP_LOCAL_QUERY:
+    k_local<LAT, CM, S, double, T, 1><<<div_up(a.N, 256), 256, 0, st>>>(a);
+    break;
+  case OP_REFILL:
+    if (a.refill_cap > 0) k_refill<LAT, CM, S, T><<<div_up(a.refill_cap, 128), 128, 0, st>>>(a);
+    break;
+  case OP_BAND_VEL:
+    if (a.list_cap > 0) k_band_vel<LAT, S, T><<<div_up(lc, 64), 64, 0, st>>>(a);
+    break;
+  case OP_FROM_DOUBLE:
+    k_from_double<LAT, S, T><<<div_up(a.N, 256), 256, 0, st>>>(a);
+    break;
+  case OP_FILL_EQ:
+    k_fill_eq<LAT, S, T><<<div_up(a.N, 256), 256, 0, st>>>(a);
+    break;
+  }
+}
+
+// collision: CM_BGK, CM_MRT (general rates) or CM_MRT_Q (only the q moments
+// relax at a rate other than 1/tau, the default)
+template <typename S, typename T>
+void launch_precision(SweepOp op, int lattice, int collision, const KArgs &a,
+                      cudaStream_t st) {
+  if (lattice == LBM_D2Q9) {
+    if (collision == CM_MRT) launch_one<0, CM_MRT, S, T>(op, a, st);
+    else if (collision == CM_MRT_Q) launch_one<0, CM_MRT_Q, S, T>(op, a, st);
+    else launch_one<0, CM_BGK, S, T>(op, a, st);
+  } else {
+    if (collision == CM_MRT) launch_one<1, CM_MRT, S, T>(op, a, st);
+    else if (collision == CM_MRT_Q) launch_one<1, CM_MRT_Q, S, T>(op, a, st);
+    else launch_one<1, CM_BGK, S, T>(op, a, st);
+  }
+}
+
+}  // namespace lbm

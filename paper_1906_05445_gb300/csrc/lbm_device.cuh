@@ -125,13 +125,19 @@ __host__ __device__ constexpr bool conserved(int k) {
 
 // ---------------------------------------------------------------- storage
 template <typename S> struct Store;
+// ld/st: default caching; ld_stream/st_stream: evict-first (each element is
+// read once and written once per sweep)
 template <> struct Store<double> {
   template <typename T> __device__ static T ld(const double *p, T) { return (T)__ldg(p); }
+  template <typename T> __device__ static T ld_stream(const double *p, T) { return (T)__ldcs(p); }
   template <typename T> __device__ static void st(double *p, T v, T) { *p = (double)v; }
+  template <typename T> __device__ static void st_stream(double *p, T v, T) { __stcs(p, (double)v); }
 };
 template <> struct Store<float> {
   template <typename T> __device__ static T ld(const float *p, T) { return (T)__ldg(p); }
+  template <typename T> __device__ static T ld_stream(const float *p, T) { return (T)__ldcs(p); }
   template <typename T> __device__ static void st(float *p, T v, T) { *p = (float)v; }
+  template <typename T> __device__ static void st_stream(float *p, T v, T) { __stcs(p, (float)v); }
 };
 template <> struct Store<__nv_bfloat16> {
   template <typename T> __device__ static T ld(const __nv_bfloat16 *p, T) {
@@ -140,6 +146,8 @@ template <> struct Store<__nv_bfloat16> {
   template <typename T> __device__ static void st(__nv_bfloat16 *p, T v, T) {
     *p = __float2bfloat16_rn((float)v);
   }
+  template <typename T> __device__ static T ld_stream(const __nv_bfloat16 *p, T s) { return ld(p, s); }
+  template <typename T> __device__ static void st_stream(__nv_bfloat16 *p, T v, T s) { st(p, v, s); }
 };
 // FP16 keeps d_i * scale (scale = 2^k) so that deviations stay in the normal
 // range; the scale is exact in binary, so it only shifts the exponent.
@@ -150,6 +158,8 @@ template <> struct Store<__half> {
   template <typename T> __device__ static void st(__half *p, T v, T inv_scale) {
     *p = __float2half_rn((float)(v / inv_scale));
   }
+  template <typename T> __device__ static T ld_stream(const __half *p, T s) { return ld(p, s); }
+  template <typename T> __device__ static void st_stream(__half *p, T v, T s) { st(p, v, s); }
 };
 
 // ---------------------------------------------------------------- collision
@@ -193,11 +203,21 @@ __device__ __forceinline__ T edot(T vx, T vy, T vz) {
 // correction (omega - s_k) (M_k.(Delta + Fbar/2)) M_ki / |M_k|^2, which
 // equals m* = m - S(m - meq) + (I - S/2) M Fbar, f* = M^-1 m* because the
 // rows of M are orthogonal.
-template <int LAT, bool MRT, typename T>
+// collision modes of the kernels
+enum : int { CM_BGK = 0, CM_MRT = 1, CM_MRT_Q = 2 };
+
+// q-moment rows (energy flux, odd in e): (5|e|^2 - 9) e_a on D3Q19,
+// (3|e|^2 - 5) e_a on D2Q9 (rows 4, 6, 8 / 4, 6 of the basis)
+template <int LAT> __host__ __device__ constexpr int qrow(int a, int i) {
+  return mrow<LAT>(4 + 2 * a, i);
+}
+
+template <int LAT, int CM, typename T>
 __device__ __forceinline__ void collide(T (&f)[Lat<LAT>::Q], T Fx, T Fy, T Fz,
                                         const Coll<T> &c) {
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
+  constexpr bool MRT = CM == CM_MRT;
   T drho = 0, jx = 0, jy = 0, jz = 0;
   static_for<Q>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
@@ -214,6 +234,55 @@ __device__ __forceinline__ void collide(T (&f)[Lat<LAT>::Q], T Fx, T Fy, T Fz,
   const T uF = ux * Fx + uy * Fy + uz * Fz;
   const T base = drho - (T)1.5 * uu;
   const T om = c.omega, omc = c.omc, cf = c.cforce;
+  if constexpr (CM != CM_MRT) {
+    // BGK, or MRT whose only non-BGK moments are the q moments: update in
+    // place pair by pair; the odd q moments of Delta + Fbar/2 only need the
+    // differences f_i - f_ib - 2A + AF of each pair
+    T mq[3] = {0, 0, 0};
+    {
+      constexpr T w0 = (T)L::w(0);
+      const T S = w0 * base, SF = (T)(-3.0 * L::w(0)) * uF;
+      f[0] = omc * f[0] + om * S + cf * SF;
+    }
+    static_for<Q>([&](auto ic) {
+      constexpr int i = decltype(ic)::value;
+      if constexpr (i > 0 && L::opp(i) > i) {
+        constexpr int j = L::opp(i);
+        constexpr T w = (T)L::w(i);
+        const T eu = edot<LAT, i, T>(ux, uy, uz);
+        const T eF = edot<LAT, i, T>(Fx, Fy, Fz);
+        const T S = w * (base + (T)4.5 * eu * eu);
+        const T A = (T)(3.0 * L::w(i)) * eu;
+        const T SF = w * ((T)9 * eu * eF - (T)3 * uF);
+        const T AF = (T)(3.0 * L::w(i)) * eF;
+        const T P = om * S + cf * SF, M = om * A + cf * AF;
+        if constexpr (CM == CM_MRT_Q) {
+          const T d = f[i] - f[j] - (T)2 * A + AF;
+          static_for<L::D>([&](auto ac) {
+            constexpr int ax = decltype(ac)::value;
+            constexpr int q = qrow<LAT>(ax, i);
+            if constexpr (q != 0) mq[ax] += (T)q * d;
+          });
+        }
+        f[i] = omc * f[i] + P + M;
+        f[j] = omc * f[j] + P - M;
+      }
+    });
+    if constexpr (CM == CM_MRT_Q) {
+      // all q rows share one rate: a_a = (omega - s_q) m_q,a / |M_q|^2
+      const T k = c.ds[4] * (T)(1.0 / mnorm<LAT>(4));
+      T aq[3] = {k * mq[0], k * mq[1], k * mq[2]};
+      static_for<Q>([&](auto ic) {
+        constexpr int i = decltype(ic)::value;
+        static_for<L::D>([&](auto ac) {
+          constexpr int ax = decltype(ac)::value;
+          constexpr int q = qrow<LAT>(ax, i);
+          if constexpr (q != 0) f[i] += (T)q * aq[ax];
+        });
+      });
+    }
+    return;
+  }
   T out[Q];
   T v[MRT ? Q : 1];
   {

@@ -77,6 +77,8 @@ struct KArgs {
   double *out_rho, *out_u, *out_S, *out_stress, *out_f;
   int local_gather;  // 1: read src locally (pre-collision state), 0: pull
   int bulk_block;    // threads per block of the bulk sweep (multiple of 32)
+  int cache_hints;   // bulk sweep: bit 0 evict-first loads, bit 1 evict-first stores
+  int list_block;    // threads per block of the boundary-node sweep (32, 64 or 128)
 };
 
 // kernel families timed by lbm_set_timing

@@ -1,5 +1,5 @@
 // sweep_bf16.cu -- sweep kernels with __nv_bfloat16 storage and float arithmetic.
-#include "sweep_impl.cuh"
+#include "boundary_impl.cuh"
 
 namespace lbm {
 void launch_sweep_bf16(SweepOp op, int lattice, int collision, const KArgs &a,

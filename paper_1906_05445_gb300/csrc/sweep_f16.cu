@@ -1,5 +1,5 @@
 // sweep_f16.cu -- sweep kernels with __half storage and float arithmetic.
-#include "sweep_impl.cuh"
+#include "boundary_impl.cuh"
 
 namespace lbm {
 void launch_sweep_f16(SweepOp op, int lattice, int collision, const KArgs &a,

@@ -1,5 +1,5 @@
 // sweep_f32.cu -- sweep kernels with float storage and float arithmetic.
-#include "sweep_impl.cuh"
+#include "boundary_impl.cuh"
 
 namespace lbm {
 void launch_sweep_f32(SweepOp op, int lattice, int collision, const KArgs &a,

@@ -1,5 +1,5 @@
 // sweep_f64.cu -- sweep kernels with double storage and double arithmetic.
-#include "sweep_impl.cuh"
+#include "boundary_impl.cuh"
 
 namespace lbm {
 void launch_sweep_f64(SweepOp op, int lattice, int collision, const KArgs &a,

@@ -93,6 +93,12 @@ def _load():
         "lbm_set_timing": (st, [vp, i]),
         "lbm_get_kernel_time": (st, [vp, i, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "lbm_get_velocity_noalloc": (st, [vp, dp, sz]),
+        "lbm_batch_create": (st, [C.POINTER(vp), C.POINTER(vp), i, vp, i]),
+        "lbm_batch_destroy": (None, [vp]),
+        "lbm_batch_step": (st, [vp, i]),
+        "lbm_batch_run_to_steady": (st, [vp, d, i, i, C.POINTER(C.c_int64), dp]),
+        "lbm_batch_info": (st, [vp, i, C.POINTER(i), C.POINTER(i), C.POINTER(C.c_int64)]),
+        "lbm_batch_last_error": (C.c_char_p, [vp]),
         "lbm_sync": (st, [vp]),
         "lbm_last_error": (C.c_char_p, [vp]),
         "lbm_version": (C.c_char_p, []),
@@ -114,7 +120,8 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_get_residual", "lbm_get_solid_centre", "lbm_get_info",
     "lbm_device_field", "lbm_save", "lbm_load", "lbm_set_timing",
     "lbm_get_kernel_time", "lbm_get_velocity_noalloc", "lbm_sync", "lbm_last_error",
-    "lbm_version")})
+    "lbm_version", "lbm_batch_create", "lbm_batch_destroy", "lbm_batch_step",
+    "lbm_batch_run_to_steady", "lbm_batch_info", "lbm_batch_last_error")})
 
 
 class LbmError(RuntimeError):
@@ -288,3 +295,49 @@ class Lattice:
 
     def sync(self):
         self._check(lbm_sync(self.h))
+
+
+class Batch:
+    """Several lattices advanced together (one CUDA graph launch per step
+    pair, per-lattice residual checks); see lbm_batch_create."""
+
+    def __init__(self, lattices: Sequence[Lattice], stream: Optional[int] = None,
+                 autotune: bool = True):
+        self.lattices = list(lattices)
+        arr = (C.c_void_p * len(self.lattices))(*[lt.h.value for lt in self.lattices])
+        self.h = C.c_void_p()
+        st = lbm_batch_create(C.byref(self.h), arr, len(self.lattices),
+                              C.c_void_p(stream or 0), int(autotune))
+        if st != LBM_OK:
+            raise LbmError(st, "lbm_batch_create failed")
+
+    def _check(self, st: int):
+        if st != LBM_OK:
+            raise LbmError(st, lbm_batch_last_error(self.h).decode())
+
+    def step(self, n=1):
+        self._check(lbm_batch_step(self.h, int(n)))
+
+    def run_to_steady(self, tol, check_every=100, max_steps=100000):
+        n = len(self.lattices)
+        steps = (C.c_int64 * n)()
+        res = np.zeros(n)
+        self._check(lbm_batch_run_to_steady(self.h, tol, check_every, max_steps, steps,
+                                            _dp(res)))
+        return np.array(list(steps), dtype=np.int64), res
+
+    def info(self, i=0):
+        bb, lb, gl = C.c_int(), C.c_int(), C.c_int64()
+        self._check(lbm_batch_info(self.h, i, C.byref(bb), C.byref(lb), C.byref(gl)))
+        return bb.value, lb.value, gl.value
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

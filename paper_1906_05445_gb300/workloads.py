@@ -115,14 +115,15 @@ def translating_sphere(nx: int = 256, ny: int = 128, nz: int = 128,
 
 
 def convergence_batch(count: int = 32, seed: int = 1906, tau: float = 0.6,
-                      re_p: float = 5.0) -> List[Problem]:
-    """Grid-convergence sweep: sphere radii 4..32, cube edge 8R, seeded
-    offsets, alternating quadratic Bouzidi / IBM."""
+                      re_p: float = 5.0, r_min: float = 4.0,
+                      r_max: float = 32.0) -> List[Problem]:
+    """Grid-convergence sweep: sphere radii r_min..r_max (4..32), cube edge
+    8R, seeded offsets, alternating quadratic Bouzidi / IBM."""
     rng = np.random.default_rng(seed)
     out = []
     nu = (tau - 0.5) / 3.0
     for k in range(count):
-        r = 4.0 + 28.0 * k / max(count - 1, 1)
+        r = r_min + (r_max - r_min) * k / max(count - 1, 1)
         n = int(round(8 * r))
         off = rng.random(3)
         c = tuple(float(n / 2 + o) for o in off)
@@ -137,22 +138,25 @@ def convergence_batch(count: int = 32, seed: int = 1906, tau: float = 0.6,
 
 
 def request_stream(count: int = 200, seed: int = 1906, rate_hz: float = 50.0,
-                   max_2d: int = 1024, max_3d: int = 256):
-    """Poisson arrivals of mixed 2D Couette and 3D sphere solves."""
+                   max_2d: int = 1024, max_3d: int = 256, min_2d: int = 64,
+                   min_3d: int = 64, tau_range=(0.55, 1.0)):
+    """Poisson arrivals of mixed 2D Couette (min_2d..max_2d squared) and 3D
+    sphere (min_3d..max_3d cubed) solves, log-uniform sizes, seeded radii,
+    offsets, tau and scheme."""
     rng = np.random.default_rng(seed)
     t = 0.0
     out = []
     for k in range(count):
         t += rng.exponential(1.0 / rate_hz)
-        tau = float(rng.uniform(0.55, 1.0))
+        tau = float(rng.uniform(*tau_range))
         scheme = [BOUZIDI_LIN, BOUZIDI_QUAD, IBM][int(rng.integers(3))]
         if rng.random() < 0.5:
-            n = int(round(math.exp(rng.uniform(math.log(64), math.log(max_2d)))))
+            n = int(round(math.exp(rng.uniform(math.log(min_2d), math.log(max_2d)))))
             r1 = n / 6.4
             c = (n / 2 + float(rng.random()), n / 2 + float(rng.random()))
             p = couette_2d(n, r1, 2.8 * r1, c, 0.01, tau, scheme, 0, FP32)
         else:
-            n = int(round(math.exp(rng.uniform(math.log(64), math.log(max_3d)))))
+            n = int(round(math.exp(rng.uniform(math.log(min_3d), math.log(max_3d)))))
             p = fixed_sphere(n, n / 8.0, int(rng.integers(1 << 30)), tau,
                              scheme=scheme, precision=FP32, steps=0)
         p.name = f"req_{k}"

@@ -1,0 +1,90 @@
+"""Batched stepping (one CUDA graph per step pair over many lattices of
+uneven size): every lattice gives the same result alone and in the batch."""
+import numpy as np
+import pytest
+
+from paper_1906_05445_gb300 import workloads as W
+
+from .parity import rel_l2
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lbm():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_1906_05445_gb300 import build
+    build.build()
+    from paper_1906_05445_gb300 import lbm as L
+    return L
+
+
+def problems(prec):
+    return [W.fixed_sphere(24, 3.1, seed=1, tau=0.7, g=2e-5, scheme=W.BOUZIDI_QUAD,
+                           precision=prec),
+            W.fixed_sphere(33, 4.3, seed=2, tau=0.8, g=1e-5, scheme=W.IBM, precision=prec),
+            W.couette_2d(48, 7.5, 21.0, (24.4, 23.7), 0.01, 0.9, W.YU_QUAD, 0, prec),
+            W.translating_sphere(36, 20, 20, 4.3, seed=23, u=0.05, tau=0.7,
+                                 scheme=W.BOUZIDI_QUAD, precision=prec)]
+
+
+@pytest.mark.parametrize("prec", [W.FP64, W.FP32])
+@pytest.mark.parametrize("steps", [40, 37])
+def test_batch_equals_alone(lbm, prec, steps):
+    alone = [lbm.Lattice.from_problem(p) for p in problems(prec)]
+    for lt in alone:
+        lt.step(steps)
+    mixed = [lbm.Lattice.from_problem(p) for p in problems(prec)]
+    b = lbm.Batch(mixed, autotune=True)
+    b.step(steps)
+    for p, a, m in zip(problems(prec), alone, mixed):
+        ua, um = a.velocity(), m.velocity()
+        err = rel_l2(um, ua)
+        # FP32 IBM spreads with atomics: rounding order varies run to run
+        tol = 1e-5 if (prec == W.FP32 and p.scheme == W.IBM) else (1e-13 if p.scheme == W.IBM else 0.0)
+        assert err <= tol, (p.name, err)
+        Fa, Ta = a.force_torque(0)
+        Fm, Tm = m.force_torque(0)
+        rtol = 1e-6 if prec == W.FP32 else 1e-11
+        assert np.linalg.norm(Fm - Fa) <= rtol * np.linalg.norm(Fa) + 1e-13, p.name
+        assert m.info().steps == steps
+    bb, lb, launches = b.info(0)
+    assert bb in (64, 128, 256) and lb in (32, 64, 128) and launches >= 1
+    b.close()
+
+
+def test_batch_run_to_steady_matches_alone(lbm):
+    ps = [W.couette_2d(32, 5.0, 14.0, (16.3, 15.8), 0.01, 0.8, W.BOUZIDI_LIN, 0, W.FP64),
+          W.couette_2d(40, 6.2, 17.4, (20.2, 19.9), 0.01, 0.9, W.BOUZIDI_QUAD, 0, W.FP64),
+          W.fixed_sphere(20, 3.3, seed=4, tau=0.9, g=1e-6, scheme=W.BOUZIDI_QUAD,
+                         precision=W.FP64)]
+    want = []
+    for p in ps:
+        lt = lbm.Lattice.from_problem(p)
+        want.append(lt.run_to_steady(1e-6, 100, 30000))
+        lt.close()
+    mixed = [lbm.Lattice.from_problem(p) for p in ps]
+    b = lbm.Batch(mixed, autotune=False)
+    steps, res = b.run_to_steady(1e-6, 100, 30000)
+    for (done, r), s, rr in zip(want, steps, res):
+        assert s == done and abs(rr - r) <= 1e-9 * r
+    b.close()
+
+
+def test_served_results_equal_sequential_solves(lbm):
+    """Continuous batching: requests admitted while others run give the same
+    result (steps, residual, field) as each request solved alone."""
+    from paper_1906_05445_gb300 import serve
+    reqs = W.request_stream(count=6, seed=5, rate_hz=200.0, max_2d=48, max_3d=24,
+                            min_2d=32, min_3d=16, tau_range=(0.8, 1.0))
+    a = {r.name: r for r in serve.serve_batched(reqs, 1e-5, 100, 20000, keep_fields=True)}
+    b = {r.name: r for r in serve.serve_sequential(reqs, 1e-5, 100, 20000, keep_fields=True)}
+    assert set(a) == set(b) and len(a) == 6
+    for k in a:
+        assert a[k].steps == b[k].steps, k
+        # FP32; IBM spreading uses atomics, so rounding order may differ
+        assert rel_l2(a[k].velocity, b[k].velocity) <= 1e-5, k
+    s = serve.summarize(list(a.values()))
+    assert s["p99_s"] >= s["p50_s"] > 0

@@ -92,6 +92,8 @@ struct lbm_ctx {
   // IBM
   double *mk_dir = nullptr, *mk_dV = nullptr, *mk_F = nullptr;
   uint8_t *mk_sid = nullptr;
+  int4 *mk_base = nullptr;  // stencil table (rebuilt with the geometry)
+  void *mk_wts = nullptr;
   int nmark = 0;
   void *u_band = nullptr, *f_ibm = nullptr;
   // forces
@@ -416,8 +418,12 @@ lbm_status build_markers(lbm_ctx *ctx) {
   dfree(ctx, ctx->mk_dV);
   dfree(ctx, ctx->mk_F);
   dfree(ctx, ctx->mk_sid);
+  dfree(ctx, ctx->mk_base);
+  dfree(ctx, ctx->mk_wts);
   ctx->mk_dir = ctx->mk_dV = ctx->mk_F = nullptr;
   ctx->mk_sid = nullptr;
+  ctx->mk_base = nullptr;
+  ctx->mk_wts = nullptr;
   ctx->nmark = 0;
   if (ctx->scheme.scheme != LBM_IBM_DIRECT || ctx->solids.empty()) return LBM_OK;
   std::vector<double> dx, dy, dz, dV;
@@ -470,6 +476,8 @@ lbm_status build_markers(lbm_ctx *ctx) {
   TRY(dalloc(ctx, (void **)&ctx->mk_dV, sizeof(double) * n));
   TRY(dalloc(ctx, (void **)&ctx->mk_F, sizeof(double) * 3 * n));
   TRY(dalloc(ctx, (void **)&ctx->mk_sid, n));
+  TRY(dalloc(ctx, (void **)&ctx->mk_base, sizeof(int4) * n));
+  TRY(dalloc(ctx, &ctx->mk_wts, ctx->tsz * (ctx->D == 3 ? 64 : 16) * (size_t)n));
   CK(cudaMemcpyAsync(ctx->mk_dir, dir.data(), sizeof(double) * 3 * n, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->mk_dV, dV.data(), sizeof(double) * n, cudaMemcpyHostToDevice, ctx->st));
   CK(cudaMemcpyAsync(ctx->mk_sid, ms.data(), n, cudaMemcpyHostToDevice, ctx->st));
@@ -483,6 +491,8 @@ lbm_status build_markers(lbm_ctx *ctx) {
   }
   return LBM_OK;
 }
+
+void ibm_prepare(lbm_ctx *ctx);
 
 lbm_status read_counts(lbm_ctx *ctx, int out[16]) {
   CK(cudaMemcpyAsync(out, ctx->counts, 16 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
@@ -531,12 +541,13 @@ lbm_status rebuild_full(lbm_ctx *ctx) {
   if (cnt[3]) return fail(ctx, LBM_ERR_CAPACITY, "boundary list overflow during rebuild");
   ctx->list_count = moving ? -1 : cnt[0];
   ctx->link_count = moving ? -1 : cnt[1];
+  ibm_prepare(ctx);
   {
     std::vector<uint8_t> fl(ctx->N);
     CK(cudaMemcpyAsync(fl.data(), ctx->flags, ctx->N, cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
     long long b = 0;
-    for (long long k = 0; k < ctx->N; k++) b += fl[k] == 0;
+    for (long long k = 0; k < ctx->N; k++) b += (fl[k] & ~FL_NOG) == 0;
     ctx->bulk_nodes = b;
   }
   ctx->geom_dirty = false;
@@ -553,6 +564,7 @@ lbm_status rebuild_boxes(lbm_ctx *ctx) {
   Timed tm(ctx, TK_GEOM, 0, ctx->st);
   launch_geometry(g, ctx->d.precision, ctx->st);
   ctx->launches += 3;
+  ibm_prepare(ctx);
   return LBM_OK;
 }
 
@@ -565,20 +577,12 @@ double *force_slot(lbm_ctx *ctx, int slot) {
   return ctx->hist + (size_t)slot * kMaxSolids * 6;
 }
 
-// IBM: unforced velocity at the band, n_it interpolation/force iterations,
-// spreading, and the solid's force (into the given record slot).
-void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStream_t s) {
-  if (ctx->scheme.scheme != LBM_IBM_DIRECT || ctx->nmark == 0) return;
-  Timed tm(ctx, TK_IBM, 0, s);
-  KArgs a = base_args(ctx);
-  a.src = src;
-  a.local_gather = local ? 1 : 0;
-  sweep(ctx, OP_BAND_VEL, a, s);
+IbmArgs ibm_args(lbm_ctx *ctx, double *acc) {
   IbmArgs ib;
   memset(&ib, 0, sizeof(ib));
-  ib.nx = a.nx;
-  ib.ny = a.ny;
-  ib.nz = a.nz;
+  ib.nx = ctx->d.nx;
+  ib.ny = ctx->d.ny;
+  ib.nz = ctx->D == 2 ? 1 : ctx->d.nz;
   ib.dim = ctx->D;
   ib.N = ctx->N;
   ib.nmark = ctx->nmark;
@@ -590,7 +594,36 @@ void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStr
   ib.u_band = ctx->u_band;
   ib.f_ibm = ctx->f_ibm;
   ib.force_acc = acc;
+  ib.mk_base = ctx->mk_base;
+  ib.mk_wts = ctx->mk_wts;
+  return ib;
+}
+
+// stencil table of the markers at the geometry centres
+void ibm_prepare(lbm_ctx *ctx) {
+  if (ctx->scheme.scheme != LBM_IBM_DIRECT || ctx->nmark == 0) return;
+  launch_ibm_prepare(ibm_args(ctx, nullptr), ctx->d.precision, ctx->st);
+  ctx->launches++;
+}
+
+// IBM: unforced velocity at the band, n_it interpolation/force iterations,
+// spreading, and the solid's force (into the given record slot).
+void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStream_t s) {
+  if (ctx->scheme.scheme != LBM_IBM_DIRECT || ctx->nmark == 0) return;
+  Timed tm(ctx, TK_IBM, 0, s);
+  KArgs a = base_args(ctx);
+  a.src = src;
+  a.local_gather = local ? 1 : 0;
+  sweep(ctx, OP_BAND_VEL, a, s);
+  IbmArgs ib = ibm_args(ctx, acc);
   const int iters = std::max(1, ctx->scheme.ibm_iters);
+  if (iters == 1) {
+    ib.first = 1;
+    ib.reduce_force = 1;
+    launch_ibm_fused(ib, ctx->d.precision, s);
+    ctx->launches++;
+    return;
+  }
   for (int it = 0; it < iters; it++) {
     ib.first = it == 0;
     ib.use_f = it > 0;

@@ -103,11 +103,13 @@ __global__ void __launch_bounds__(512) k_bulk_query(const KArgs a) {
   const int y = blockIdx.y, z = blockIdx.z;
   if (x >= a.nx) return;
   const long long n = x + (long long)a.nx * (y + (long long)a.ny * z);
-  if (a.flags[n] != 0) return;
+  const uint8_t fl = a.flags[n];
+  if (fl & (uint8_t)~FL_NOG) return;
   double f[Lat<LAT>::Q];
   gather_pull<LAT, S, double>((const S *)a.src, a.fs, x, y, z, a.nx, a.ny, a.nz,
                               a.inv_scale, f);
-  write_fields<LAT, double>(a, n, f, a.g[0], a.g[1], a.g[2]);
+  const double gon = fl ? 0.0 : 1.0;
+  write_fields<LAT, double>(a, n, f, gon * a.g[0], gon * a.g[1], gon * a.g[2]);
 }
 
 // Warp-sum of a double.

@@ -172,7 +172,9 @@ __global__ void k_geom_list(const GeomArgs g, const uint8_t *sid_new) {
       if (sid_new[src]) mask |= 1u << i;
     }
   }
-  const bool listed = ibb ? mask != 0 : (fl & (FL_NOG | FL_BAND)) != 0;
+  // IBM: only band nodes need the spread force; nodes inside the solid
+  // that are not in the band run in the bulk sweep without external force
+  const bool listed = ibb ? mask != 0 : (fl & FL_BAND) != 0;
   const bool refill = (fl & FL_NEW) != 0;
   if (!listed && !refill) return;
   // claim the node once even if it lies in several boxes

@@ -80,19 +80,43 @@ __device__ __forceinline__ long long stencil_point(const IbmArgs &a, const Stenc
   return x + (long long)a.nx * (y + (long long)a.ny * z);
 }
 
+// Stencil base and the 4^dim weights of every marker, from its FP64
+// position (one warp per marker, a lane per stencil point).
 template <typename T>
-__global__ void __launch_bounds__(128) k_interp(const IbmArgs a) {
+__global__ void __launch_bounds__(128) k_prepare(const IbmArgs a) {
   const int m = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
   const int lane = threadIdx.x & 31;
-  if (m >= a.nmark) return;  // whole warp exits together
+  if (m >= a.nmark) return;
   const Marker k = marker(a, m);
   const Stencil<T> stc = stencil_of<T>(a, k);
   const int npts = a.dim == 3 ? 64 : 16;
-  const T *ub = (const T *)a.u_band, *fi = (const T *)a.f_ibm;
-  T U[3] = {0, 0, 0};
+  T *wts = (T *)a.mk_wts + (long long)m * npts;
   for (int p = lane; p < npts; p += 32) {
-    T wgt;
-    const long long n = stencil_point<T>(a, stc, p, wgt);
+    const int kx = p & 3, ky = (p >> 2) & 3, kz = p >> 4;
+    T wgt = phi4<T>(stc.dx + (T)kx) * phi4<T>(stc.dy + (T)ky);
+    if (a.dim == 3) wgt *= phi4<T>(stc.dz + (T)kz);
+    wts[p] = wgt;
+  }
+  if (lane == 0) a.mk_base[m] = make_int4(stc.ix, stc.iy, stc.iz, k.s);
+}
+
+__device__ __forceinline__ long long table_node(const IbmArgs &a, int4 b, int p) {
+  const int kx = p & 3, ky = (p >> 2) & 3, kz = p >> 4;
+  const int x = wrap(b.x + kx, a.nx), y = wrap(b.y + ky, a.ny);
+  const int z = a.dim == 3 ? wrap(b.z + kz, a.nz) : 0;
+  return x + (long long)a.nx * (y + (long long)a.ny * z);
+}
+
+// interpolated velocity of marker m (all lanes get the sum)
+template <typename T>
+__device__ __forceinline__ void interp_marker(const IbmArgs &a, int m, int lane, int4 b, T U[3]) {
+  const int npts = a.dim == 3 ? 64 : 16;
+  const T *ub = (const T *)a.u_band, *fi = (const T *)a.f_ibm;
+  const T *wts = (const T *)a.mk_wts + (long long)m * npts;
+  U[0] = U[1] = U[2] = 0;
+  for (int p = lane; p < npts; p += 32) {
+    const T wgt = wts[p];
+    const long long n = table_node(a, b, p);
     for (int c = 0; c < a.dim; c++) {
       T v = ub[c * a.N + n];
       if (a.use_f) v += fi[c * a.N + n];  // u~ + f dt / rho0, rho0 = 1
@@ -101,44 +125,44 @@ __global__ void __launch_bounds__(128) k_interp(const IbmArgs a) {
   }
   for (int c = 0; c < 3; c++)
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) U[c] += __shfl_down_sync(0xffffffffu, U[c], o);
-  if (lane == 0) {
-    const SolidDev &b = a.solids.s[k.s];
-    // desired velocity U + Omega x (X - c)
-    double Ud[3] = {b.U[0] + b.Om[1] * k.r[2] - b.Om[2] * k.r[1],
-                    b.U[1] + b.Om[2] * k.r[0] - b.Om[0] * k.r[2],
-                    b.U[2] + b.Om[0] * k.r[1] - b.Om[1] * k.r[0]};
-    for (int c = 0; c < 3; c++) {
-      const double F = c < a.dim ? (Ud[c] - (double)U[c]) : 0.0;  // rho0 (U^d - U~)/dt
-      a.Fm[c * a.nmark + m] = (a.first ? 0.0 : a.Fm[c * a.nmark + m]) + F;
-    }
-  }
+    for (int o = 16; o > 0; o >>= 1) U[c] += __shfl_xor_sync(0xffffffffu, U[c], o);
+}
+
+// desired velocity U + Omega x (X - c) of marker m minus the interpolated one
+__device__ __forceinline__ void direct_force(const IbmArgs &a, const Marker &k, const double U[3],
+                                             double F[3]) {
+  const SolidDev &b = a.solids.s[k.s];
+  const double Ud[3] = {b.U[0] + b.Om[1] * k.r[2] - b.Om[2] * k.r[1],
+                        b.U[1] + b.Om[2] * k.r[0] - b.Om[0] * k.r[2],
+                        b.U[2] + b.Om[0] * k.r[1] - b.Om[1] * k.r[0]};
+  for (int c = 0; c < 3; c++) F[c] = c < a.dim ? Ud[c] - U[c] : 0.0;  // rho0 (U^d - U~)/dt
 }
 
 template <typename T>
-__global__ void __launch_bounds__(128) k_spread(const IbmArgs a) {
+__device__ __forceinline__ void spread_marker(const IbmArgs &a, int m, int lane, int4 b,
+                                              const double F[3]) {
+  const int npts = a.dim == 3 ? 64 : 16;
+  const double dV = a.dV[m];
+  const T FdV[3] = {(T)(F[0] * dV), (T)(F[1] * dV), (T)(F[2] * dV)};
+  const T *wts = (const T *)a.mk_wts + (long long)m * npts;
+  T *fi = (T *)a.f_ibm;
+  for (int p = lane; p < npts; p += 32) {
+    const T wgt = wts[p];
+    const long long n = table_node(a, b, p);
+    for (int c = 0; c < a.dim; c++) atomicAdd(fi + c * a.N + n, FdV[c] * wgt);
+  }
+}
+
+// force on the solid, minus the marker forces (Sec. 3.1, Eq. B.7), reduced
+// per block in FP64
+__device__ __forceinline__ void reduce_solid_force(const IbmArgs &a, bool active, int lane,
+                                                   int warp, const Marker &k, const double F[3],
+                                                   double dV) {
   __shared__ double part[4][6];
   __shared__ int psid[4];
-  const int warp = threadIdx.x >> 5;
-  const int m = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
-  const int lane = threadIdx.x & 31;
-  const bool active = m < a.nmark;
-  if (lane == 0) psid[warp] = -1;
-  if (active) {
-    const Marker k = marker(a, m);
-    const Stencil<T> stc = stencil_of<T>(a, k);
-    const double dV = a.dV[m];
-    const double F[3] = {a.Fm[m], a.Fm[a.nmark + m], a.Fm[2 * a.nmark + m]};
-    const T FdV[3] = {(T)(F[0] * dV), (T)(F[1] * dV), (T)(F[2] * dV)};
-    const int npts = a.dim == 3 ? 64 : 16;
-    T *fi = (T *)a.f_ibm;
-    for (int p = lane; p < npts; p += 32) {
-      T wgt;
-      const long long n = stencil_point<T>(a, stc, p, wgt);
-      for (int c = 0; c < a.dim; c++) atomicAdd(fi + c * a.N + n, FdV[c] * wgt);
-    }
-    if (lane == 0 && a.reduce_force) {
-      // force on the solid: minus the marker forces (Sec. 3.1, Eq. B.7)
+  if (lane == 0) {
+    psid[warp] = -1;
+    if (active) {
       const double Fs[3] = {-F[0] * dV, -F[1] * dV, -F[2] * dV};
       part[warp][0] = Fs[0];
       part[warp][1] = Fs[1];
@@ -149,7 +173,6 @@ __global__ void __launch_bounds__(128) k_spread(const IbmArgs a) {
       psid[warp] = k.s;
     }
   }
-  if (!a.reduce_force) return;
   __syncthreads();
   if (threadIdx.x < 6) {
     const int c = threadIdx.x;
@@ -167,6 +190,67 @@ __global__ void __launch_bounds__(128) k_spread(const IbmArgs a) {
 }
 
 template <typename T>
+__global__ void __launch_bounds__(128) k_interp(const IbmArgs a) {
+  const int m = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  if (m >= a.nmark) return;  // whole warp exits together
+  const int4 b = a.mk_base[m];
+  T U[3];
+  interp_marker<T>(a, m, lane, b, U);
+  if (lane == 0) {
+    const Marker k = marker(a, m);
+    const double Ud[3] = {(double)U[0], (double)U[1], (double)U[2]};
+    double F[3];
+    direct_force(a, k, Ud, F);
+    for (int c = 0; c < 3; c++) a.Fm[c * a.nmark + m] = (a.first ? 0.0 : a.Fm[c * a.nmark + m]) + F[c];
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(128) k_spread(const IbmArgs a) {
+  const int warp = threadIdx.x >> 5;
+  const int m = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool active = m < a.nmark;
+  Marker k;
+  double F[3] = {0, 0, 0}, dV = 0;
+  if (active) {
+    k = marker(a, m);
+    F[0] = a.Fm[m];
+    F[1] = a.Fm[a.nmark + m];
+    F[2] = a.Fm[2 * a.nmark + m];
+    dV = a.dV[m];
+    spread_marker<T>(a, m, lane, a.mk_base[m], F);
+  }
+  if (a.reduce_force) reduce_solid_force(a, active, lane, warp, k, F, dV);
+}
+
+// single forcing iteration: interpolate, force, spread and reduce in one
+// pass (each warp spreads the force it just computed)
+template <typename T>
+__global__ void __launch_bounds__(128) k_fused(const IbmArgs a) {
+  const int warp = threadIdx.x >> 5;
+  const int m = (int)(((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5);
+  const int lane = threadIdx.x & 31;
+  const bool active = m < a.nmark;
+  Marker k;
+  double F[3] = {0, 0, 0}, dV = 0;
+  if (active) {
+    const int4 b = a.mk_base[m];
+    T U[3];
+    interp_marker<T>(a, m, lane, b, U);
+    k = marker(a, m);
+    const double Ud[3] = {(double)U[0], (double)U[1], (double)U[2]};
+    direct_force(a, k, Ud, F);
+    if (lane == 0)
+      for (int c = 0; c < 3; c++) a.Fm[c * a.nmark + m] = F[c];
+    dV = a.dV[m];
+    spread_marker<T>(a, m, lane, b, F);
+  }
+  reduce_solid_force(a, active, lane, warp, k, F, dV);
+}
+
+template <typename T>
 __global__ void __launch_bounds__(128) k_zero_band(const KArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   int cnt = a.counts[0];
@@ -179,6 +263,24 @@ __global__ void __launch_bounds__(128) k_zero_band(const KArgs a) {
 }
 
 }  // namespace
+
+void launch_ibm_prepare(const IbmArgs &a, int precision, cudaStream_t st) {
+  if (a.nmark <= 0) return;
+  const unsigned grid = (unsigned)((32LL * a.nmark + 127) / 128);
+  if (precision == LBM_FP64)
+    k_prepare<double><<<grid, 128, 0, st>>>(a);
+  else
+    k_prepare<float><<<grid, 128, 0, st>>>(a);
+}
+
+void launch_ibm_fused(const IbmArgs &a, int precision, cudaStream_t st) {
+  if (a.nmark <= 0) return;
+  const unsigned grid = (unsigned)((32LL * a.nmark + 127) / 128);
+  if (precision == LBM_FP64)
+    k_fused<double><<<grid, 128, 0, st>>>(a);
+  else
+    k_fused<float><<<grid, 128, 0, st>>>(a);
+}
 
 void launch_ibm_interp(const IbmArgs &a, int precision, cudaStream_t st) {
   if (a.nmark <= 0) return;

@@ -148,7 +148,13 @@ struct IbmArgs {
   int first;          // first iteration: Fm = 0 before adding
   double *force_acc;  // [solid][6]
   int reduce_force;   // accumulate -sum F dV and the torque
+  int4 *mk_base;      // [nmark] first stencil node (unwrapped x, y, z) and solid
+  void *mk_wts;       // T [nmark][4^dim] delta weights of the stencil points
 };
+// stencil bases and weights of every marker (after each geometry change)
+void launch_ibm_prepare(const IbmArgs &a, int precision, cudaStream_t st);
+// interpolation, direct force and spreading in one pass (single iteration)
+void launch_ibm_fused(const IbmArgs &a, int precision, cudaStream_t st);
 void launch_ibm_interp(const IbmArgs &a, int precision, cudaStream_t st);
 void launch_ibm_spread(const IbmArgs &a, int precision, cudaStream_t st);
 void launch_zero_band(const KArgs &a, int precision, cudaStream_t st);

@@ -51,7 +51,12 @@ SWEEP_SOURCES = ["paper_1906_05445_gb300/csrc/sweep_impl.cuh",
 TRAFFIC_FILE = "profiles/bulk_sweep_d3q19_mrt_fp32_128.md"
 
 
-def workload(precision=W.FP32):
+def workload(precision=W.FP32, kind="fixed"):
+    if kind == "moving":
+        base = dict(nx=256, ny=128, nz=128, radius=8.0, seed=1906, u=0.01, tau=0.6,
+                    precision=precision)
+        return [W.translating_sphere(scheme=W.BOUZIDI_QUAD, **base),
+                W.translating_sphere(scheme=W.IBM, **base)]
     base = dict(n=128, radius=12.0, seed=1906, tau=0.6, g=3.4e-8,
                 precision=precision, collision=W.MRT)
     return [W.fixed_sphere(scheme=W.BOUZIDI_QUAD, **base),
@@ -60,6 +65,15 @@ def workload(precision=W.FP32):
 
 def workload_config(problems, precision):
     p = problems[0]
+    if p.solids[0].velocity[0] != 0:
+        return {"workload": f"moving_sphere_{p.nx}x{p.ny}x{p.nz}_D3Q19_MRT_ibb_quadratic_refill+ibm",
+                "lattice": "D3Q19", "collision": "MRT", "nodes_per_lattice": p.nodes,
+                "lattices": len(problems), "radius": p.solids[0].radius,
+                "velocity": list(p.solids[0].velocity), "tau": p.tau,
+                "storage": {W.FP32: "fp32 f-w", W.FP64: "fp64", W.FP32_BF16: "bf16 f-w",
+                            W.FP32_FP16: "fp16 (f-w)*2^10"}[precision],
+                "schemes": ["bouzidi_quadratic+refill", "ibm_direct_forcing(peskin4, n_it=1)"],
+                "l2": "inputs larger than L2: 2 x 319 MB read + 2 x 319 MB written per step"}
     return {"workload": f"sphere_{p.nx}^3_D3Q19_MRT_ibb_quadratic+ibm_side_by_side",
             "lattice": "D3Q19", "collision": "MRT", "nodes_per_lattice": p.nodes,
             "lattices": len(problems), "radius": p.solids[0].radius,
@@ -247,7 +261,7 @@ def run_reference(args, rank, world):
 
 # ------------------------------------------------------------------ batch / serve
 BATCH_CFG = dict(count=8, r_min=3.0, r_max=8.0, tau=0.8, re_p=2.0, tol=1e-6,
-                 check_every=200, max_steps=100000)
+                 check_every=200, max_steps=200000)
 SERVE_CFG = dict(count=24, seed=11, rate_hz=40.0, min_2d=48, max_2d=160, min_3d=24,
                  max_3d=48, tau_range=(0.7, 1.0), tol=1e-5, check_every=200)
 
@@ -260,11 +274,13 @@ def run_batch_leg(lbm, stream):
     ps = W.convergence_batch(c["count"], tau=c["tau"], re_p=c["re_p"], r_min=c["r_min"],
                              r_max=c["r_max"])
     t0 = time.perf_counter()
-    seq_steps = []
+    seq_steps, seq_res = [], []
     for p in ps:
         lt = lbm.Lattice.from_problem(p, stream=stream)
         lt.init_equilibrium()
-        seq_steps.append(lt.run_to_steady(c["tol"], c["check_every"], c["max_steps"])[0])
+        k, r = lt.run_to_steady(c["tol"], c["check_every"], c["max_steps"])
+        seq_steps.append(k)
+        seq_res.append(r)
         lt.close()
     t_seq = time.perf_counter() - t0
     lats = [lbm.Lattice.from_problem(p, stream=stream) for p in ps]
@@ -282,6 +298,7 @@ def run_batch_leg(lbm, stream):
             "sequential_value": len(ps) / t_seq, "speedup": t_seq / t_batch,
             "batch_s": t_batch, "sequential_s": t_seq,
             "steps": [int(x) for x in steps], "sequential_steps": [int(x) for x in seq_steps],
+            "residuals": [float(x) for x in res], "sequential_residuals": [float(x) for x in seq_res],
             "converged": bool(all(r < c["tol"] for r in res)),
             "blocks_bulk_list": blocks,
             "stated_error": f"steady-state residual < {c['tol']} (every {c['check_every']} steps); "
@@ -321,7 +338,7 @@ def run_ours(args, rank, world, local):
     from paper_1906_05445_gb300 import lbm
     precision = {"fp32": W.FP32, "bf16": W.FP32_BF16, "fp16": W.FP32_FP16,
                  "fp64": W.FP64}[args.precision]
-    problems = workload(precision)
+    problems = workload(precision, args.workload)
     stream = torch.cuda.current_stream(device)
     lats = [lbm.Lattice.from_problem(p, stream=stream.cuda_stream) for p in problems]
     for lt in lats:
@@ -404,7 +421,7 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_sample(problems, steps_each=1)
     batch = serve_leg = None
-    if rank == 0 and world == 1 and not args.no_batch:
+    if rank == 0 and world == 1 and not args.no_batch and args.workload == "fixed":
         batch = run_batch_leg(lbm, stream.cuda_stream)
         serve_leg = run_serve_leg(stream.cuda_stream)
 
@@ -441,6 +458,9 @@ def main(argv=None):
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--precision", default="fp32", choices=["fp32", "bf16", "fp16", "fp64"])
     ap.add_argument("--no-cpu", action="store_true", help="skip the oracle CPU baseline")
+    ap.add_argument("--workload", default="fixed", choices=["fixed", "moving"],
+                    help="fixed: the 128^3 sphere (default); moving: the 256x128x128 "
+                         "translating sphere")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-solve and served-stream legs")
     args = ap.parse_args(argv)

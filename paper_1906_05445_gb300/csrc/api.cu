@@ -87,6 +87,8 @@ struct lbm_ctx {
   long long bulk_nodes = 0;              // plain fluid nodes at the last full build
   void *link_mem = nullptr;
   LinkArrays links{};
+  int *link_list = nullptr;
+  uint8_t *link_dir = nullptr;
   int *refill_node = nullptr;
   uint8_t *refill_sid = nullptr;
   // IBM
@@ -94,6 +96,7 @@ struct lbm_ctx {
   uint8_t *mk_sid = nullptr;
   int4 *mk_base = nullptr;  // stencil table (rebuilt with the geometry)
   void *mk_wts = nullptr;
+  bool markers_dirty = false;
   int nmark = 0;
   void *u_band = nullptr, *f_ibm = nullptr;
   // forces
@@ -347,8 +350,14 @@ lbm_status ensure_list_capacity(lbm_ctx *ctx, int list_cap, int link_cap, int re
   }
   if (link_cap > ctx->link_cap) {
     dfree(ctx, ctx->link_mem);
+    dfree(ctx, ctx->link_list);
+    dfree(ctx, ctx->link_dir);
     ctx->link_mem = nullptr;
+    ctx->link_list = nullptr;
+    ctx->link_dir = nullptr;
     const size_t lk = std::max(link_cap, 1);
+    TRY(dalloc(ctx, (void **)&ctx->link_list, sizeof(int) * lk));
+    TRY(dalloc(ctx, (void **)&ctx->link_dir, lk));
     const size_t per = 12 * ctx->tsz + 1;
     TRY(dalloc(ctx, &ctx->link_mem, per * lk + 64));
     char *p = (char *)ctx->link_mem;
@@ -390,6 +399,8 @@ GeomArgs geom_args(lbm_ctx *ctx) {
   g.list_mask = ctx->list_mask;
   g.list_link = ctx->list_link;
   g.list_cst = ctx->list_cst;
+  g.link_list = ctx->link_list;
+  g.link_dir = ctx->link_dir;
   g.list_cap = ctx->list_cap;
   g.link_cap = ctx->link_cap;
   g.links = ctx->links;
@@ -493,6 +504,7 @@ lbm_status build_markers(lbm_ctx *ctx) {
 }
 
 void ibm_prepare(lbm_ctx *ctx);
+void ibm_prepare(lbm_ctx *ctx, cudaStream_t s);
 
 lbm_status read_counts(lbm_ctx *ctx, int out[16]) {
   CK(cudaMemcpyAsync(out, ctx->counts, 16 * sizeof(int), cudaMemcpyDeviceToHost, ctx->st));
@@ -513,7 +525,7 @@ lbm_status rebuild_full(lbm_ctx *ctx) {
   g.track_new = 0;
   CK(cudaMemsetAsync(ctx->counts, 0, 16 * sizeof(int), ctx->st));
   launch_geometry(g, ctx->d.precision, ctx->st);
-  ctx->launches += 3;
+  ctx->launches += 4;
   int cnt[16];
   TRY(read_counts(ctx, cnt));
   const bool moving = any_moving(ctx);
@@ -536,7 +548,7 @@ lbm_status rebuild_full(lbm_ctx *ctx) {
   g.track_new = 0;
   CK(cudaMemsetAsync(ctx->counts, 0, 16 * sizeof(int), ctx->st));
   launch_geometry(g, ctx->d.precision, ctx->st);
-  ctx->launches += 3;
+  ctx->launches += 4;
   TRY(read_counts(ctx, cnt));
   if (cnt[3]) return fail(ctx, LBM_ERR_CAPACITY, "boundary list overflow during rebuild");
   ctx->list_count = moving ? -1 : cnt[0];
@@ -563,8 +575,8 @@ lbm_status rebuild_boxes(lbm_ctx *ctx) {
   CK(cudaMemsetAsync(ctx->counts, 0, 4 * sizeof(int), ctx->st));
   Timed tm(ctx, TK_GEOM, 0, ctx->st);
   launch_geometry(g, ctx->d.precision, ctx->st);
-  ctx->launches += 3;
-  ibm_prepare(ctx);
+  ctx->launches += 4;
+  ctx->markers_dirty = true;  // marker table: rebuilt by the IBM pre-pass
   return LBM_OK;
 }
 
@@ -600,17 +612,20 @@ IbmArgs ibm_args(lbm_ctx *ctx, double *acc) {
 }
 
 // stencil table of the markers at the geometry centres
-void ibm_prepare(lbm_ctx *ctx) {
+void ibm_prepare(lbm_ctx *ctx, cudaStream_t s) {
+  ctx->markers_dirty = false;
   if (ctx->scheme.scheme != LBM_IBM_DIRECT || ctx->nmark == 0) return;
-  launch_ibm_prepare(ibm_args(ctx, nullptr), ctx->d.precision, ctx->st);
+  launch_ibm_prepare(ibm_args(ctx, nullptr), ctx->d.precision, s);
   ctx->launches++;
 }
+void ibm_prepare(lbm_ctx *ctx) { ibm_prepare(ctx, ctx->st); }
 
 // IBM: unforced velocity at the band, n_it interpolation/force iterations,
 // spreading, and the solid's force (into the given record slot).
 void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStream_t s) {
   if (ctx->scheme.scheme != LBM_IBM_DIRECT || ctx->nmark == 0) return;
   Timed tm(ctx, TK_IBM, 0, s);
+  if (ctx->markers_dirty) ibm_prepare(ctx, s);  // moving solids: every step
   KArgs a = base_args(ctx);
   a.src = src;
   a.local_gather = local ? 1 : 0;
@@ -676,8 +691,6 @@ lbm_status step_once(lbm_ctx *ctx) {
     a.src = ctx->f[cur];
     a.dst = ctx->f[cur];
     sweep(ctx, OP_REFILL, a);
-    launch_clear_new(ctx->flags, ctx->counts, ctx->refill_node, ctx->refill_cap, ctx->st);
-    ctx->launches++;
   }
   ctx->slot = (ctx->slot + 1) % kHistCap;
   double *acc = force_slot(ctx, ctx->slot);

@@ -104,11 +104,11 @@ __global__ void __launch_bounds__(512) k_bulk_query(const KArgs a) {
   if (x >= a.nx) return;
   const long long n = x + (long long)a.nx * (y + (long long)a.ny * z);
   const uint8_t fl = a.flags[n];
-  if (fl & (uint8_t)~FL_NOG) return;
+  if (fl & (uint8_t)~(FL_NOG | FL_NEW)) return;
   double f[Lat<LAT>::Q];
   gather_pull<LAT, S, double>((const S *)a.src, a.fs, x, y, z, a.nx, a.ny, a.nz,
                               a.inv_scale, f);
-  const double gon = fl ? 0.0 : 1.0;
+  const double gon = (fl & FL_NOG) ? 0.0 : 1.0;
   write_fields<LAT, double>(a, n, f, gon * a.g[0], gon * a.g[1], gon * a.g[2]);
 }
 
@@ -254,6 +254,35 @@ template <typename T> __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
+// Lane-parallel collision (lane = direction, lanes >= Q carry fi = 0): Eq. 1
+// / Eq. 3 with Guo forcing as in collide(), the moments and the q moments of
+// MRT as warp reductions.  Returns f*_lane.
+template <int LAT, int CM, typename T>
+__device__ __forceinline__ T collide_lane(const KArgs &a, T fi, bool dir, int ex, int ey,
+                                          int ez, int cls, T w, T Fx, T Fy, T Fz) {
+  using L = Lat<LAT>;
+  const T drho = wsum<T>(fi);
+  const T jx = wsum<T>((T)ex * fi), jy = wsum<T>((T)ey * fi), jz = wsum<T>((T)ez * fi);
+  const T ux = jx + (T)0.5 * Fx, uy = jy + (T)0.5 * Fy, uz = jz + (T)0.5 * Fz;
+  const T uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
+  const T eu = (T)ex * ux + (T)ey * uy + (T)ez * uz;
+  const T eF = (T)ex * Fx + (T)ey * Fy + (T)ez * Fz;
+  const T feq = w * (drho + (T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * uu);
+  const T fb = w * ((T)3 * (eF - uF) + (T)9 * eu * eF);
+  const Coll<T> c = make_coll<LAT, T>(a);
+  T out = c.omc * fi + c.omega * feq + c.cforce * fb;
+  if constexpr (CM == CM_MRT_Q) {
+    const T v = dir ? fi - feq + (T)0.5 * fb : (T)0;
+    const T qf = L::D == 3 ? (T)(5 * cls - 9) : (T)(3 * cls - 5);
+    const T kq = c.ds[4] * (T)(1.0 / mnorm<LAT>(4));
+    const T mx = wsum<T>(qf * (T)ex * v), my = wsum<T>(qf * (T)ey * v);
+    T corr = qf * ((T)ex * mx + (T)ey * my);
+    if (L::D == 3) corr += qf * (T)ez * wsum<T>(qf * (T)ez * v);
+    out += kq * corr;
+  }
+  return out;
+}
+
 template <int LAT, int CM, typename S, typename T>
 __global__ void __launch_bounds__(256) k_list_warp(const KArgs a) {
   using L = Lat<LAT>;
@@ -299,25 +328,7 @@ __global__ void __launch_bounds__(256) k_list_warp(const KArgs a) {
     const uint8_t fl = a.flags[n];
     T Fx, Fy, Fz;
     node_force<T, T>(a, n, fl, Fx, Fy, Fz);
-    const T drho = wsum<T>(fi);
-    const T jx = wsum<T>((T)ex * fi), jy = wsum<T>((T)ey * fi), jz = wsum<T>((T)ez * fi);
-    const T ux = jx + (T)0.5 * Fx, uy = jy + (T)0.5 * Fy, uz = jz + (T)0.5 * Fz;
-    const T uu = ux * ux + uy * uy + uz * uz, uF = ux * Fx + uy * Fy + uz * Fz;
-    const T eu = (T)ex * ux + (T)ey * uy + (T)ez * uz;
-    const T eF = (T)ex * Fx + (T)ey * Fy + (T)ez * Fz;
-    const T feq = w * (drho + (T)3 * eu + (T)4.5 * eu * eu - (T)1.5 * uu);
-    const T fb = w * ((T)3 * (eF - uF) + (T)9 * eu * eF);
-    const Coll<T> c = make_coll<LAT, T>(a);
-    T out = c.omc * fi + c.omega * feq + c.cforce * fb;
-    if constexpr (CM == CM_MRT_Q) {
-      const T v = dir ? fi - feq + (T)0.5 * fb : (T)0;
-      const T qf = L::D == 3 ? (T)(5 * cls - 9) : (T)(3 * cls - 5);
-      const T kq = c.ds[4] * (T)(1.0 / mnorm<LAT>(4));
-      const T mx = wsum<T>(qf * (T)ex * v), my = wsum<T>(qf * (T)ey * v);
-      T corr = qf * ((T)ex * mx + (T)ey * my);
-      if (L::D == 3) corr += qf * (T)ez * wsum<T>(qf * (T)ez * v);
-      out += kq * corr;
-    }
+    const T out = collide_lane<LAT, CM, T>(a, fi, dir, ex, ey, ez, cls, w, Fx, Fy, Fz);
     if (dir) Store<S>::st((S *)a.dst + (long long)lane * a.fs + n, out, isc);
     // Eq. 17 on this node's cut links (first solid: deviation part here,
     // state-independent part from the geometry build)
@@ -388,6 +399,71 @@ __global__ void __launch_bounds__(256) k_list_warp(const KArgs a) {
     if (s0 >= 0) atomicAdd(a.force_acc + 6 * s0 + k, sum);
   }
 }
+
+template <int LAT, int CM, typename S, typename T>
+__device__ __forceinline__ void refill_node_warp(const KArgs &a, int t, int lane) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  constexpr unsigned long long PX = pack_dir<LAT>(0), PY = pack_dir<LAT>(1), PZ = pack_dir<LAT>(2);
+  const long long n = a.refill_node[t];
+  const int sidx = a.refill_sid[t];
+  int x, y, z;
+  node_xyz(n, a.nx, a.ny, x, y, z);
+  const int ex = (int)((PX >> (2 * lane)) & 3ull) - 1;
+  const int ey = (int)((PY >> (2 * lane)) & 3ull) - 1;
+  const int ez = (int)((PZ >> (2 * lane)) & 3ull) - 1;
+  const bool dir = lane < Q;
+  const S *src = (const S *)a.src;
+  const T isc = kisc<T>(a);
+  double rj = 0;
+  int cj = 0;
+  if (dir && lane > 0) {
+    const long long nb = wrap(x + ex, a.nx) +
+                         (long long)a.nx * (wrap(y + ey, a.ny) + (long long)a.ny * wrap(z + ez, a.nz));
+    if (a.sid[nb] == 0 && !(a.flags[nb] & FL_NEW)) {
+      rj = 1.0;
+      for (int k = 0; k < Q; k++) rj += (double)Store<S>::ld(src + (long long)k * a.fs + nb, isc);
+      cj = 1;
+    }
+  }
+  const double rs = wsum<double>(rj);
+  int cn = cj;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(0xffffffffu, cn, o);
+  const double rho = cn ? rs / cn : 1.0;
+  const SolidDev &b = a.solids.s[sidx];
+  double r[3] = {x - b.c[0], y - b.c[1], z - b.c[2]};
+  r[0] -= a.nx * round(r[0] / a.nx);
+  r[1] -= a.ny * round(r[1] / a.ny);
+  r[2] = (L::D == 2 || b.kind == 1) ? 0.0 : r[2] - a.nz * round(r[2] / a.nz);
+  double uw[3] = {b.U[0] + b.Om[1] * r[2] - b.Om[2] * r[1],
+                  b.U[1] + b.Om[2] * r[0] - b.Om[0] * r[2],
+                  b.U[2] + b.Om[0] * r[1] - b.Om[1] * r[0]};
+  if (L::D == 2) uw[2] = 0;
+  const int cls = ex * ex + ey * ey + ez * ez;
+  const double wd = cls == 0 ? L::w(0) : (cls == 1 ? L::w(1) : L::w(Q - 1));
+  const double eu = ex * uw[0] + ey * uw[1] + ez * uw[2];
+  const double uu = uw[0] * uw[0] + uw[1] * uw[1] + uw[2] * uw[2];
+  const T fi = dir ? (T)(wd * (rho - 1.0 + 3.0 * eu + 4.5 * eu * eu - 1.5 * uu)) : (T)0;
+  T Fx, Fy, Fz;
+  node_force<T, T>(a, n, a.flags[n], Fx, Fy, Fz);
+  const T out = collide_lane<LAT, CM, T>(a, fi, dir, ex, ey, ez, cls, (T)wd, Fx, Fy, Fz);
+  if (dir) Store<S>::st((S *)a.dst + (long long)lane * a.fs + n, out, isc);
+}
+
+// Refill with a warp per uncovered node: lane j sums the density of
+// neighbour x + e_j (if it was fluid before and after the move), then lane i
+// forms f^eq_i(rho_mean, u_w) and the node's collision runs lane-parallel.
+template <int LAT, int CM, typename S, typename T>
+__global__ void __launch_bounds__(256) k_refill_warp(const KArgs a) {
+  const int lane = threadIdx.x & 31;
+  int cnt = a.counts[2];
+  if (cnt > a.refill_cap) cnt = a.refill_cap;
+  const int stride = gridDim.x * (blockDim.x >> 5);
+  for (int t = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); t < cnt; t += stride)
+    refill_node_warp<LAT, CM, S, T>(a, t, lane);
+}
+
 
 // Local read of a pre-collision state: collide into dst (MODE 0) or write
 // fields (MODE 1).  One thread per node.
@@ -572,7 +648,12 @@ void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
     k_local<LAT, CM, S, double, T, 1><<<div_up(a.N, 256), 256, 0, st>>>(a);
     break;
   case OP_REFILL:
-    if (a.refill_cap > 0) k_refill<LAT, CM, S, T><<<div_up(a.refill_cap, 128), 128, 0, st>>>(a);
+    if (a.refill_cap > 0) {
+      if constexpr (CM != CM_MRT)
+        k_refill_warp<LAT, CM, S, T><<<std::min(div_up(a.refill_cap, 8), 64), 256, 0, st>>>(a);
+      else
+        k_refill<LAT, CM, S, T><<<div_up(a.refill_cap, 128), 128, 0, st>>>(a);
+    }
     break;
   case OP_BAND_VEL:
     if (a.list_cap > 0) k_band_vel<LAT, S, T><<<div_up(lc, 64), 64, 0, st>>>(a);

@@ -6,9 +6,11 @@
 // surface (FP64), and the rule's coefficients are stored per link.
 //
 // Work is done over boxes (the bounding boxes of the solids, or the whole
-// lattice) in three passes: flags (reads the previous solid ids), list
-// (claims each node once, appends list entries, links and refill entries),
-// commit (previous ids <- new ids).
+// lattice) in four passes: flags (reads the previous solid ids; a node
+// uncovered since the last build is marked FL_NEW until the next one), list
+// (claims each node once, appends list entries, cut links and refill
+// entries), links (one thread per cut link) and commit (previous ids <- new
+// ids).
 #include "lbm_device.cuh"
 #include "lbm_internal.h"
 
@@ -18,7 +20,12 @@ namespace {
 
 constexpr uint8_t FL_CLAIM = 0x80;
 
-__device__ __forceinline__ double mimage(double d, int L) { return d - L * round(d / L); }
+// nearest periodic image; the reciprocal replaces a division (the two can
+// only disagree for a separation within an ulp of half the period, where
+// both images are equally far and the solid tests below do not change)
+__device__ __forceinline__ double mimage(double d, int L) {
+  return d - L * round(d * (1.0 / L));
+}
 
 // separation of node (x,y,z) from the solid's axis/centre, nearest image;
 // z is dropped on 2D lattices and for cylinders along z
@@ -88,82 +95,52 @@ __global__ void k_geom_flags(const GeomArgs g, uint8_t *sid_new) {
   } else if (g.scheme == LBM_IBM_DIRECT) {
     if (s_in && !g.force_all) fl |= FL_NOG;
     for (int s = 0; s < g.solids.n; s++) {
+      // | |r| - R_L | <= band_w, without the square root
       double r[3];
       rel(g, g.solids.s[s], x, y, z, r);
-      const double dist = sqrt(norm2(r));
-      if (fabs(dist - g.solids.s[s].RL) <= g.band_w) fl |= FL_BAND;
+      const double r2 = norm2(r), RL = g.solids.s[s].RL;
+      const double lo = RL - g.band_w, hi = RL + g.band_w;
+      if (r2 <= hi * hi && (lo <= 0 || r2 >= lo * lo)) fl |= FL_BAND;
     }
   }
   g.flags[n] = fl;
   sid_new[n] = (uint8_t)s_in;
 }
 
-// Bounce-back coefficients of Sec. 2.2 (Eq. 9, Eq. 11, Eqs. 12-14 and their
-// two-point forms) with the fallback quadratic -> linear -> Eq. 9 when the
-// interpolation nodes x_ff / x_fff are not fluid.  Returns the rule used.
-__device__ int ibb_rule(int scheme, double q, bool ff, bool fff, double c[6]) {
-  for (int k = 0; k < 6; k++) c[k] = 0.0;
-  int s = scheme;
-  if (s == LBM_BOUZIDI_QUAD && !(ff && fff)) s = LBM_BOUZIDI_LIN;
-  if (s == LBM_YU_QUAD && !(ff && fff)) s = LBM_YU_LIN;
-  if ((s == LBM_BOUZIDI_LIN || s == LBM_YU_LIN) && !ff) s = LBM_BOUNCE_BACK;
-  const double tq = 2.0 * q;
-  if (s == LBM_BOUZIDI_QUAD) {
-    if (q < 0.5) {  // virtual point 1 - 2q between x_f and x_ff
-      c[0] = q * (tq + 1.0);
-      c[1] = (1.0 + tq) * (1.0 - tq);
-      c[2] = -q * (1.0 - tq);
-      c[5] = 1.0;
-    } else {        // bounce first, then interpolate x_t, x_ff, x_fff
-      c[0] = 1.0 / (q * (tq + 1.0));
-      c[5] = c[0];
-      c[3] = (tq - 1.0) / q;
-      c[4] = (1.0 - tq) / (tq + 1.0);
-    }
-  } else if (s == LBM_BOUZIDI_LIN) {
-    if (q < 0.5) {
-      c[0] = tq;
-      c[1] = 1.0 - tq;
-      c[5] = 1.0;
-    } else {
-      c[0] = 1.0 / tq;
-      c[5] = c[0];
-      c[3] = (tq - 1.0) / tq;
-    }
-  } else if (s == LBM_YU_QUAD) {
-    const double wall = 2.0 / ((1.0 + q) * (2.0 + q));
-    c[0] = q / (2.0 + q);                              // wall * q(q+1)/2
-    c[1] = 2.0 * (1.0 - q) / (2.0 + q);                // wall * (1+q)(1-q)
-    c[2] = -q * (1.0 - q) / ((1.0 + q) * (2.0 + q));   // wall * -q(1-q)/2
-    c[3] = 2.0 * q / (1.0 + q);
-    c[4] = -q / (2.0 + q);
-    c[5] = wall;
-  } else if (s == LBM_YU_LIN) {
-    const double wall = 1.0 / (1.0 + q);
-    c[0] = q * wall;
-    c[1] = (1.0 - q) * wall;
-    c[3] = q * wall;
-    c[5] = wall;
-  } else {
-    s = LBM_BOUNCE_BACK;
-    c[0] = 1.0;
-    c[5] = 1.0;
+// Warp-aggregated append: every lane of the warp calls it (want may be 0);
+// returns the lane's first slot in the counter's list.
+__device__ __forceinline__ int warp_append(int *counter, int want) {
+  const int lane = threadIdx.x & 31;
+  int incl = want;  // inclusive prefix over the warp
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int v = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += v;
   }
-  return s;
+  const int total = __shfl_sync(0xffffffffu, incl, 31);
+  int base = 0;
+  if (lane == 31 && total > 0) base = atomicAdd(counter, total);
+  base = __shfl_sync(0xffffffffu, base, 31);
+  return base + incl - want;
 }
 
-template <int LAT, typename T>
-__global__ void k_geom_list(const GeomArgs g, const uint8_t *sid_new) {
+// Node pass: cut-link masks, list entries and refill entries.  Every thread
+// of the grid reaches the warp-wide appends (no early return).
+template <int LAT>
+__global__ void __launch_bounds__(256) k_geom_list(const GeomArgs g, const uint8_t *sid_new) {
   using L = Lat<LAT>;
   const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= g.box_offset[g.nbox]) return;
-  int x, y, z;
-  const long long n = box_node(g, t, x, y, z);
-  const uint8_t fl = g.flags[n];
-  if (fl & FL_SOLID) return;
+  const bool valid = t < g.box_offset[g.nbox];
+  int x = 0, y = 0, z = 0;
+  long long n = 0;
+  uint8_t fl = FL_SOLID;
+  if (valid) {
+    n = box_node(g, t, x, y, z);
+    fl = g.flags[n];
+  }
   const bool ibb = g.scheme >= LBM_BOUNCE_BACK && g.scheme <= LBM_YU_QUAD;
   uint32_t mask = 0;
-  if (ibb) {
+  if (valid && !(fl & FL_SOLID) && ibb) {
 #pragma unroll
     for (int i = 1; i < L::Q; i++) {
       const long long src = wrap(x - L::ex(i), g.nx) +
@@ -174,13 +151,12 @@ __global__ void k_geom_list(const GeomArgs g, const uint8_t *sid_new) {
   }
   // IBM: only band nodes need the spread force; nodes inside the solid
   // that are not in the band run in the bulk sweep without external force
-  const bool listed = ibb ? mask != 0 : (fl & FL_BAND) != 0;
-  const bool refill = (fl & FL_NEW) != 0;
-  if (!listed && !refill) return;
+  bool listed = valid && !(fl & FL_SOLID) && (ibb ? mask != 0 : (fl & FL_BAND) != 0);
+  bool refill = valid && !(fl & FL_SOLID) && (fl & FL_NEW) != 0;
   // claim the node once even if it lies in several boxes
-  if (flag_or(g.flags, n, FL_CLAIM) & FL_CLAIM) return;
+  if ((listed || refill) && (flag_or(g.flags, n, FL_CLAIM) & FL_CLAIM)) listed = refill = false;
+  const int r = warp_append(&g.counts[2], refill ? 1 : 0);
   if (refill) {
-    const int r = atomicAdd(&g.counts[2], 1);
     if (r < g.refill_cap) {
       g.refill_node[r] = (int)n;
       g.refill_sid[r] = (uint8_t)(g.sid[n] - 1);
@@ -188,11 +164,11 @@ __global__ void k_geom_list(const GeomArgs g, const uint8_t *sid_new) {
       atomicOr(&g.counts[3], 1);
     }
   }
+  const int nl = listed ? __popc(mask) : 0;
+  const int idx = warp_append(&g.counts[0], listed ? 1 : 0);
+  const int lo = warp_append(&g.counts[1], nl);
   if (!listed) return;
   flag_or(g.flags, n, FL_LIST);
-  const int nl = __popc(mask);
-  const int idx = atomicAdd(&g.counts[0], 1);
-  const int lo = nl ? atomicAdd(&g.counts[1], nl) : 0;
   if (idx >= g.list_cap || lo + nl > g.link_cap) {
     atomicOr(&g.counts[3], 1);
     return;
@@ -200,70 +176,145 @@ __global__ void k_geom_list(const GeomArgs g, const uint8_t *sid_new) {
   g.list_node[idx] = (int)n;
   g.list_mask[idx] = mask;
   g.list_link[idx] = lo;
+  for (int c = 0; c < 6; c++) g.list_cst[(long long)c * g.list_cap + idx] = 0.0;
   int link = lo;
-  // state-independent part of the momentum exchange, -2 w_i e_i per cut link
-  // to the node's first solid, and its torque (FP64)
-  double cst[6] = {0, 0, 0, 0, 0, 0};
-  int first_solid = -1;
   for (int i = 1; i < L::Q; i++) {
     if (!((mask >> i) & 1u)) continue;
-    const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
-    const long long src = wrap(x - ex, g.nx) +
-                          (long long)g.nx * (wrap(y - ey, g.ny) + (long long)g.ny * wrap(z - ez, g.nz));
-    const int s = sid_new[src] - 1;
-    const SolidDev &b = g.solids.s[s];
-    double r[3];
-    rel(g, b, x, y, z, r);
-    const bool flat = g.lattice == LBM_D2Q9 || b.kind == LBM_CYLINDER_Z;
-    const double d[3] = {(double)-ex, (double)-ey, flat ? 0.0 : (double)-ez};
-    const double A = d[0] * d[0] + d[1] * d[1] + d[2] * d[2];
-    const double B = 2.0 * (r[0] * d[0] + r[1] * d[1] + r[2] * d[2]);
-    const double C = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] - b.R * b.R;
-    double q = 0.5;
-    if (A > 0) {
-      double disc = B * B - 4.0 * A * C;
-      if (disc < 0) disc = 0;
-      q = b.fluid_inside ? (-B + sqrt(disc)) / (2.0 * A) : (-B - sqrt(disc)) / (2.0 * A);
-    }
-    if (q > 1.0) q = 1.0;
-    if (q < 1e-12) q = 1e-12;
-    const long long nff = wrap(x + ex, g.nx) +
-                          (long long)g.nx * (wrap(y + ey, g.ny) + (long long)g.ny * wrap(z + ez, g.nz));
-    const long long nfff = wrap(x + 2 * ex, g.nx) +
-                           (long long)g.nx * (wrap(y + 2 * ey, g.ny) +
-                                              (long long)g.ny * wrap(z + 2 * ez, g.nz));
-    const bool ff = sid_new[nff] == 0;
-    const bool fff = ff && sid_new[nfff] == 0;
-    double c[6];
-    const int used = ibb_rule(g.scheme, q, ff, fff, c);
-    atomicAdd(&g.counts[4 + used], 1);
-    // wall point relative to the centre and the wall velocity there
-    const double arm[3] = {r[0] - q * ex, r[1] - q * ey, flat ? 0.0 : r[2] - q * ez};
-    double uw[3] = {b.U[0] + b.Om[1] * arm[2] - b.Om[2] * arm[1],
-                    b.U[1] + b.Om[2] * arm[0] - b.Om[0] * arm[2],
-                    b.U[2] + b.Om[0] * arm[1] - b.Om[1] * arm[0]};
-    if (g.lattice == LBM_D2Q9) uw[2] = 0;
-    const double eu = ex * uw[0] + ey * uw[1] + ez * uw[2];
-    for (int k = 0; k < 5; k++) ((T *)g.links.c[k])[link] = (T)c[k];
-    ((T *)g.links.mw)[link] = (T)(c[5] * 6.0 * L::w(i) * eu);  // c5 * 2 rho0 w_i e.u / cs2
-    for (int k = 0; k < 3; k++) {
-      ((T *)g.links.uw[k])[link] = (T)uw[k];
-      ((T *)g.links.arm[k])[link] = (T)arm[k];
-    }
-    g.links.sid[link] = (uint8_t)s;
-    if (first_solid < 0) first_solid = s;
-    if (s == first_solid) {
-      const double p[3] = {-2.0 * L::w(i) * ex, -2.0 * L::w(i) * ey, -2.0 * L::w(i) * ez};
-      cst[0] += p[0];
-      cst[1] += p[1];
-      cst[2] += p[2];
-      cst[3] += arm[1] * p[2] - arm[2] * p[1];
-      cst[4] += arm[2] * p[0] - arm[0] * p[2];
-      cst[5] += arm[0] * p[1] - arm[1] * p[0];
-    }
+    g.link_list[link] = idx;
+    g.link_dir[link] = (uint8_t)i;
     link++;
   }
-  for (int c = 0; c < 6; c++) g.list_cst[(long long)c * g.list_cap + idx] = cst[c];
+}
+
+// Bounce-back coefficients in the compute type (FP64 build: FP64).
+template <typename T>
+__device__ int ibb_rule_t(int scheme, T q, bool ff, bool fff, T c[6]) {
+  for (int k = 0; k < 6; k++) c[k] = (T)0;
+  int s = scheme;
+  if (s == LBM_BOUZIDI_QUAD && !(ff && fff)) s = LBM_BOUZIDI_LIN;
+  if (s == LBM_YU_QUAD && !(ff && fff)) s = LBM_YU_LIN;
+  if ((s == LBM_BOUZIDI_LIN || s == LBM_YU_LIN) && !ff) s = LBM_BOUNCE_BACK;
+  const T one = (T)1, two = (T)2, tq = two * q;
+  if (s == LBM_BOUZIDI_QUAD) {
+    if (q < (T)0.5) {  // virtual point 1 - 2q between x_f and x_ff
+      c[0] = q * (tq + one);
+      c[1] = (one + tq) * (one - tq);
+      c[2] = -q * (one - tq);
+      c[5] = one;
+    } else {           // bounce first, then interpolate x_t, x_ff, x_fff
+      c[0] = one / (q * (tq + one));
+      c[5] = c[0];
+      c[3] = (tq - one) / q;
+      c[4] = (one - tq) / (tq + one);
+    }
+  } else if (s == LBM_BOUZIDI_LIN) {
+    if (q < (T)0.5) {
+      c[0] = tq;
+      c[1] = one - tq;
+      c[5] = one;
+    } else {
+      c[0] = one / tq;
+      c[5] = c[0];
+      c[3] = (tq - one) / tq;
+    }
+  } else if (s == LBM_YU_QUAD) {
+    const T wall = two / ((one + q) * (two + q));
+    c[0] = q / (two + q);                                // wall * q(q+1)/2
+    c[1] = two * (one - q) / (two + q);                  // wall * (1+q)(1-q)
+    c[2] = -q * (one - q) / ((one + q) * (two + q));     // wall * -q(1-q)/2
+    c[3] = two * q / (one + q);
+    c[4] = -q / (two + q);
+    c[5] = wall;
+  } else if (s == LBM_YU_LIN) {
+    const T wall = one / (one + q);
+    c[0] = q * wall;
+    c[1] = (one - q) * wall;
+    c[3] = q * wall;
+    c[5] = wall;
+  } else {
+    s = LBM_BOUNCE_BACK;
+    c[0] = one;
+    c[5] = one;
+  }
+  return s;
+}
+
+// Link pass: one thread per cut link -- wall fraction (FP64), rule
+// coefficients, wall velocity, lever arm, and the node's state-independent
+// part of Eq. 17 (-2 w_i e_i for links to the node's first solid).
+template <int LAT, typename T>
+__global__ void __launch_bounds__(128) k_geom_links(const GeomArgs g, const uint8_t *sid_new) {
+  using L = Lat<LAT>;
+  const int link = blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = g.counts[1];
+  if (cnt > g.link_cap) cnt = g.link_cap;
+  if (link >= cnt) return;
+  const int idx = g.link_list[link];
+  const int i = g.link_dir[link];
+  const long long n = g.list_node[idx];
+  const uint32_t mask = g.list_mask[idx];
+  const int x = (int)(n % g.nx), y = (int)((n / g.nx) % g.ny), z = (int)(n / ((long long)g.nx * g.ny));
+  const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
+  const long long src = wrap(x - ex, g.nx) +
+                        (long long)g.nx * (wrap(y - ey, g.ny) + (long long)g.ny * wrap(z - ez, g.nz));
+  const int s = sid_new[src] - 1;
+  const SolidDev &b = g.solids.s[s];
+  double r[3];
+  rel(g, b, x, y, z, r);
+  const bool flat = g.lattice == LBM_D2Q9 || b.kind == LBM_CYLINDER_Z;
+  const double d[3] = {(double)-ex, (double)-ey, flat ? 0.0 : (double)-ez};
+  const int A = (int)(d[0] * d[0] + d[1] * d[1] + d[2] * d[2]);
+  const double B = 2.0 * (r[0] * d[0] + r[1] * d[1] + r[2] * d[2]);
+  const double C = r[0] * r[0] + r[1] * r[1] + r[2] * r[2] - b.R * b.R;
+  double q = 0.5;
+  if (A > 0) {
+    double disc = B * B - 4.0 * A * C;
+    if (disc < 0) disc = 0;
+    const double h = A == 1 ? 0.5 : (A == 2 ? 0.25 : 1.0 / 6.0);  // 1 / (2A)
+    q = b.fluid_inside ? (-B + sqrt(disc)) * h : (-B - sqrt(disc)) * h;
+  }
+  if (q > 1.0) q = 1.0;
+  if (q < 1e-12) q = 1e-12;
+  const long long nff = wrap(x + ex, g.nx) +
+                        (long long)g.nx * (wrap(y + ey, g.ny) + (long long)g.ny * wrap(z + ez, g.nz));
+  const long long nfff = wrap(x + 2 * ex, g.nx) +
+                         (long long)g.nx * (wrap(y + 2 * ey, g.ny) + (long long)g.ny * wrap(z + 2 * ez, g.nz));
+  const bool ff = sid_new[nff] == 0;
+  const bool fff = ff && sid_new[nfff] == 0;
+  T c[6];
+  ibb_rule_t<T>(g.scheme, (T)q, ff, fff, c);
+  // wall point relative to the centre and the wall velocity there
+  const T arm[3] = {(T)(r[0] - q * ex), (T)(r[1] - q * ey), flat ? (T)0 : (T)(r[2] - q * ez)};
+  T uw[3] = {(T)b.U[0] + (T)b.Om[1] * arm[2] - (T)b.Om[2] * arm[1],
+             (T)b.U[1] + (T)b.Om[2] * arm[0] - (T)b.Om[0] * arm[2],
+             (T)b.U[2] + (T)b.Om[0] * arm[1] - (T)b.Om[1] * arm[0]};
+  if (g.lattice == LBM_D2Q9) uw[2] = (T)0;
+  const T eu = (T)ex * uw[0] + (T)ey * uw[1] + (T)ez * uw[2];
+  for (int k = 0; k < 5; k++) ((T *)g.links.c[k])[link] = c[k];
+  ((T *)g.links.mw)[link] = c[5] * (T)(6.0 * L::w(i)) * eu;  // c5 * 2 rho0 w_i e.u / cs2
+  for (int k = 0; k < 3; k++) {
+    ((T *)g.links.uw[k])[link] = uw[k];
+    ((T *)g.links.arm[k])[link] = arm[k];
+  }
+  g.links.sid[link] = (uint8_t)s;
+  // the node's first cut link decides which solid its constant part goes to
+  const int first = __ffs(mask) - 1;
+  const long long src0 = wrap(x - L::ex(first), g.nx) +
+                         (long long)g.nx * (wrap(y - L::ey(first), g.ny) +
+                                            (long long)g.ny * wrap(z - L::ez(first), g.nz));
+  if (sid_new[src0] - 1 == s) {
+    const double w2 = -2.0 * L::w(i);
+    const double p[3] = {w2 * ex, w2 * ey, w2 * ez};
+    const double am[3] = {(double)arm[0], (double)arm[1], (double)arm[2]};
+    double *cst = g.list_cst;
+    const long long lc = g.list_cap;
+    atomicAdd(cst + 0 * lc + idx, p[0]);
+    atomicAdd(cst + 1 * lc + idx, p[1]);
+    atomicAdd(cst + 2 * lc + idx, p[2]);
+    atomicAdd(cst + 3 * lc + idx, am[1] * p[2] - am[2] * p[1]);
+    atomicAdd(cst + 4 * lc + idx, am[2] * p[0] - am[0] * p[2]);
+    atomicAdd(cst + 5 * lc + idx, am[0] * p[1] - am[1] * p[0]);
+  }
 }
 
 __global__ void k_geom_commit(const GeomArgs g, const uint8_t *sid_new) {
@@ -275,21 +326,7 @@ __global__ void k_geom_commit(const GeomArgs g, const uint8_t *sid_new) {
   g.flags[n] &= (uint8_t)~FL_CLAIM;
 }
 
-__global__ void k_clear_new(uint8_t *flags, const int *counts, const int *node, int cap) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int cnt = counts[2];
-  if (cnt > cap) cnt = cap;
-  if (t >= cnt) return;
-  flags[node[t]] &= (uint8_t)~FL_NEW;
-}
-
 }  // namespace
-
-void launch_clear_new(uint8_t *flags, const int *counts, const int *node, int cap,
-                      cudaStream_t st) {
-  if (cap <= 0) return;
-  k_clear_new<<<(cap + 127) / 128, 128, 0, st>>>(flags, counts, node, cap);
-}
 
 // sid_new lives right after sid in the same allocation (N bytes each, padded)
 void launch_geometry(const GeomArgs &g, int precision, cudaStream_t st) {
@@ -300,12 +337,20 @@ void launch_geometry(const GeomArgs &g, int precision, cudaStream_t st) {
   uint8_t *sid_new = g.sid + ((g.N + 15) / 16) * 16;
   k_geom_flags<<<grid, bs, 0, st>>>(g, sid_new);
   const bool dbl = precision == LBM_FP64;
-  if (g.lattice == LBM_D2Q9) {
-    if (dbl) k_geom_list<0, double><<<grid, bs, 0, st>>>(g, sid_new);
-    else k_geom_list<0, float><<<grid, bs, 0, st>>>(g, sid_new);
-  } else {
-    if (dbl) k_geom_list<1, double><<<grid, bs, 0, st>>>(g, sid_new);
-    else k_geom_list<1, float><<<grid, bs, 0, st>>>(g, sid_new);
+  if (g.lattice == LBM_D2Q9)
+    k_geom_list<0><<<grid, bs, 0, st>>>(g, sid_new);
+  else
+    k_geom_list<1><<<grid, bs, 0, st>>>(g, sid_new);
+  // one thread per link, up to the link capacity (the count is on the device)
+  if (g.link_cap > 0) {
+    const unsigned lg = (unsigned)((g.link_cap + 127) / 128);
+    if (g.lattice == LBM_D2Q9) {
+      if (dbl) k_geom_links<0, double><<<lg, 128, 0, st>>>(g, sid_new);
+      else k_geom_links<0, float><<<lg, 128, 0, st>>>(g, sid_new);
+    } else {
+      if (dbl) k_geom_links<1, double><<<lg, 128, 0, st>>>(g, sid_new);
+      else k_geom_links<1, float><<<lg, 128, 0, st>>>(g, sid_new);
+    }
   }
   k_geom_commit<<<grid, bs, 0, st>>>(g, sid_new);
 }

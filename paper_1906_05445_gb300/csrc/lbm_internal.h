@@ -118,6 +118,8 @@ struct GeomArgs {
   uint32_t *list_mask;
   int *list_link;
   double *list_cst;
+  int *link_list;     // [link_cap] list entry owning each link
+  uint8_t *link_dir;  // [link_cap] direction of each link
   int list_cap, link_cap;
   LinkArrays links;
   int *refill_node;
@@ -130,8 +132,6 @@ struct GeomArgs {
   long long box_offset[kMaxSolids + 1];
 };
 void launch_geometry(const GeomArgs &g, int precision, cudaStream_t st);
-void launch_clear_new(uint8_t *flags, const int *counts, const int *node, int cap,
-                      cudaStream_t st);
 
 // IBM (ibm.cu)
 struct IbmArgs {

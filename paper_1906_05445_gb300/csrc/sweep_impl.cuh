@@ -133,10 +133,10 @@ template <int LAT, int CM, typename S, typename T, int HINT>
 __global__ void __launch_bounds__(512) k_bulk_sweep(const KArgs a) {
   const unsigned n = blockIdx.x * blockDim.x + threadIdx.x;
   if (n >= (unsigned)a.N) return;
-  // plain fluid nodes; nodes inside an IBM solid (FL_NOG alone) also run
-  // here, without the external force
+  // plain fluid nodes; nodes inside an IBM solid (FL_NOG) also run here,
+  // without the external force, and so do nodes refilled this step (FL_NEW)
   const uint8_t fl = a.flags[n];
-  if (fl & (uint8_t)~FL_NOG) return;
+  if (fl & (uint8_t)~(FL_NOG | FL_NEW)) return;
   const unsigned yz = n / (unsigned)a.nx;
   const int x = (int)(n - yz * (unsigned)a.nx);
   const int z = (int)(yz / (unsigned)a.ny);
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(512) k_bulk_sweep(const KArgs a) {
   T f[Lat<LAT>::Q];
   gather_pull<LAT, S, T, (HINT & 1)>((const S *)a.src, a.fs, x, y, z, a.nx, a.ny, a.nz, isc, f);
   const Coll<T> c = make_coll<LAT, T>(a);
-  const T gon = fl ? (T)0 : (T)1;
+  const T gon = (fl & FL_NOG) ? (T)0 : (T)1;
   collide<LAT, CM, T>(f, gon * kg<T>(a, 0), gon * kg<T>(a, 1), gon * kg<T>(a, 2), c);
   scatter<LAT, S, T, (HINT & 2) != 0>((S *)a.dst, a.fs, n, isc, f);
 }

@@ -46,7 +46,8 @@ from paper_1906_05445_gb300 import workloads as W  # noqa: E402
 METRIC = "D3Q19 MLUPS"
 UNIT = "MLUPS"
 BYTES_PER_NODE = {W.FP64: 304, W.FP32: 152, W.FP32_BF16: 76, W.FP32_FP16: 76}
-SWEEP_SOURCES = ["paper_1906_05445_gb300/csrc/sweep_impl.cuh",
+SWEEP_SOURCES = ["paper_1906_05445_gb300/csrc/sweep_vec.cuh",
+                 "paper_1906_05445_gb300/csrc/sweep_impl.cuh",
                  "paper_1906_05445_gb300/csrc/lbm_device.cuh"]
 TRAFFIC_FILE = "profiles/bulk_sweep_d3q19_mrt_fp32_128.md"
 
@@ -346,8 +347,10 @@ def run_ours(args, rank, world, local):
     for _ in range(args.warmup):
         for lt in lats:
             lt.step(1)
+    # the timed region times the bulk sweeps (the roofline's kernel) with
+    # CUDA events on their stream; the other kinds get their own short pass
     for lt in lats:
-        lt.set_timing(True)
+        lt.set_timing(lbm.TIME_BULK)
     launches0 = sum(lt.info().kernel_launches for lt in lats)
     sampler = ClockSampler(local)
     sampler.start()
@@ -377,9 +380,18 @@ def run_ours(args, rank, world, local):
     achieved = per_launch_bytes / (ms / max(nl, 1) / 1e3) / 1e9
     peaks, peak_kind = measured_peaks()
     peak = float(peaks["hbm_gbs"])
-    kt = {}
-    for name, k in (("bulk", lbm.TK_BULK), ("boundary_list", lbm.TK_LIST), ("ibm", lbm.TK_IBM)):
-        kt[name] = [round(lt.kernel_time(k)[0] / max(args.steps, 1), 5) for lt in lats]
+    # per-kind breakdown over a shorter pass with every kind timed
+    kt_steps = max(min(args.steps // 5, 500), 1)
+    for lt in lats:
+        lt.set_timing(lbm.TIME_ALL)
+    for _ in range(kt_steps):
+        for lt in lats:
+            lt.step(1)
+    torch.cuda.synchronize(device)
+    kt = {"steps": kt_steps}
+    for name, k in (("bulk", lbm.TK_BULK), ("boundary_list", lbm.TK_LIST), ("ibm", lbm.TK_IBM),
+                    ("geometry", lbm.TK_GEOM)):
+        kt[name] = [round(lt.kernel_time(k)[0] / kt_steps, 5) for lt in lats]
     for lt in lats:
         lt.set_timing(False)
     traffic = recorded_traffic() if precision == W.FP32 else None
@@ -435,7 +447,7 @@ def run_ours(args, rank, world, local):
                 "data": "synthetic", "config": workload_config(problems, precision),
                 "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                              "frac": achieved / peak, "traffic": traffic,
-                             "kernel": "k_bulk_sweep<D3Q19,MRT,float>",
+                             "kernel": "k_bulk_vec<D3Q19,MRT-q,storage,2 words>",
                              "bytes_per_node": bpn, "nodes_per_launch": nodes / max(nl, 1),
                              "launch_ms": ms / max(nl, 1), "peak_kind": peak_kind + " hbm_gbs"},
                 "kernel_ms_per_step": kt,

@@ -217,10 +217,13 @@ lbm_status lbm_device_field(lbm_ctx *ctx, int which, void **dptr,
 lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size);
 lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size);
 
-/* Per-kernel device timing with CUDA events on the context's stream.
- * kernel: 0 bulk sweep, 1 boundary-node sweep, 2 IBM (all kernels),
- * 3 geometry.  Totals since the last reset, in ms, with launch counts and
- * the number of node updates done by those launches. */
+/* Per-kernel device timing with CUDA events on the stream each kernel runs
+ * on.  kernel: 0 bulk sweep, 1 boundary-node sweep, 2 IBM (all kernels),
+ * 3 geometry.  enable: 0 off, 1 every kind, otherwise a mask with bit
+ * (kernel + 1) set for each kind to time (each timed launch adds two event
+ * records; timing only the bulk sweep, enable = 2, disturbs the step least).
+ * Totals since the last reset, in ms, with launch counts and the number of
+ * node updates done by those launches. */
 lbm_status lbm_set_timing(lbm_ctx *ctx, int enable);
 lbm_status lbm_get_kernel_time(lbm_ctx *ctx, int kernel, double *total_ms,
                                int64_t *launches, int64_t *node_updates);
@@ -262,9 +265,10 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * scratch buffer (the simulation state is untouched).  While in a batch the
  * contexts must be stepped only through the batch; their queries remain
  * valid.  lbm_batch_destroy gives the contexts their streams back (it does
- * not destroy them).  cuda_stream is kept for reference only: the batch runs
- * on private streams, so lbm_batch_step returns with work in flight and the
- * contexts' queries (which synchronise their streams) wait for it.
+ * not destroy them).  The batch runs on private streams but is ordered on
+ * cuda_stream: lbm_batch_step and lbm_batch_run_to_steady start after the
+ * work already queued there, and work queued there afterwards (an event, a
+ * copy) waits for them; the contexts' queries wait for them as well.
  * Stepping captures one step pair of every lattice with static solids into
  * a CUDA graph whose per-lattice chains are independent branches, and
  * replays it: two steps of the whole batch per launch.  Lattices with

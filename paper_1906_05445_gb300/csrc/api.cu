@@ -64,6 +64,9 @@ struct lbm_ctx {
   int bulk_block = 128;
   int list_block = 256;
   int cache_hints = 0;
+  int bulk_mode = 1;
+  int bulk_vec_words = 0;
+  int bulk_vec_packed = -1;
   int coll_mode = 0;  // CM_BGK, CM_MRT or CM_MRT_Q
   cudaStream_t st = 0;
   // auxiliary high-priority stream: the boundary-node sweep and the IBM
@@ -118,7 +121,7 @@ struct lbm_ctx {
   // collision constants
   double omega = 0, ds[19] = {0}, s_bulk = 0, nu = 0, inv_scale = 1;
   // timing
-  bool timing = false;
+  int timing = 0;  // bit k + 1: kernel kind k is timed
   struct Pending {
     cudaEvent_t a, b;
     int kind;
@@ -196,14 +199,16 @@ struct Timed {
   long long nodes;
   cudaStream_t s;
   cudaEvent_t a = nullptr;
-  Timed(lbm_ctx *c, int k, long long n, cudaStream_t stream) : ctx(c), kind(k), nodes(n), s(stream) {
-    if (ctx->timing) {
+  bool on;
+  Timed(lbm_ctx *c, int k, long long n, cudaStream_t stream)
+      : ctx(c), kind(k), nodes(n), s(stream), on(((c->timing >> (k + 1)) & 1) != 0) {
+    if (on) {
       a = take_event(ctx);
       cudaEventRecord(a, s);
     }
   }
   ~Timed() {
-    if (ctx->timing) {
+    if (on) {
       cudaEvent_t b = take_event(ctx);
       cudaEventRecord(b, s);
       ctx->pending.push_back({a, b, kind, nodes});
@@ -261,6 +266,9 @@ KArgs base_args(lbm_ctx *ctx) {
   a.fs = ctx->fs;
   a.bulk_block = ctx->bulk_block;
   a.cache_hints = ctx->cache_hints;
+  a.bulk_mode = ctx->bulk_mode;
+  a.bulk_vec_words = ctx->bulk_vec_words;
+  a.bulk_vec_packed = ctx->bulk_vec_packed;
   a.list_block = ctx->list_block;
   a.flags = ctx->flags;
   a.omega = ctx->omega;
@@ -887,6 +895,9 @@ lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_st
       if (b >= 32 && b <= 512 && b % 32 == 0) ctx->bulk_block = b;
     }
     if (const char *e = getenv("LBM_CACHE_HINTS")) ctx->cache_hints = atoi(e) & 3;
+    if (const char *e = getenv("LBM_BULK_MODE")) ctx->bulk_mode = atoi(e);
+    if (const char *e = getenv("LBM_VEC_WORDS")) ctx->bulk_vec_words = atoi(e);
+    if (const char *e = getenv("LBM_VEC_PACKED")) ctx->bulk_vec_packed = atoi(e);
     if (const char *e = getenv("LBM_MRT_GENERAL"))
       if (atoi(e) && ctx->coll_mode == CM_MRT_Q) ctx->coll_mode = CM_MRT;
   }
@@ -1268,7 +1279,7 @@ lbm_status lbm_set_timing(lbm_ctx *ctx, int enable) {
   if (!ctx) return LBM_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
-  ctx->timing = enable != 0;
+  ctx->timing = enable == 1 ? ~0 : (enable & ~1);
   for (int k = 0; k < TK_COUNT; k++) {
     ctx->tk_ms[k] = 0;
     ctx->tk_launch[k] = ctx->tk_nodes[k] = 0;
@@ -1374,6 +1385,7 @@ struct lbm_batch {
   std::vector<cudaStream_t> own_st;    // private stream per lattice
   std::vector<cudaEvent_t> ev_done;
   cudaEvent_t ev_origin = nullptr;
+  cudaEvent_t ev_user = nullptr;       // orders the batch after the caller's stream
   cudaStream_t origin = nullptr;       // private stream the graph runs on
   cudaStream_t user = nullptr;         // stream given at creation
   std::vector<char> active;
@@ -1471,7 +1483,8 @@ lbm_status capture(lbm_batch *b) {
   b->graph_slot.assign(n, 0);
   struct Saved {
     int cur, slot;
-    bool prev_local, timing;
+    bool prev_local;
+    int timing;
     long long step, launches, records;
   };
   std::vector<Saved> saved(n);
@@ -1483,7 +1496,7 @@ lbm_status capture(lbm_batch *b) {
     lbm_ctx *c = b->ctx[i];
     if (!b->active[i] || any_moving(c)) continue;
     saved[i] = {c->cur, c->slot, c->prev_local, c->timing, c->step, c->launches, c->records};
-    c->timing = false;
+    c->timing = 0;
     b->graph_cur[i] = c->cur;
     cudaStreamWaitEvent(c->st, b->ev_origin, 0);
     st = step_once(c);
@@ -1548,6 +1561,21 @@ bool graph_valid(const lbm_batch *b) {
     if (want && b->ctx[i]->cur != b->graph_cur[i]) return false;
   }
   return true;
+}
+
+// The batch's private streams start after the work already queued on the
+// caller's stream, and the caller's stream waits for all of them at the end.
+lbm_status enter(lbm_batch *b) {
+  BCK(cudaEventRecord(b->ev_user, b->user));
+  for (lbm_ctx *c : b->ctx) BCK(cudaStreamWaitEvent(c->st, b->ev_user, 0));
+  return LBM_OK;
+}
+lbm_status leave(lbm_batch *b) {
+  for (size_t i = 0; i < b->ctx.size(); i++) {
+    BCK(cudaEventRecord(b->ev_done[i], b->ctx[i]->st));
+    BCK(cudaStreamWaitEvent(b->user, b->ev_done[i], 0));
+  }
+  return LBM_OK;
 }
 
 lbm_status batch_advance(lbm_batch *b, int nsteps) {
@@ -1639,6 +1667,7 @@ lbm_status lbm_batch_create(lbm_batch **out, lbm_ctx *const *ctxs, int n, void *
   b->in_graph.assign(n, 0);
   b->graph_cur.assign(n, 0);
   cudaError_t e = cudaEventCreateWithFlags(&b->ev_origin, cudaEventDisableTiming);
+  if (e == cudaSuccess) e = cudaEventCreateWithFlags(&b->ev_user, cudaEventDisableTiming);
   if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&b->origin, cudaStreamNonBlocking);
   for (int i = 0; i < n && e == cudaSuccess; i++) {
     lbm_ctx *c = b->ctx[i];
@@ -1696,6 +1725,7 @@ void lbm_batch_destroy(lbm_batch *b) {
     if (i < b->ev_done.size() && b->ev_done[i]) cudaEventDestroy(b->ev_done[i]);
   }
   if (b->ev_origin) cudaEventDestroy(b->ev_origin);
+  if (b->ev_user) cudaEventDestroy(b->ev_user);
   if (b->origin) {
     cudaStreamSynchronize(b->origin);
     cudaStreamDestroy(b->origin);
@@ -1705,8 +1735,11 @@ void lbm_batch_destroy(lbm_batch *b) {
 
 lbm_status lbm_batch_step(lbm_batch *b, int nsteps) {
   if (!b || nsteps < 0) return LBM_ERR_ARG;
-  lbm_status s = batch_advance(b, nsteps);
+  lbm_status s = enter(b);
+  if (s == LBM_OK) s = batch_advance(b, nsteps);
+  const lbm_status s2 = leave(b);
   if (s != LBM_OK) return s;
+  if (s2 != LBM_OK) return s2;
   BCK(cudaGetLastError());
   return LBM_OK;
 }
@@ -1725,7 +1758,14 @@ lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int check_every, in
     b->active[i] = 1;
     b->steps_done[i] = 0;
     b->residual[i] = INFINITY;
-    TRY(velocity_to(c, c->u_snap));
+  }
+  {
+    const lbm_status s = enter(b);
+    if (s != LBM_OK) return s;
+  }
+  for (int i = 0; i < n; i++) {
+    lbm_ctx *ctx = b->ctx[i];
+    TRY(velocity_to(ctx, ctx->u_snap));
   }
   int left = n;
   lbm_status result = LBM_OK;
@@ -1770,7 +1810,8 @@ lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int check_every, in
     if (steps_done) steps_done[i] = b->steps_done[i];
     if (residual) residual[i] = b->residual[i];
   }
-  return result;
+  const lbm_status s2 = leave(b);
+  return result != LBM_OK ? result : s2;
 }
 
 lbm_status lbm_batch_info(lbm_batch *b, int i, int *bulk_block, int *list_block, int64_t *graph_launches) {

@@ -6,6 +6,7 @@
 #pragma once
 
 #include "sweep_impl.cuh"
+#include "sweep_vec.cuh"
 
 namespace lbm {
 
@@ -606,6 +607,28 @@ __global__ void __launch_bounds__(256) k_fill_eq(const KArgs a) {
 // ---------------------------------------------------------------- launch
 inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 
+// The vector bulk sweep: W words per thread and direction (bulk_vec_words 2
+// or 4; 0 = 2) and the node-pair collision packed (bulk_vec_packed 1) or
+// node by node (0); -1 picks what measured fastest on the 128^3 sphere
+// lattice: 8-byte vectors, node by node for FP32 storage, packed for 16-bit
+// storage.  Returns false where nx or the direction stride is not a
+// multiple of the V nodes of a vector.
+template <int LAT, int CM, typename S, int W>
+bool launch_bulk_vec_w(const KArgs &a, int want, bool packed, cudaStream_t st) {
+  constexpr int V = W * VecS<S>::per_word;
+  if (a.nx % V != 0 || a.fs % V != 0) return false;
+  const int nt = (int)(a.N / V);
+  if (packed) k_bulk_vec<LAT, CM, S, W, true><<<div_up(nt, want), want, 0, st>>>(a);
+  else k_bulk_vec<LAT, CM, S, W, false><<<div_up(nt, want), want, 0, st>>>(a);
+  return true;
+}
+template <int LAT, int CM, typename S>
+bool launch_bulk_vec(const KArgs &a, int want, cudaStream_t st) {
+  const bool packed = a.bulk_vec_packed >= 0 ? a.bulk_vec_packed != 0 : sizeof(S) == 2;
+  if (a.bulk_vec_words == 4) return launch_bulk_vec_w<LAT, CM, S, 4>(a, want, packed, st);
+  return launch_bulk_vec_w<LAT, CM, S, 2>(a, want, packed, st);
+}
+
 template <int LAT, int CM, typename S, typename T>
 void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
   const int want = a.bulk_block > 0 ? a.bulk_block : 128;
@@ -614,6 +637,9 @@ void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
   const int lc = a.list_cap > 0 ? a.list_cap : 1;
   switch (op) {
   case OP_BULK_SWEEP:
+    if constexpr (std::is_same<T, float>::value && CM != CM_MRT) {
+      if (a.bulk_mode == 1 && launch_bulk_vec<LAT, CM, S>(a, want, st)) break;
+    }
     switch (a.cache_hints & 3) {
     case 1: k_bulk_sweep<LAT, CM, S, T, 1><<<div_up(a.N, want), want, 0, st>>>(a); break;
     case 2: k_bulk_sweep<LAT, CM, S, T, 2><<<div_up(a.N, want), want, 0, st>>>(a); break;

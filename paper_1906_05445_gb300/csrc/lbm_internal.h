@@ -79,6 +79,11 @@ struct KArgs {
   int bulk_block;    // threads per block of the bulk sweep (multiple of 32)
   int cache_hints;   // bulk sweep: bit 0 evict-first loads, bit 1 evict-first stores
   int list_block;    // threads per block of the boundary-node sweep (32, 64 or 128)
+  int bulk_mode;       // bulk sweep: 0 one node per thread, 1 vectors of nodes per thread
+                       // (where nx and the direction stride allow)
+  int bulk_vec_words;  // vector sweep: 32-bit words per thread and direction (2 or 4; 0 = 2)
+  int bulk_vec_packed; // vector sweep: 1 packed FP32x2 collision of node pairs, 0 node by
+                       // node, -1 by storage type
 };
 
 // kernel families timed by lbm_set_timing

@@ -30,6 +30,9 @@ SPHERE, CYLINDER_Z = 0, 1
 (SCHEME_NONE, BOUNCE_BACK, BOUZIDI_LIN, BOUZIDI_QUAD, YU_LIN, YU_QUAD,
  IBM_DIRECT) = range(7)
 TK_BULK, TK_LIST, TK_IBM, TK_GEOM = range(4)
+# lbm_set_timing masks: every kind, or bit (kind + 1) per kind
+TIME_ALL = 1
+TIME_BULK, TIME_LIST, TIME_IBM, TIME_GEOM = (2 << k for k in range(4))
 
 
 class lbm_lattice_desc(C.Structure):

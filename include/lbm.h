@@ -71,12 +71,12 @@ enum { LBM_SPHERE = 0, LBM_CYLINDER_Z = 1 };
 /* no-slip schemes (Sec. 2.1 and Sec. 2.2 of the paper) */
 enum {
   LBM_SCHEME_NONE = 0,    /* solids ignored: periodic box */
-  LBM_BOUNCE_BACK = 1,    /* Eq. 9 */
+  LBM_BOUNCE_BACK = 1,    /* Eq. 10 */
   LBM_BOUZIDI_LIN = 2,    /* two-point form of Eq. 11 */
   LBM_BOUZIDI_QUAD = 3,   /* Eq. 11 */
   LBM_YU_LIN = 4,         /* two-point form of Eqs. 12-14 */
   LBM_YU_QUAD = 5,        /* Eqs. 12-14 (the combined Eq. 15) */
-  LBM_IBM_DIRECT = 6      /* direct-forcing IBM, Eqs. 5-10 */
+  LBM_IBM_DIRECT = 6      /* direct-forcing IBM, Eqs. 4-9 */
 };
 /* fields for lbm_device_field */
 enum { LBM_FIELD_F_POST = 0, LBM_FIELD_FLAGS = 1 };
@@ -118,7 +118,7 @@ typedef struct {
   int fluid_inside;
 } lbm_solid_desc;
 
-/* Scheme.  For LBM_IBM_DIRECT: ibm_iters >= 1 forcing iterations (Eq. 10
+/* Scheme.  For LBM_IBM_DIRECT: ibm_iters >= 1 forcing iterations (Eq. 9
  * applied to the spread force), ibm_retraction = R_d (markers at R - R_d, or
  * R + R_d for an enclosing wall), ibm_marker_density = markers per unit
  * surface area (per unit length in 2D), 0 -> 1. */
@@ -182,7 +182,7 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, int check_every,
 /* Fields at the current time (synchronous), 0 at solid nodes:
  * density [nodes]; velocity [d][nodes] with the half-force correction;
  * strain rate [d(d+1)/2][nodes] from non-equilibrium moments (Sec. 3.1,
- *   Eq. 27 generalised), order xx, yy, xy (2D) / xx, yy, zz, xy, yz, xz (3D);
+ *   Eq. 19 generalised), order xx, yy, xy (2D) / xx, yy, zz, xy, yz, xz (3D);
  * stress = -c_s^2 rho I + 2 rho0 nu S, same order. */
 lbm_status lbm_get_density(lbm_ctx *ctx, double *host_out, size_t n);
 lbm_status lbm_get_velocity(lbm_ctx *ctx, double *host_out, size_t n);

@@ -9,14 +9,14 @@
  * Readings of passages where the paper is silent (all listed in the design
  * notes of the repository):
  *  - equilibrium: incompressible form w_i[rho + rho0(3e.u + 4.5(e.u)^2 -
- *    1.5u^2)] with u = (j + F dt/2)/rho0 (the paper uses rho0 in Eqs. 9-17);
+ *    1.5u^2)] with u = (j + F dt/2)/rho0 (the paper uses rho0 in Eqs. 10-17);
  *  - MRT basis: Lallemand-Luo (D2Q9) and d'Humieres et al. (D3Q19)
  *    polynomial rows, m_eq = M f_eq, forcing Psi = (I - S/2) M Fbar, i.e.
  *    Guo's term in moment space (the inverse design cited in Sec. 2.1);
  *  - linear Bouzidi / Yu rules: two-point versions of the constructions that
  *    give Eq. 11 and Eqs. 12-14; Eq. 15 is composed from Eqs. 12-14 (its
  *    printed second coefficient does not sum to one);
- *  - missing interpolation neighbours: quadratic -> linear -> Eq. 9;
+ *  - missing interpolation neighbours: quadratic -> linear -> Eq. 10;
  *  - refilling: equilibrium at the mean density of neighbours that were
  *    fluid before and after the move, at the local wall velocity.
  *    "parity unpinned": the paper gives no formula for this step.
@@ -130,7 +130,7 @@ void ora_mrt_default_rates(int lattice, double tau, double *s) {
     s[k] = moment_kind(lattice, k) == 'q' ? sq : snu;
 }
 
-/* Incompressible equilibrium (reading: the paper's rho0 in Eqs. 9-17). */
+/* Incompressible equilibrium (reading: the paper's rho0 in Eqs. 10-17). */
 void ora_equilibrium(int lattice, double rho, const double u[3], double *feq) {
   int Q = ora_q(lattice), e[MAXQ * 3];
   double w[MAXQ];
@@ -256,7 +256,7 @@ void ora_collide(int lattice, int collision, double tau, const double *rates,
  *                + c3 f_i(x_ff,t+1) + c4 f_i(x_fff,t+1)
  *                + c5 * 2 rho0 w_i (e_i.u_w)/cs2,
  * with f_i(x_ff,t+1) = f*_i(x_f) and f_i(x_fff,t+1) = f*_i(x_ff).
- * Eq. 9 (simple), Eq. 11 (Bouzidi quadratic, both branches), Eqs. 12-14
+ * Eq. 10 (simple), Eq. 11 (Bouzidi quadratic, both branches), Eqs. 12-14
  * composed (Yu quadratic); the linear rules are the two-point versions of the
  * same constructions (named in Sec. 3.3, not printed). */
 int ora_ibb_coeffs(int scheme, double q, int have_ff, int have_fff,
@@ -314,7 +314,7 @@ int ora_ibb_coeffs(int scheme, double q, int have_ff, int have_fff,
     c[5] = bw;
     break;
   }
-  default: /* Eq. 9 */
+  default: /* Eq. 10 */
     s = ORA_BB;
     c[0] = 1;
     c[5] = 1;
@@ -600,7 +600,7 @@ static void wall_velocity(const solid_t *b, const double r[3], double uw[3]) {
   uw[2] = b->U[2] + b->Om[0] * r[1] - b->Om[1] * r[0];
 }
 
-/* ---- immersed boundary (Sec. 2.1, Eqs. 5-10) ---- */
+/* ---- immersed boundary (Sec. 2.1, Eqs. 4-9) ---- */
 static double delta_w(int d, const double r[3]) {
   double v = ora_phi(r[0]) * ora_phi(r[1]);
   return d == 3 ? v * ora_phi(r[2]) : v;
@@ -655,8 +655,8 @@ void ora_ibm_spread(int d, int nx, int ny, int nz, double *f, int n,
  * interpolate the unforced velocity (external half force only, no IBM half
  * force) to the markers, F = rho0 (U^d - U~)/dt (Eq. 7), spread it (Eq. 8);
  * extra iterations re-interpolate u~ + f dt/rho0 and add the correction
- * (Eq. 10 applied to the spread force).  Force and torque on the solid are
- * minus the sum of marker forces times dV (Eq. B.7 / Sec. 3.1). */
+ * (Eq. 9 applied to the spread force).  Force and torque on the solid are
+ * minus the sum of marker forces times dV (Eq. 45 / Sec. 3.1). */
 static void ibm_forces(ora_sim *s) {
   long N = s->N;
   int d = s->d;
@@ -912,7 +912,7 @@ void ora_velocity(ora_sim *s, double *u) {
 }
 
 /* Strain rate from the non-equilibrium second moment with the forcing
- * correction (Sec. 3.1, Eq. 27 for D2Q9 MRT; the same Chapman-Enskog
+ * correction (Sec. 3.1, Eq. 19 for D2Q9 MRT; the same Chapman-Enskog
  * relation written for the deviatoric (rate s_nu) and trace (rate s_b)
  * parts on either lattice):
  *   P = Pi_neq + (F u + u F)/2,

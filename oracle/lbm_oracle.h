@@ -39,12 +39,12 @@ extern "C" {
 #define ORA_CYLINDER_Z 1 /* infinite cylinder along z */
 /* no-slip schemes */
 #define ORA_NONE 0
-#define ORA_BB 1            /* simple bounce-back, Eq. 9 */
+#define ORA_BB 1            /* simple bounce-back, Eq. 10 */
 #define ORA_BOUZIDI_LIN 2   /* linear analogue of Eq. 11 */
 #define ORA_BOUZIDI_QUAD 3  /* Eq. 11 */
 #define ORA_YU_LIN 4        /* linear analogue of Eqs. 12-14 */
 #define ORA_YU_QUAD 5       /* Eqs. 12-14 (combined: Eq. 15, corrected) */
-#define ORA_IBM 6           /* direct-forcing IBM, Sec. 2.1 (Eqs. 5-10) */
+#define ORA_IBM 6           /* direct-forcing IBM, Sec. 2.1 (Eqs. 4-9) */
 
 typedef struct ora_sim ora_sim;
 

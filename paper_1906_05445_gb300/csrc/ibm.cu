@@ -153,7 +153,7 @@ __device__ __forceinline__ void spread_marker(const IbmArgs &a, int m, int lane,
   }
 }
 
-// force on the solid, minus the marker forces (Sec. 3.1, Eq. B.7), reduced
+// force on the solid, minus the marker forces (Sec. 3.1, Eq. 45), reduced
 // per block in FP64
 __device__ __forceinline__ void reduce_solid_force(const IbmArgs &a, bool active, int lane,
                                                    int warp, const Marker &k, const double F[3],

@@ -110,7 +110,7 @@ def test_couette_fp64_other_rules(scheme):
 
 @pytest.mark.parametrize("iters,rd", [(1, 0.0), (3, 0.3)])
 def test_fixed_sphere_ibm_fp64(iters, rd):
-    """Direct-forcing IBM (Eqs. 5-10): band velocity, interpolation with
+    """Direct-forcing IBM (Eqs. 4-9): band velocity, interpolation with
     Peskin's kernel, force, spreading, forced sweep; force on the solid."""
     p = W.fixed_sphere(26, 6.1, seed=13, tau=0.7, g=2e-4, scheme=W.IBM,
                        precision=W.FP64, collision=W.MRT, steps=20,
@@ -211,7 +211,7 @@ def test_sphere_across_periodic_wrap_and_tiny_lattices():
 
 def test_fallback_rules_and_link_counts():
     """Two close spheres leave links whose x_ff / x_fff are solid: the
-    rules fall back to linear and to Eq. 9 exactly as in the oracle."""
+    rules fall back to linear and to Eq. 10 exactly as in the oracle."""
     p = W.Problem("gap", W.D3Q19, 30, 20, 20, 0.75, W.MRT, W.FP64, (3e-4, 0, 0),
                   [W.Solid(W.SPHERE, (9.3, 10.2, 9.7), 5.1),
                    W.Solid(W.SPHERE, (20.6, 9.9, 10.3), 5.2)], W.BOUZIDI_QUAD, 12)

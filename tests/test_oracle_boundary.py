@@ -3,12 +3,12 @@ mathematics fix:
 
 * interpolated bounce-back (Sec. 2.2): every rule is an interpolation, so it
   is exact on polynomial data of its degree along the link; the Bouzidi rules
-  reduce to Eq. 9 at q = 1/2; Eq. 15 composed from Eqs. 12-14;
+  reduce to Eq. 10 at q = 1/2; Eq. 15 composed from Eqs. 12-14;
 * Peskin's delta function (Eq. 6): the discrete moment identities it was
   built for;
 * interpolation (Eq. 5) and spreading (Eq. 8) are adjoint;
 * Appendix B: one forcing step on a kinked linear profile leaves the error
-  of Eq. B.9, first order in the grid spacing;
+  of Eq. 43, first order in the grid spacing;
 * the momentum exchange of Eq. 17 and the IBM force balance the fluid's
   momentum change exactly, step by step.
 """
@@ -142,7 +142,7 @@ def test_interp_spread_adjoint_and_exact_for_linear(oracle, d):
 
 
 def kink_error(oracle, h, slope_fluid, slope_solid, Xw=5.37, rows=8):
-    """One direct-forcing step (Eqs. 5, 7, 8, 10) on u(x) = a (x - Xw) for
+    """One direct-forcing step (Eqs. 5, 7, 8, 9) on u(x) = a (x - Xw) for
     x > Xw and b (x - Xw) for x < Xw sampled at spacing h; markers on a line
     x = Xw (one per grid row, so the y-sum of phi is exactly one)."""
     nx = int(round(16 / h))
@@ -157,12 +157,12 @@ def kink_error(oracle, h, slope_fluid, slope_solid, Xw=5.37, rows=8):
     Ut = oracle.ibm_interp(2, shape, u, Xl)          # Eq. 5 (grid units)
     F = 0.0 - Ut                                      # Eq. 7, U^d = 0
     f = oracle.ibm_spread(2, shape, F, Xl, np.ones(rows))
-    du = f[0].reshape(rows, nx)[0]                    # Eq. 10: u + f dt
+    du = f[0].reshape(rows, nx)[0]                    # Eq. 9: u + f dt
     return x, du
 
 
 def test_appendix_b_kink_error_is_first_order(oracle):
-    """Eq. B.9: du_j = -phi_j c (du/dx|fluid - du/dx|solid), c = sum over the
+    """Eq. 43: du_j = -phi_j c (du/dx|fluid - du/dx|solid), c = sum over the
     fluid-side nodes of phi_j (x_j - X) (a first-order length)."""
     a, b = 1.0, -0.5
     errs = []

@@ -1,7 +1,7 @@
 """Pins of whole oracle runs against the closed forms the paper uses:
-steady circular Couette flow (Appendix A, Eq. A.3) and its torque, the
-transient pipe flow (Eq. 20), the convergence orders stated in Sec. 3.1 and
-Sec. 3.3, and the strain rate from non-equilibrium moments (Eq. 27)."""
+steady circular Couette flow (Appendix A, Eq. 31) and its torque, the
+transient pipe flow (Eq. 28), the convergence orders stated in Sec. 3.1 and
+Sec. 3.3, and the strain rate from non-equilibrium moments (Eq. 19)."""
 import json
 import os
 
@@ -70,7 +70,7 @@ def couette_errors(oracle, p, tol=1e-9, max_steps=60000):
 
 def test_couette_c1_profile_and_torque(oracle):
     """The 64x64 D2Q9 case run from rest for 5000 steps with linear Bouzidi
-    bounce-back reaches the Eq. A.3 profile and the analytic torque."""
+    bounce-back reaches the Eq. 31 profile and the analytic torque."""
     p = W.couette_2d()
     s, (i1, i2) = couette_sim(oracle, p)
     s.step(p.steps)
@@ -148,7 +148,7 @@ def pipe_error(oracle, scheme, R, steps, tau=0.8, g=1e-6, coll=1, nz=4):
 
 
 def test_transient_pipe_flow(oracle):
-    """Eq. 20 (Bessel series) at an early time and at steady state."""
+    """Eq. 28 (Bessel series) at an early time and at steady state."""
     assert pipe_error(oracle, W.BOUZIDI_QUAD, 6.3, 150) < 1.5e-2
     assert pipe_error(oracle, W.BOUZIDI_QUAD, 6.3, 2500) < 1e-2
 
@@ -162,7 +162,7 @@ def test_pipe_ibb_second_order(oracle):
 
 def test_couette_strain_rate(oracle):
     """S_xy etc. from non-equilibrium moments against the analytic strain of
-    Eq. A.3: S_r_theta = -A / r^2."""
+    Eq. 31: S_r_theta = -A / r^2."""
     p = W.couette_2d(scheme=W.BOUZIDI_QUAD)
     err, _, s = couette_errors(oracle, p, tol=1e-10)
     S = s.strain_rate()[:, 0]
@@ -180,7 +180,7 @@ def test_couette_strain_rate(oracle):
 
 
 def test_strain_rate_matches_d2q9_moment_form(oracle):
-    """For D2Q9 MRT without force, Eq. 27 expresses the strain rate through
+    """For D2Q9 MRT without force, Eq. 19 expresses the strain rate through
     the non-equilibrium energy (e), normal-stress (p_xx) and shear-stress
     (p_xy) moments with their own rates; the oracle's tensor form must give
     the same numbers for distinct s_e, s_n = s_c."""

@@ -231,30 +231,58 @@ def oracle_sample(problems, steps_each=2):
                       f"({units} node updates, {secs:.1f} s, FP64, single thread)"}
 
 
+REFERENCE_BUDGET_S = 150.0
+PRECISIONS = {"fp32": W.FP32, "bf16": W.FP32_BF16, "fp16": W.FP32_FP16, "fp64": W.FP64}
+
+
 def run_reference(args, rank, world):
+    """The oracle as the reference arm: rank 0 only, on the host.  Each timed
+    step is one oracle step of one lattice of the workload, alternating the
+    bounce-back and the IBM lattice; where K full-size steps would not end
+    within a few minutes, each step runs on a cube of the same geometry
+    scaled down (sphere radius / edge kept) so that the whole run takes about
+    REFERENCE_BUDGET_S seconds."""
     if rank != 0:
         return
     problems = workload()
-    cpu = oracle_sample(problems, steps_each=1)
-    # the timed reference arm: K steps, each a bounded sample of one step on
-    # one lattice (alternating IBB / IBM)
-    sims = [make_oracle(p) for p in problems]
+    # calibrate the oracle's node-update rate on a small lattice
+    cal = make_oracle(W.fixed_sphere(32, 3.0, seed=1906, scheme=W.BOUZIDI_QUAD))
+    t0 = time.perf_counter()
+    cal.step(1)
+    rate = 32 ** 3 / max(time.perf_counter() - t0, 1e-6)
+    cal.close()
+    per_step = REFERENCE_BUDGET_S / max(args.steps + args.warmup, 1)
+    full = problems[0].nx
+    edge = int(min(full, max(16, round((rate * per_step) ** (1.0 / 3.0)))))
+    edge -= edge % 2
+    if edge < full:
+        r = problems[0].solids[0].radius * edge / full
+        sample = [W.fixed_sphere(edge, r, seed=1906, scheme=p.scheme, precision=W.FP64,
+                                 g=p.g[0] * (full / edge) ** 2) for p in problems]
+    else:
+        sample = problems
+    sims = [make_oracle(p) for p in sample]
     for k in range(args.warmup):
         sims[k % 2].step(1)
     t0 = time.perf_counter()
     units = 0
     for k in range(args.steps):
         sims[k % 2].step(1)
-        units += problems[k % 2].nodes
+        units += sample[k % 2].nodes
     secs = time.perf_counter() - t0
+    for o in sims:
+        o.close()
     value = units / secs / 1e6
-    cpu["value"] = value
-    cpu["sample"] = (f"{args.steps} timed steps alternating the two 128^3 lattices, one lattice "
-                     f"per step, FP64 oracle on one host thread")
+    what = "the two full-size lattices" if edge >= full else \
+        f"{edge}^3 samples of the two lattices (sphere radius scaled with the edge)"
+    cpu = {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+           "sample": f"{args.steps} timed steps alternating {what}, one lattice per step, "
+                     f"FP64 oracle on one host thread ({units} node updates, {secs:.1f} s)"}
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": secs / args.steps * 1e3,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(problems, W.FP64),
+            # the same config line as the GPU arm (the oracle computes in FP64)
+            "data": "synthetic", "config": workload_config(problems, PRECISIONS[args.precision]),
             "cpu_baseline": cpu,
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -337,8 +365,7 @@ def run_ours(args, rank, world, local):
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=device)
     from paper_1906_05445_gb300 import lbm
-    precision = {"fp32": W.FP32, "bf16": W.FP32_BF16, "fp16": W.FP32_FP16,
-                 "fp64": W.FP64}[args.precision]
+    precision = PRECISIONS[args.precision]
     problems = workload(precision, args.workload)
     stream = torch.cuda.current_stream(device)
     lats = [lbm.Lattice.from_problem(p, stream=stream.cuda_stream) for p in problems]

@@ -869,6 +869,8 @@ lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_st
   {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    // high priority: the boundary and IBM kernels start with the bulk sweep
+    // (at the default priority they start late and the join waits on them)
     if (cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, hi) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {

@@ -618,8 +618,9 @@ bool launch_bulk_vec_w(const KArgs &a, int want, bool packed, cudaStream_t st) {
   constexpr int V = W * VecS<S>::per_word;
   if (a.nx % V != 0 || a.fs % V != 0) return false;
   const int nt = (int)(a.N / V);
-  if (packed) k_bulk_vec<LAT, CM, S, W, true><<<div_up(nt, want), want, 0, st>>>(a);
-  else k_bulk_vec<LAT, CM, S, W, false><<<div_up(nt, want), want, 0, st>>>(a);
+  const int grid = div_up(nt, want);
+  if (packed) k_bulk_vec<LAT, CM, S, W, true><<<grid, want, 0, st>>>(a);
+  else k_bulk_vec<LAT, CM, S, W, false><<<grid, want, 0, st>>>(a);
   return true;
 }
 template <int LAT, int CM, typename S>

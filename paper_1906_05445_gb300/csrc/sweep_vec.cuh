@@ -280,17 +280,17 @@ template <int V> __device__ __forceinline__ void ld_flags(const uint8_t *p, uint
 }
 
 // ---------------------------------------------------------------- kernel
-// A node is updated here when its flag byte has no bit but FL_NOG / FL_NEW;
-// the other nodes of a vector (boundary-list nodes, solid nodes) are loaded
-// and computed but not stored, since the boundary-node kernel writes them.
+// Thread t updates the vector of nodes [V t, V t + V).  A node is updated
+// when its flag byte has no bit but FL_NOG / FL_NEW; the other nodes of a
+// vector (boundary-list nodes, solid nodes) are loaded and computed but not
+// stored, since the boundary-node kernel writes them.  Every lane of the
+// warp calls this (threads past the end with t >= nt), for the shuffles.
 template <int LAT, int CM, typename S, int W, bool PACKED>
-__global__ void __launch_bounds__(256) k_bulk_vec(const KArgs a) {
+__device__ __forceinline__ void bulk_vec_update(const KArgs &a, unsigned t, unsigned nt) {
   using L = Lat<LAT>;
   using VS = VecS<S>;
   constexpr int Q = L::Q, V = W * VS::per_word, NP = V / 2;
   static_assert(V % 2 == 0, "nodes are collided in pairs");
-  const unsigned nt = (unsigned)a.N / V;
-  const unsigned t = blockIdx.x * blockDim.x + threadIdx.x;
   const bool valid = t < nt;
   // threads past the end still take part in the lane shuffles (on node 0)
   const unsigned n0 = valid ? t * V : 0u;
@@ -400,6 +400,15 @@ __global__ void __launch_bounds__(256) k_bulk_vec(const KArgs a) {
       });
     }
   }
+}
+
+// One thread per vector.  (A persistent grid walking the lattice measured
+// slower: it holds more registers and leaves the boundary kernels less room.)
+template <int LAT, int CM, typename S, int W, bool PACKED>
+__global__ void __launch_bounds__(256) k_bulk_vec(const KArgs a) {
+  constexpr int V = W * VecS<S>::per_word;
+  bulk_vec_update<LAT, CM, S, W, PACKED>(a, blockIdx.x * blockDim.x + threadIdx.x,
+                                         (unsigned)a.N / V);
 }
 
 }  // namespace lbm

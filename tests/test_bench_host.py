@@ -3,6 +3,7 @@ ranks (max-over-ranks time, weak scaling) with a 2-rank gloo group, the
 nvidia-smi sample parser and the traffic/roofline bookkeeping."""
 import os
 import socket
+import time
 
 import pytest
 import torch.multiprocessing as mp
@@ -78,3 +79,22 @@ def test_workload_is_the_128_cube_sphere():
     assert p[0].solids[0].radius == 12.0 and p[0].collision == 1
     cfg = bench.workload_config(p, p[0].precision)
     assert "128^3" in cfg["workload"] and cfg["lattices"] == 2
+
+
+def test_reference_arm_is_bounded(monkeypatch, capsys):
+    """--impl reference times the oracle on the host on samples sized so the
+    whole run stays within the budget; it prints one JSON line with the
+    benchmark's metric and config."""
+    import json
+    monkeypatch.setattr(bench, "REFERENCE_BUDGET_S", 1.0)
+
+    class A:
+        steps, warmup, precision = 4, 1, "fp32"
+    t0 = time.perf_counter()
+    bench.run_reference(A, 0, 1)
+    assert time.perf_counter() - t0 < 60
+    line = json.loads(capsys.readouterr().out.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["metric"] == bench.METRIC
+    assert line["value"] > 0 and line["cpu_baseline"]["cores"] == 1
+    assert line["config"] == bench.workload_config(bench.workload(), bench.W.FP32)
+    assert "^3 samples" in line["cpu_baseline"]["sample"]

@@ -220,11 +220,13 @@ lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size);
 /* Per-kernel device timing with CUDA events on the stream each kernel runs
  * on.  kernel: 0 bulk sweep, 1 boundary-node sweep, 2 IBM (all kernels),
  * 3 geometry.  enable: 0 off, 1 every kind, otherwise a mask with bit
- * (kernel + 1) set for each kind to time (each timed launch adds two event
- * records; timing only the bulk sweep, enable = 2, disturbs the step least).
- * Totals since the last reset, in ms, with launch counts and the number of
- * node updates done by those launches. */
-lbm_status lbm_set_timing(lbm_ctx *ctx, int enable);
+ * (kernel + 1) set for each kind to time.  every >= 1: only the launches of
+ * steps whose index is a multiple of `every` are timed.  Each timed launch
+ * adds two event records to its stream, which cost the step a few
+ * microseconds, so timing only the bulk sweep (enable = 2) on a sample of
+ * steps disturbs the step least.  Totals since the last reset, in ms, with
+ * launch counts and the number of node updates done by the timed launches. */
+lbm_status lbm_set_timing(lbm_ctx *ctx, int enable, int every);
 lbm_status lbm_get_kernel_time(lbm_ctx *ctx, int kernel, double *total_ms,
                                int64_t *launches, int64_t *node_updates);
 

@@ -122,6 +122,7 @@ struct lbm_ctx {
   double omega = 0, ds[19] = {0}, s_bulk = 0, nu = 0, inv_scale = 1;
   // timing
   int timing = 0;  // bit k + 1: kernel kind k is timed
+  int timing_every = 1;  // time the launches of every n-th step
   struct Pending {
     cudaEvent_t a, b;
     int kind;
@@ -201,7 +202,8 @@ struct Timed {
   cudaEvent_t a = nullptr;
   bool on;
   Timed(lbm_ctx *c, int k, long long n, cudaStream_t stream)
-      : ctx(c), kind(k), nodes(n), s(stream), on(((c->timing >> (k + 1)) & 1) != 0) {
+      : ctx(c), kind(k), nodes(n), s(stream),
+        on(((c->timing >> (k + 1)) & 1) != 0 && c->step % c->timing_every == 0) {
     if (on) {
       a = take_event(ctx);
       cudaEventRecord(a, s);
@@ -1277,11 +1279,12 @@ lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size) {
   return LBM_OK;
 }
 
-lbm_status lbm_set_timing(lbm_ctx *ctx, int enable) {
-  if (!ctx) return LBM_ERR_ARG;
+lbm_status lbm_set_timing(lbm_ctx *ctx, int enable, int every) {
+  if (!ctx || every < 1) return LBM_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->st));
   resolve_timing(ctx);
   ctx->timing = enable == 1 ? ~0 : (enable & ~1);
+  ctx->timing_every = every;
   for (int k = 0; k < TK_COUNT; k++) {
     ctx->tk_ms[k] = 0;
     ctx->tk_launch[k] = ctx->tk_nodes[k] = 0;

@@ -93,7 +93,7 @@ def _load():
         "lbm_device_field": (st, [vp, i, C.POINTER(vp), C.POINTER(sz), C.POINTER(sz)]),
         "lbm_save": (st, [vp, vp, C.POINTER(sz)]),
         "lbm_load": (st, [vp, vp, sz]),
-        "lbm_set_timing": (st, [vp, i]),
+        "lbm_set_timing": (st, [vp, i, i]),
         "lbm_get_kernel_time": (st, [vp, i, dp, C.POINTER(C.c_int64), C.POINTER(C.c_int64)]),
         "lbm_get_velocity_noalloc": (st, [vp, dp, sz]),
         "lbm_batch_create": (st, [C.POINTER(vp), C.POINTER(vp), i, vp, i]),
@@ -288,8 +288,10 @@ class Lattice:
         buf = C.create_string_buffer(data, len(data))
         self._check(lbm_load(self.h, C.cast(buf, C.c_void_p), len(data)))
 
-    def set_timing(self, on=True):
-        self._check(lbm_set_timing(self.h, int(on)))
+    def set_timing(self, on=True, every=1):
+        """on: False, True (every kind) or a TIME_* mask; every: time only
+        the launches of every n-th step."""
+        self._check(lbm_set_timing(self.h, int(on), int(every)))
 
     def kernel_time(self, kernel=TK_BULK):
         ms, nl, nn = C.c_double(), C.c_int64(), C.c_int64()

@@ -630,6 +630,13 @@ void ibm_prepare(lbm_ctx *ctx, cudaStream_t s) {
 }
 void ibm_prepare(lbm_ctx *ctx) { ibm_prepare(ctx, ctx->st); }
 
+// Whether ibm_prepass launches the band-velocity kernel, which clears the
+// step's force record before the IBM kernels accumulate into it.
+bool ibm_zeroes_record(const lbm_ctx *ctx) {
+  const int lc = ctx->list_count >= 0 ? std::min(ctx->list_count, ctx->list_cap) : ctx->list_cap;
+  return ctx->scheme.scheme == LBM_IBM_DIRECT && ctx->nmark > 0 && lc > 0;
+}
+
 // IBM: unforced velocity at the band, n_it interpolation/force iterations,
 // spreading, and the solid's force (into the given record slot).
 void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStream_t s) {
@@ -639,6 +646,7 @@ void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStr
   KArgs a = base_args(ctx);
   a.src = src;
   a.local_gather = local ? 1 : 0;
+  a.force_acc = acc;  // cleared by the band-velocity kernel
   sweep(ctx, OP_BAND_VEL, a, s);
   IbmArgs ib = ibm_args(ctx, acc);
   const int iters = std::max(1, ctx->scheme.ibm_iters);
@@ -713,7 +721,9 @@ lbm_status step_once(lbm_ctx *ctx) {
   // f*(t) and write disjoint nodes of f*(t+1)
   CK(cudaEventRecord(ctx->ev_fork, ctx->st));
   CK(cudaStreamWaitEvent(ctx->aux, ctx->ev_fork, 0));
-  CK(cudaMemsetAsync(acc, 0, sizeof(double) * kMaxSolids * 6, ctx->aux));
+  // the IBM band-velocity kernel clears the record itself (one launch fewer
+  // on the IBM lattice's critical chain); otherwise a memset does
+  if (!ibm_zeroes_record(ctx)) CK(cudaMemsetAsync(acc, 0, sizeof(double) * kMaxSolids * 6, ctx->aux));
   ibm_prepass(ctx, ctx->f[cur], false, acc, ctx->aux);
   {
     Timed tm(ctx, TK_LIST, ctx->list_count >= 0 ? ctx->list_count : 0, ctx->aux);

@@ -546,6 +546,9 @@ template <int LAT, typename S, typename T>
 __global__ void __launch_bounds__(64) k_band_vel(const KArgs a) {
   using L = Lat<LAT>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  // this step's force record, accumulated by the IBM kernels that follow on
+  // the same stream, starts at zero
+  if (a.force_acc && t < 6 * kMaxSolids) a.force_acc[t] = 0.0;
   int cnt = a.counts[0];
   if (cnt > a.list_cap) cnt = a.list_cap;
   if (t >= cnt) return;

@@ -98,3 +98,13 @@ def test_reference_arm_is_bounded(monkeypatch, capsys):
     assert line["value"] > 0 and line["cpu_baseline"]["cores"] == 1
     assert line["config"] == bench.workload_config(bench.workload(), bench.W.FP32)
     assert "^3 samples" in line["cpu_baseline"]["sample"]
+
+
+def test_all_cores_oracle_baseline():
+    """The all-cores baseline runs the unchanged oracle in spawned processes
+    (one lattice each, started together) and reports the processes used."""
+    ps = [bench.W.fixed_sphere(24, 3.0, seed=3, scheme=s, precision=bench.W.FP64)
+          for s in (bench.W.BOUZIDI_QUAD, bench.W.IBM)]
+    r = bench.oracle_sample_all_cores(ps, procs=2)
+    assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
+    assert "2 processes" in r["sample"]

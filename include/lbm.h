@@ -118,15 +118,26 @@ typedef struct {
   int fluid_inside;
 } lbm_solid_desc;
 
+/* delta-function kernels of the IBM (Sec. 3.1 compares the first three) */
+enum {
+  LBM_DELTA_PESKIN4 = 0, /* Peskin's 4-point kernel, Eq. 6 (default) */
+  LBM_DELTA_ROMA3 = 1,   /* Roma, Peskin & Berger's 3-point kernel */
+  LBM_DELTA_LINEAR2 = 2, /* 2-point linear kernel */
+  LBM_DELTA_COSINE4 = 3  /* 4-point cosine kernel (Appendix B) */
+};
+
 /* Scheme.  For LBM_IBM_DIRECT: ibm_iters >= 1 forcing iterations (Eq. 9
  * applied to the spread force), ibm_retraction = R_d (markers at R - R_d, or
  * R + R_d for an enclosing wall), ibm_marker_density = markers per unit
- * surface area (per unit length in 2D), 0 -> 1. */
+ * surface area (per unit length in 2D), 0 -> 1, ibm_kernel = LBM_DELTA_*
+ * (zero-initialised descriptors get Peskin's kernel).  An unknown kernel is
+ * LBM_ERR_ARG. */
 typedef struct {
   int scheme;
   int ibm_iters;
   double ibm_retraction;
   double ibm_marker_density;
+  int ibm_kernel;
 } lbm_scheme_desc;
 
 typedef struct {

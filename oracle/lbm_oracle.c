@@ -330,6 +330,31 @@ double ora_phi(double r) {
   return (3 - 2 * a + sqrt(1 + 4 * a - 4 * r * r)) / 8;
 }
 
+/* The one-dimensional kernels compared in Sec. 3.1 (and the cosine kernel
+ * named in Appendix B):
+ *  - Peskin's 4-point kernel, Eq. 6;
+ *  - Roma, Peskin & Berger's 3-point kernel: (1 + sqrt(1 - 3 r^2)) / 3 for
+ *    |r| <= 1/2, (5 - 3|r| - sqrt(1 - 3 (1 - |r|)^2)) / 6 for
+ *    1/2 <= |r| <= 3/2, 0 beyond;
+ *  - the 2-point linear kernel 1 - |r| for |r| <= 1;
+ *  - the 4-point cosine kernel (1 + cos(pi r / 2)) / 4 for |r| <= 2.
+ * Every support lies inside the 4-point window from floor(X) - 1. */
+double ora_phi_kernel(int kernel, double r) {
+  double a = fabs(r);
+  switch (kernel) {
+  case ORA_DELTA_ROMA3:
+    if (a >= 1.5) return 0;
+    if (a <= 0.5) return (1 + sqrt(1 - 3 * r * r)) / 3;
+    return (5 - 3 * a - sqrt(1 - 3 * (1 - a) * (1 - a))) / 6;
+  case ORA_DELTA_LINEAR2:
+    return a >= 1 ? 0 : 1 - a;
+  case ORA_DELTA_COSINE4:
+    return a >= 2 ? 0 : (1 + cos(3.14159265358979323846 * r / 2)) / 4;
+  default:
+    return ora_phi(r);
+  }
+}
+
 /* ------------------------------------------------------------------ */
 typedef struct {
   int kind, fluid_inside;
@@ -355,7 +380,7 @@ struct ora_sim {
   double *usnap;               /* [3][N] */
   int nsol;
   solid_t sol[MAXS];
-  int scheme, ibm_iters;
+  int scheme, ibm_iters, ibm_kernel;
   double retraction, density;
   long steps;
   long link_counts[7];
@@ -415,6 +440,7 @@ ora_sim *ora_create(int lattice, int nx, int ny, int nz, double tau,
   s->usnap = (double *)calloc((size_t)3 * s->N, sizeof(double));
   s->scheme = ORA_NONE;
   s->ibm_iters = 1;
+  s->ibm_kernel = ORA_DELTA_PESKIN4;
   s->density = 1;
   coll_init(&s->coll, lattice, collision, tau, rates);
   double u0[3] = {0, 0, 0};
@@ -568,6 +594,11 @@ void ora_set_scheme(ora_sim *s, int scheme, int ibm_iters, double retraction,
   s->have_prev = 0;
 }
 
+void ora_set_ibm_kernel(ora_sim *s, int kernel) {
+  s->ibm_kernel = (kernel >= ORA_DELTA_PESKIN4 && kernel <= ORA_DELTA_COSINE4) ? kernel
+                                                                               : ORA_DELTA_PESKIN4;
+}
+
 static int simulated(const ora_sim *s, long n) {
   return !(is_ibb(s->scheme) && s->inside[n]);
 }
@@ -601,13 +632,13 @@ static void wall_velocity(const solid_t *b, const double r[3], double uw[3]) {
 }
 
 /* ---- immersed boundary (Sec. 2.1, Eqs. 4-9) ---- */
-static double delta_w(int d, const double r[3]) {
-  double v = ora_phi(r[0]) * ora_phi(r[1]);
-  return d == 3 ? v * ora_phi(r[2]) : v;
+static double delta_w(int kernel, int d, const double r[3]) {
+  double v = ora_phi_kernel(kernel, r[0]) * ora_phi_kernel(kernel, r[1]);
+  return d == 3 ? v * ora_phi_kernel(kernel, r[2]) : v;
 }
 
-void ora_ibm_interp(int d, int nx, int ny, int nz, const double *u, int n,
-                    const double *X, double *U) {
+void ora_ibm_interp_k(int kernel, int d, int nx, int ny, int nz, const double *u, int n,
+                      const double *X, double *U) {
   long N = (long)nx * ny * (d == 3 ? nz : 1);
   for (int m = 0; m < n; m++) {
     double Xm[3] = {X[m], X[n + m], d == 3 ? X[2 * n + m] : 0};
@@ -620,7 +651,7 @@ void ora_ibm_interp(int d, int nx, int ny, int nz, const double *u, int n,
         for (int kx = 0; kx < 4; kx++) {
           double r[3] = {b[0] + kx - Xm[0], b[1] + ky - Xm[1],
                          d == 3 ? b[2] + kz - Xm[2] : 0};
-          double wgt = delta_w(d, r);
+          double wgt = delta_w(kernel, d, r);
           long nn = wrapi(b[0] + kx, nx) +
                     nx * (wrapi(b[1] + ky, ny) +
                           ny * (d == 3 ? wrapi(b[2] + kz, nz) : 0));
@@ -629,8 +660,8 @@ void ora_ibm_interp(int d, int nx, int ny, int nz, const double *u, int n,
   }
 }
 
-void ora_ibm_spread(int d, int nx, int ny, int nz, double *f, int n,
-                    const double *X, const double *F, const double *dV) {
+void ora_ibm_spread_k(int kernel, int d, int nx, int ny, int nz, double *f, int n,
+                      const double *X, const double *F, const double *dV) {
   long N = (long)nx * ny * (d == 3 ? nz : 1);
   for (int m = 0; m < n; m++) {
     double Xm[3] = {X[m], X[n + m], d == 3 ? X[2 * n + m] : 0};
@@ -642,13 +673,23 @@ void ora_ibm_spread(int d, int nx, int ny, int nz, double *f, int n,
         for (int kx = 0; kx < 4; kx++) {
           double r[3] = {b[0] + kx - Xm[0], b[1] + ky - Xm[1],
                          d == 3 ? b[2] + kz - Xm[2] : 0};
-          double wgt = delta_w(d, r);
+          double wgt = delta_w(kernel, d, r);
           long nn = wrapi(b[0] + kx, nx) +
                     nx * (wrapi(b[1] + ky, ny) +
                           ny * (d == 3 ? wrapi(b[2] + kz, nz) : 0));
           for (int a = 0; a < d; a++) f[a * N + nn] += F[a * n + m] * wgt * dV[m];
         }
   }
+}
+
+void ora_ibm_interp(int d, int nx, int ny, int nz, const double *u, int n,
+                    const double *X, double *U) {
+  ora_ibm_interp_k(ORA_DELTA_PESKIN4, d, nx, ny, nz, u, n, X, U);
+}
+
+void ora_ibm_spread(int d, int nx, int ny, int nz, double *f, int n,
+                    const double *X, const double *F, const double *dV) {
+  ora_ibm_spread_k(ORA_DELTA_PESKIN4, d, nx, ny, nz, f, n, X, F, dV);
 }
 
 /* The IB-LBM variant examined in Sec. 2.1: before the collision of step t,
@@ -699,7 +740,7 @@ static void ibm_forces(ora_sim *s) {
     for (int k = 0; k < s->nsol; k++) {
       solid_t *b = &s->sol[k];
       int nm = b->nm;
-      ora_ibm_interp(d, s->nx, s->ny, s->nz, uc, nm, X[k], Ui[k]);
+      ora_ibm_interp_k(s->ibm_kernel, d, s->nx, s->ny, s->nz, uc, nm, X[k], Ui[k]);
       for (int a = 0; a < d; a++)
         for (int m = 0; m < nm; m++)
           b->Fm[a * nm + m] += RHO0 * (Ud[k][a * nm + m] - Ui[k][a * nm + m]);
@@ -707,8 +748,8 @@ static void ibm_forces(ora_sim *s) {
     /* Eulerian force = spread of the accumulated marker forces (Eq. 8) */
     for (long q = 0; q < 3 * N; q++) s->fibm[q] = 0;
     for (int k = 0; k < s->nsol; k++)
-      ora_ibm_spread(d, s->nx, s->ny, s->nz, s->fibm, s->sol[k].nm, X[k],
-                     s->sol[k].Fm, s->sol[k].dV);
+      ora_ibm_spread_k(s->ibm_kernel, d, s->nx, s->ny, s->nz, s->fibm, s->sol[k].nm, X[k],
+                       s->sol[k].Fm, s->sol[k].dV);
   }
   for (int k = 0; k < s->nsol; k++) {
     solid_t *b = &s->sol[k];

@@ -67,6 +67,12 @@ void ora_collide(int lattice, int collision, double tau, const double *rates,
 int ora_ibb_coeffs(int scheme, double q, int have_ff, int have_fff, double c[6]);
 /* Peskin's 4-point kernel, Eq. 6 */
 double ora_phi(double r);
+/* delta-function kernels compared in Sec. 3.1 (selector ORA_DELTA_*) */
+#define ORA_DELTA_PESKIN4 0  /* Eq. 6 */
+#define ORA_DELTA_ROMA3 1    /* Roma, Peskin & Berger 3-point */
+#define ORA_DELTA_LINEAR2 2  /* 2-point linear */
+#define ORA_DELTA_COSINE4 3  /* 4-point cosine (Appendix B) */
+double ora_phi_kernel(int kernel, double r);
 
 /* ---- simulation ---- */
 ora_sim *ora_create(int lattice, int nx, int ny, int nz, double tau,
@@ -76,6 +82,8 @@ void ora_destroy(ora_sim *s);
 /* returns the solid id or -1 */
 int ora_add_solid(ora_sim *s, int kind, const double c[3], double R,
                   const double U[3], const double Om[3], int fluid_inside);
+/* the IBM kernel (ORA_DELTA_*, default Peskin's 4-point) */
+void ora_set_ibm_kernel(ora_sim *s, int kernel);
 void ora_set_scheme(ora_sim *s, int scheme, int ibm_iters, double retraction,
                     double marker_density);
 void ora_init_equilibrium(ora_sim *s, double rho, const double u[3]);
@@ -112,6 +120,11 @@ void ora_ibm_interp(int d, int nx, int ny, int nz, const double *u,
                     int n, const double *X, double *U);
 void ora_ibm_spread(int d, int nx, int ny, int nz, double *f, int n,
                     const double *X, const double *F, const double *dV);
+/* the same with another kernel */
+void ora_ibm_interp_k(int kernel, int d, int nx, int ny, int nz, const double *u,
+                      int n, const double *X, double *U);
+void ora_ibm_spread_k(int kernel, int d, int nx, int ny, int nz, double *f, int n,
+                      const double *X, const double *F, const double *dV);
 
 #ifdef __cplusplus
 }

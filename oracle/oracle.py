@@ -58,6 +58,8 @@ def lib():
                 "ora_collide": (None, [i, i, d, dp, dp, dp, dp]),
                 "ora_ibb_coeffs": (i, [i, d, i, i, dp]),
                 "ora_phi": (d, [d]),
+                "ora_phi_kernel": (d, [i, d]),
+                "ora_set_ibm_kernel": (None, [vp, i]),
                 "ora_create": (vp, [i, i, i, i, d, i, dp, dp, i]),
                 "ora_destroy": (None, [vp]),
                 "ora_add_solid": (i, [vp, i, dp, d, dp, dp, i]),
@@ -79,6 +81,8 @@ def lib():
                 "ora_link_stats": (None, [vp, C.POINTER(C.c_long)]),
                 "ora_ibm_interp": (None, [i, i, i, i, dp, i, dp, dp]),
                 "ora_ibm_spread": (None, [i, i, i, i, dp, i, dp, dp, dp]),
+                "ora_ibm_interp_k": (None, [i, i, i, i, i, dp, i, dp, dp]),
+                "ora_ibm_spread_k": (None, [i, i, i, i, i, dp, i, dp, dp, dp]),
             }
             for name, (res, args) in sig.items():
                 fn = getattr(L, name)
@@ -146,29 +150,42 @@ def ibb_coeffs(scheme: int, q: float, have_ff=True, have_fff=True):
     return c, used
 
 
-def phi(r: float) -> float:
-    return lib().ora_phi(float(r))
+# delta-function kernels (same selectors as the library's LBM_DELTA_*)
+PESKIN4, ROMA3, LINEAR2, COSINE4 = range(4)
 
 
-def ibm_interp(d, shape, u, X):
+def phi(r: float, kernel: int = PESKIN4) -> float:
+    if kernel == PESKIN4:
+        return lib().ora_phi(float(r))
+    return lib().ora_phi_kernel(int(kernel), float(r))
+
+
+def ibm_interp(d, shape, u, X, kernel: int = PESKIN4):
     """u: [d][nz][ny][nx] (nz=1 for d=2); X: [3][n] -> U [d][n]."""
     nx, ny, nz = shape
     u = np.ascontiguousarray(u, dtype=np.float64)
     X = np.ascontiguousarray(X, dtype=np.float64)
     n = X.shape[1]
     U = np.zeros((d, n))
-    lib().ora_ibm_interp(d, nx, ny, nz, _p(u), n, _p(X), _p(U))
+    if kernel == PESKIN4:
+        lib().ora_ibm_interp(d, nx, ny, nz, _p(u), n, _p(X), _p(U))
+    else:
+        lib().ora_ibm_interp_k(int(kernel), d, nx, ny, nz, _p(u), n, _p(X), _p(U))
     return U
 
 
-def ibm_spread(d, shape, F, X, dV):
+def ibm_spread(d, shape, F, X, dV, kernel: int = PESKIN4):
     nx, ny, nz = shape
     N = nx * ny * (nz if d == 3 else 1)
     f = np.zeros((d, N))
     F = np.ascontiguousarray(F, dtype=np.float64)
     X = np.ascontiguousarray(X, dtype=np.float64)
     dV = np.ascontiguousarray(dV, dtype=np.float64)
-    lib().ora_ibm_spread(d, nx, ny, nz, _p(f), X.shape[1], _p(X), _p(F), _p(dV))
+    if kernel == PESKIN4:
+        lib().ora_ibm_spread(d, nx, ny, nz, _p(f), X.shape[1], _p(X), _p(F), _p(dV))
+    else:
+        lib().ora_ibm_spread_k(int(kernel), d, nx, ny, nz, _p(f), X.shape[1], _p(X), _p(F),
+                               _p(dV))
     return f
 
 
@@ -213,7 +230,9 @@ class OracleSim:
             raise ValueError("too many solids")
         return sid
 
-    def set_scheme(self, scheme, ibm_iters=1, retraction=0.0, marker_density=1.0):
+    def set_scheme(self, scheme, ibm_iters=1, retraction=0.0, marker_density=1.0,
+                   ibm_kernel=PESKIN4):
+        self.L.ora_set_ibm_kernel(self.h, int(ibm_kernel))
         self.L.ora_set_scheme(self.h, scheme, ibm_iters, retraction, marker_density)
 
     def init_equilibrium(self, rho=1.0, u=None):

@@ -94,6 +94,26 @@ struct lbm_ctx {
   uint8_t *link_dir = nullptr;
   int *refill_node = nullptr;
   uint8_t *refill_sid = nullptr;
+  // moving solids: a second geometry set, built for the next step on its own
+  // stream while the current step's kernels run (see prefetch_geometry)
+  struct GeomBuf {
+    uint8_t *flags = nullptr, *sid = nullptr;
+    int *counts = nullptr;
+    int *list_node = nullptr;
+    uint32_t *list_mask = nullptr;
+    int *list_link = nullptr;
+    double *list_cst = nullptr;
+    void *link_mem = nullptr;
+    LinkArrays links{};
+    int *link_list = nullptr;
+    uint8_t *link_dir = nullptr;
+    int *refill_node = nullptr;
+    uint8_t *refill_sid = nullptr;
+  } spare;
+  bool spare_ready = false, prefetched = false, geom_prefetch = true;
+  double pf_c[kMaxSolids][3] = {};
+  cudaStream_t gst = nullptr;
+  cudaEvent_t ev_geom = nullptr, ev_gfree = nullptr;
   // IBM
   double *mk_dir = nullptr, *mk_dV = nullptr, *mk_F = nullptr;
   uint8_t *mk_sid = nullptr;
@@ -334,6 +354,27 @@ bool any_moving(const lbm_ctx *ctx) {
   return false;
 }
 
+// link records: c0..c4, mw, uw[3], arm[3] in the compute type, then the solid id
+size_t link_bytes(const lbm_ctx *ctx, size_t lk) { return (12 * ctx->tsz + 1) * lk + 64; }
+void layout_links(const lbm_ctx *ctx, void *mem, size_t lk, LinkArrays &L) {
+  char *p = (char *)mem;
+  for (int k = 0; k < 5; k++) {
+    L.c[k] = p;
+    p += ctx->tsz * lk;
+  }
+  L.mw = p;
+  p += ctx->tsz * lk;
+  for (int k = 0; k < 3; k++) {
+    L.uw[k] = p;
+    p += ctx->tsz * lk;
+  }
+  for (int k = 0; k < 3; k++) {
+    L.arm[k] = p;
+    p += ctx->tsz * lk;
+  }
+  L.sid = (uint8_t *)p;
+}
+
 lbm_status ensure_list_capacity(lbm_ctx *ctx, int list_cap, int link_cap, int refill_cap) {
   if (list_cap > ctx->list_cap || refill_cap > ctx->refill_cap) {
     dfree(ctx, ctx->list_node);
@@ -368,26 +409,74 @@ lbm_status ensure_list_capacity(lbm_ctx *ctx, int list_cap, int link_cap, int re
     const size_t lk = std::max(link_cap, 1);
     TRY(dalloc(ctx, (void **)&ctx->link_list, sizeof(int) * lk));
     TRY(dalloc(ctx, (void **)&ctx->link_dir, lk));
-    const size_t per = 12 * ctx->tsz + 1;
-    TRY(dalloc(ctx, &ctx->link_mem, per * lk + 64));
-    char *p = (char *)ctx->link_mem;
-    for (int k = 0; k < 5; k++) {
-      ctx->links.c[k] = p;
-      p += ctx->tsz * lk;
-    }
-    ctx->links.mw = p;
-    p += ctx->tsz * lk;
-    for (int k = 0; k < 3; k++) {
-      ctx->links.uw[k] = p;
-      p += ctx->tsz * lk;
-    }
-    for (int k = 0; k < 3; k++) {
-      ctx->links.arm[k] = p;
-      p += ctx->tsz * lk;
-    }
-    ctx->links.sid = (uint8_t *)p;
+    TRY(dalloc(ctx, &ctx->link_mem, link_bytes(ctx, lk)));
+    layout_links(ctx, ctx->link_mem, lk, ctx->links);
     ctx->link_cap = link_cap;
   }
+  return LBM_OK;
+}
+
+// exchange the current geometry set with the spare one
+void swap_geom(lbm_ctx *ctx) {
+  auto &b = ctx->spare;
+  std::swap(ctx->flags, b.flags);
+  std::swap(ctx->sid, b.sid);
+  std::swap(ctx->counts, b.counts);
+  std::swap(ctx->list_node, b.list_node);
+  std::swap(ctx->list_mask, b.list_mask);
+  std::swap(ctx->list_link, b.list_link);
+  std::swap(ctx->list_cst, b.list_cst);
+  std::swap(ctx->link_mem, b.link_mem);
+  std::swap(ctx->links, b.links);
+  std::swap(ctx->link_list, b.link_list);
+  std::swap(ctx->link_dir, b.link_dir);
+  std::swap(ctx->refill_node, b.refill_node);
+  std::swap(ctx->refill_sid, b.refill_sid);
+}
+
+void free_spare(lbm_ctx *ctx) {
+  if (!ctx->spare_ready) return;
+  if (ctx->gst) cudaStreamSynchronize(ctx->gst);
+  auto &b = ctx->spare;
+  for (void *p : {(void *)b.flags, (void *)b.sid, (void *)b.counts, (void *)b.list_node,
+                  (void *)b.list_mask, (void *)b.list_link, (void *)b.list_cst, b.link_mem,
+                  (void *)b.link_list, (void *)b.link_dir, (void *)b.refill_node,
+                  (void *)b.refill_sid})
+    dfree(ctx, p);
+  b = lbm_ctx::GeomBuf{};
+  ctx->spare_ready = false;
+  ctx->prefetched = false;
+}
+
+// the spare geometry set, with the capacities of the current one
+lbm_status alloc_spare(lbm_ctx *ctx) {
+  if (ctx->spare_ready) return LBM_OK;
+  if (!ctx->gst) {
+    int lo = 0, hi = 0;
+    cudaDeviceGetStreamPriorityRange(&lo, &hi);
+    if (cudaStreamCreateWithPriority(&ctx->gst, cudaStreamNonBlocking, hi) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_geom, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_gfree, cudaEventDisableTiming) != cudaSuccess)
+      return fail(ctx, LBM_ERR_CUDA, "geometry stream");
+  }
+  auto &b = ctx->spare;
+  const size_t padN = ((ctx->N + 15) / 16) * 16;
+  const int lc = std::max(ctx->list_cap, 1), rc = std::max(ctx->refill_cap, 1);
+  const size_t lk = std::max(ctx->link_cap, 1);
+  TRY(dalloc(ctx, (void **)&b.flags, padN));
+  TRY(dalloc(ctx, (void **)&b.sid, 2 * padN));
+  TRY(dalloc(ctx, (void **)&b.counts, 16 * sizeof(int)));
+  TRY(dalloc(ctx, (void **)&b.list_node, sizeof(int) * lc));
+  TRY(dalloc(ctx, (void **)&b.list_mask, sizeof(uint32_t) * lc));
+  TRY(dalloc(ctx, (void **)&b.list_link, sizeof(int) * lc));
+  TRY(dalloc(ctx, (void **)&b.list_cst, sizeof(double) * 6 * lc));
+  TRY(dalloc(ctx, (void **)&b.refill_node, sizeof(int) * rc));
+  TRY(dalloc(ctx, (void **)&b.refill_sid, rc));
+  TRY(dalloc(ctx, (void **)&b.link_list, sizeof(int) * lk));
+  TRY(dalloc(ctx, (void **)&b.link_dir, lk));
+  TRY(dalloc(ctx, &b.link_mem, link_bytes(ctx, lk)));
+  layout_links(ctx, b.link_mem, lk, b.links);
+  ctx->spare_ready = true;
   return LBM_OK;
 }
 
@@ -525,6 +614,7 @@ lbm_status read_counts(lbm_ctx *ctx, int out[16]) {
 // Full rebuild over the whole lattice (solids or scheme changed): count the
 // boundary nodes and links first, size the lists exactly, then build.
 lbm_status rebuild_full(lbm_ctx *ctx) {
+  free_spare(ctx);  // capacities may change; the next moving step prefetches again
   if (!ctx->restore_geometry)
     for (auto &s : ctx->solids) memcpy(s.cg, s.c, sizeof(s.c));
   ctx->restore_geometry = false;
@@ -590,6 +680,57 @@ lbm_status rebuild_boxes(lbm_ctx *ctx) {
   return LBM_OK;
 }
 
+// Build the next step's geometry (solids at centres `next`) into the spare
+// set on the geometry stream.  The spare set was last read by the previous
+// step's kernels; ev_gfree, recorded on the main stream at the start of the
+// current step, follows them.  The current set is only read here (its
+// solid ids are the previous ids of the next build, its flags the starting
+// point outside the solids' boxes), so the build overlaps the current step.
+lbm_status prefetch_geometry(lbm_ctx *ctx, const double next[][3]) {
+  TRY(alloc_spare(ctx));
+  const size_t padN = ((ctx->N + 15) / 16) * 16;
+  CK(cudaStreamWaitEvent(ctx->gst, ctx->ev_gfree, 0));
+  CK(cudaMemcpyAsync(ctx->spare.flags, ctx->flags, padN, cudaMemcpyDeviceToDevice, ctx->gst));
+  CK(cudaMemcpyAsync(ctx->spare.sid, ctx->sid, padN, cudaMemcpyDeviceToDevice, ctx->gst));
+  CK(cudaMemsetAsync(ctx->spare.counts, 0, 4 * sizeof(int), ctx->gst));
+  double saved[kMaxSolids][3];
+  for (size_t k = 0; k < ctx->solids.size(); k++) {
+    memcpy(saved[k], ctx->solids[k].cg, sizeof(saved[k]));
+    memcpy(ctx->solids[k].cg, next[k], sizeof(saved[k]));
+    memcpy(ctx->pf_c[k], next[k], sizeof(saved[k]));
+  }
+  swap_geom(ctx);
+  GeomArgs g = geom_args(ctx);
+  set_boxes(ctx, g, false);
+  swap_geom(ctx);
+  for (size_t k = 0; k < ctx->solids.size(); k++)
+    memcpy(ctx->solids[k].cg, saved[k], sizeof(saved[k]));
+  g.track_new = is_ibb(ctx->scheme.scheme) ? 1 : 0;
+  {
+    Timed tm(ctx, TK_GEOM, 0, ctx->gst);
+    launch_geometry(g, ctx->d.precision, ctx->gst);
+  }
+  ctx->launches += 4;
+  CK(cudaEventRecord(ctx->ev_geom, ctx->gst));
+  ctx->prefetched = true;
+  return LBM_OK;
+}
+
+// Switch to the prefetched geometry if it was built for the centres the
+// current step needs (the caller may have moved the solids since).
+bool take_prefetched(lbm_ctx *ctx) {
+  if (!ctx->prefetched) return false;
+  ctx->prefetched = false;
+  for (size_t k = 0; k < ctx->solids.size(); k++)
+    for (int a = 0; a < 3; a++)
+      if (ctx->pf_c[k][a] != ctx->solids[k].c[a]) return false;
+  if (cudaStreamWaitEvent(ctx->st, ctx->ev_geom, 0) != cudaSuccess) return false;
+  swap_geom(ctx);
+  for (auto &sh : ctx->solids) memcpy(sh.cg, sh.c, sizeof(sh.c));
+  ctx->markers_dirty = true;  // marker table: rebuilt by the IBM pre-pass
+  return true;
+}
+
 lbm_status ensure_geometry(lbm_ctx *ctx) {
   if (ctx->geom_dirty) return rebuild_full(ctx);
   return LBM_OK;
@@ -612,6 +753,7 @@ IbmArgs ibm_args(lbm_ctx *ctx, double *acc) {
   ib.dV = ctx->mk_dV;
   ib.msid = ctx->mk_sid;
   ib.Fm = ctx->mk_F;
+  ib.kernel = ctx->scheme.ibm_kernel;
   ib.solids = solids_dev(ctx, true);
   ib.u_band = ctx->u_band;
   ib.f_ibm = ctx->f_ibm;
@@ -701,7 +843,14 @@ lbm_status step_once(lbm_ctx *ctx) {
   if (ibm && moving)
     for (auto &s : ctx->solids)
       for (int a = 0; a < 3; a++) s.c[a] += s.d.velocity[a];
-  if (moving) TRY(rebuild_boxes(ctx));
+  const bool prefetch = moving && ctx->geom_prefetch;
+  if (prefetch && ctx->gst) CK(cudaEventRecord(ctx->ev_gfree, ctx->st));
+  if (moving && !take_prefetched(ctx)) TRY(rebuild_boxes(ctx));
+  if (prefetch && !ctx->gst) {
+    // first moving step: the spare set and its stream come into being
+    TRY(alloc_spare(ctx));
+    CK(cudaEventRecord(ctx->ev_gfree, ctx->st));
+  }
   const int cur = ctx->cur, nxt = 1 - ctx->cur;
   KArgs a = base_args(ctx);
   if (moving && is_ibb(ctx->scheme.scheme)) {
@@ -741,6 +890,15 @@ lbm_status step_once(lbm_ctx *ctx) {
   if (!ibm && moving)
     for (auto &s : ctx->solids)
       for (int k = 0; k < 3; k++) s.c[k] += s.d.velocity[k];
+  if (prefetch) {
+    // the next step's geometry: bounce-back uses the centres just reached,
+    // IBM moves first and uses them plus one step
+    double next[kMaxSolids][3];
+    for (size_t k = 0; k < ctx->solids.size(); k++)
+      for (int a = 0; a < 3; a++)
+        next[k][a] = ctx->solids[k].c[a] + (ibm ? ctx->solids[k].d.velocity[a] : 0.0);
+    TRY(prefetch_geometry(ctx, next));
+  }
   ctx->records = std::min<long long>(ctx->records + 1, kHistCap);
   ctx->step++;
   return LBM_OK;
@@ -911,6 +1069,7 @@ lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_st
     if (const char *e = getenv("LBM_CACHE_HINTS")) ctx->cache_hints = atoi(e) & 3;
     if (const char *e = getenv("LBM_BULK_MODE")) ctx->bulk_mode = atoi(e);
     if (const char *e = getenv("LBM_VEC_WORDS")) ctx->bulk_vec_words = atoi(e);
+    if (const char *e = getenv("LBM_GEOM_PREFETCH")) ctx->geom_prefetch = atoi(e) != 0;
     if (const char *e = getenv("LBM_VEC_PACKED")) ctx->bulk_vec_packed = atoi(e);
     if (const char *e = getenv("LBM_MRT_GENERAL"))
       if (atoi(e) && ctx->coll_mode == CM_MRT_Q) ctx->coll_mode = CM_MRT;
@@ -958,6 +1117,12 @@ void lbm_destroy(lbm_ctx *ctx) {
     cudaStreamSynchronize(ctx->aux);
     cudaStreamDestroy(ctx->aux);
   }
+  if (ctx->gst) {
+    cudaStreamSynchronize(ctx->gst);
+    cudaStreamDestroy(ctx->gst);
+  }
+  if (ctx->ev_geom) cudaEventDestroy(ctx->ev_geom);
+  if (ctx->ev_gfree) cudaEventDestroy(ctx->ev_gfree);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   for (void *p : ctx->allocs) cudaFree(p);
@@ -1018,6 +1183,8 @@ lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme) {
     return fail(ctx, LBM_ERR_ARG, "unknown scheme");
   if (scheme->ibm_iters < 0 || scheme->ibm_retraction < 0 || scheme->ibm_marker_density < 0)
     return fail(ctx, LBM_ERR_ARG, "negative IBM parameter");
+  if (scheme->ibm_kernel < LBM_DELTA_PESKIN4 || scheme->ibm_kernel > LBM_DELTA_COSINE4)
+    return fail(ctx, LBM_ERR_ARG, "unknown delta-function kernel");
   ctx->scheme = *scheme;
   ctx->geom_dirty = true;
   return LBM_OK;
@@ -1221,7 +1388,7 @@ lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size) {
   SaveHeader h;
   memset(&h, 0, sizeof(h));
   memcpy(h.magic, "LBMGB300", 8);
-  h.version = 1;
+  h.version = 2;  // 2: the scheme carries the delta-function kernel
   h.lattice = ctx->d.lattice;
   h.nx = ctx->d.nx;
   h.ny = ctx->d.ny;
@@ -1252,7 +1419,7 @@ lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size) {
   if (!ctx || !host_buf || size < sizeof(SaveHeader)) return LBM_ERR_ARG;
   SaveHeader h;
   memcpy(&h, host_buf, sizeof(h));
-  if (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 1) return fail(ctx, LBM_ERR_ARG, "not a checkpoint");
+  if (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2) return fail(ctx, LBM_ERR_ARG, "not a checkpoint of this version");
   if (h.lattice != ctx->d.lattice || h.nx != ctx->d.nx || h.ny != ctx->d.ny || h.nz != ctx->d.nz ||
       h.precision != ctx->d.precision || h.nsolids < 0 || h.nsolids > kMaxSolids ||
       h.fs != ctx->fs)

@@ -1,6 +1,7 @@
 // ibm.cu -- direct-forcing immersed boundary (Sec. 2.1 of Peng, Ayala &
 // Wang): interpolation of the unforced velocity to the Lagrangian markers
-// with Peskin's 4-point delta function (Eqs. 5-6), the direct force
+// with a regularised delta function (Eqs. 5-6; Peskin's 4-point kernel by
+// default, or the 3-point, linear or cosine kernels of Sec. 3.1), the direct force
 // F = rho0 (U^d - U~)/dt (Eq. 7), and its spreading back to the lattice as a
 // body force (Eq. 8) with atomic accumulation.  One warp per marker: its 4^d
 // stencil points are split over the lanes and the interpolated velocity is
@@ -13,13 +14,29 @@ namespace lbm {
 
 namespace {
 
-// Peskin's 4-point kernel (Eq. 6)
+// The one-dimensional delta-function kernels compared in Sec. 3.1:
+// Peskin's 4-point kernel (Eq. 6, the default), Roma, Peskin & Berger's
+// 3-point kernel, the 2-point linear kernel, and the 4-point cosine kernel of
+// Appendix B.  Each support lies inside the 4-point window from floor(X) - 1,
+// so every kernel uses the same 4^d stencil (points outside the support get
+// weight 0).
 template <typename T>
-__device__ __forceinline__ T phi4(T r) {
+__device__ __forceinline__ T phi_k(int kernel, T r) {
   const T a = fabs(r);
-  if (a >= (T)2) return (T)0;
-  if (a >= (T)1) return ((T)5 - (T)2 * a - sqrt((T)-7 + (T)12 * a - (T)4 * a * a)) / (T)8;
-  return ((T)3 - (T)2 * a + sqrt((T)1 + (T)4 * a - (T)4 * a * a)) / (T)8;
+  switch (kernel) {
+  case LBM_DELTA_ROMA3:
+    if (a >= (T)1.5) return (T)0;
+    if (a <= (T)0.5) return ((T)1 + sqrt((T)1 - (T)3 * a * a)) / (T)3;
+    return ((T)5 - (T)3 * a - sqrt((T)1 - (T)3 * ((T)1 - a) * ((T)1 - a))) / (T)6;
+  case LBM_DELTA_LINEAR2:
+    return a >= (T)1 ? (T)0 : (T)1 - a;
+  case LBM_DELTA_COSINE4:
+    return a >= (T)2 ? (T)0 : ((T)1 + cospi(r / (T)2)) / (T)4;
+  default:
+    if (a >= (T)2) return (T)0;
+    if (a >= (T)1) return ((T)5 - (T)2 * a - sqrt((T)-7 + (T)12 * a - (T)4 * a * a)) / (T)8;
+    return ((T)3 - (T)2 * a + sqrt((T)1 + (T)4 * a - (T)4 * a * a)) / (T)8;
+  }
 }
 
 struct Marker {
@@ -73,8 +90,8 @@ template <typename T>
 __device__ __forceinline__ long long stencil_point(const IbmArgs &a, const Stencil<T> &st,
                                                    int p, T &wgt) {
   const int kx = p & 3, ky = (p >> 2) & 3, kz = p >> 4;
-  wgt = phi4<T>(st.dx + (T)kx) * phi4<T>(st.dy + (T)ky);
-  if (a.dim == 3) wgt *= phi4<T>(st.dz + (T)kz);
+  wgt = phi_k<T>(a.kernel, st.dx + (T)kx) * phi_k<T>(a.kernel, st.dy + (T)ky);
+  if (a.dim == 3) wgt *= phi_k<T>(a.kernel, st.dz + (T)kz);
   const int x = wrap(st.ix + kx, a.nx), y = wrap(st.iy + ky, a.ny);
   const int z = a.dim == 3 ? wrap(st.iz + kz, a.nz) : 0;
   return x + (long long)a.nx * (y + (long long)a.ny * z);
@@ -93,8 +110,8 @@ __global__ void __launch_bounds__(128) k_prepare(const IbmArgs a) {
   T *wts = (T *)a.mk_wts + (long long)m * npts;
   for (int p = lane; p < npts; p += 32) {
     const int kx = p & 3, ky = (p >> 2) & 3, kz = p >> 4;
-    T wgt = phi4<T>(stc.dx + (T)kx) * phi4<T>(stc.dy + (T)ky);
-    if (a.dim == 3) wgt *= phi4<T>(stc.dz + (T)kz);
+    T wgt = phi_k<T>(a.kernel, stc.dx + (T)kx) * phi_k<T>(a.kernel, stc.dy + (T)ky);
+    if (a.dim == 3) wgt *= phi_k<T>(a.kernel, stc.dz + (T)kz);
     wts[p] = wgt;
   }
   if (lane == 0) a.mk_base[m] = make_int4(stc.ix, stc.iy, stc.iz, k.s);

@@ -155,6 +155,7 @@ struct IbmArgs {
   int reduce_force;   // accumulate -sum F dV and the torque
   int4 *mk_base;      // [nmark] first stencil node (unwrapped x, y, z) and solid
   void *mk_wts;       // T [nmark][4^dim] delta weights of the stencil points
+  int kernel;         // delta-function kernel (LBM_DELTA_*)
 };
 // stencil bases and weights of every marker (after each geometry change)
 void launch_ibm_prepare(const IbmArgs &a, int precision, cudaStream_t st);

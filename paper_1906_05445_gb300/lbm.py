@@ -30,6 +30,7 @@ SPHERE, CYLINDER_Z = 0, 1
 (SCHEME_NONE, BOUNCE_BACK, BOUZIDI_LIN, BOUZIDI_QUAD, YU_LIN, YU_QUAD,
  IBM_DIRECT) = range(7)
 TK_BULK, TK_LIST, TK_IBM, TK_GEOM = range(4)
+DELTA_PESKIN4, DELTA_ROMA3, DELTA_LINEAR2, DELTA_COSINE4 = range(4)
 # lbm_set_timing masks: every kind, or bit (kind + 1) per kind
 TIME_ALL = 1
 TIME_BULK, TIME_LIST, TIME_IBM, TIME_GEOM = (2 << k for k in range(4))
@@ -50,7 +51,8 @@ class lbm_solid_desc(C.Structure):
 
 class lbm_scheme_desc(C.Structure):
     _fields_ = [("scheme", C.c_int), ("ibm_iters", C.c_int),
-                ("ibm_retraction", C.c_double), ("ibm_marker_density", C.c_double)]
+                ("ibm_retraction", C.c_double), ("ibm_marker_density", C.c_double),
+                ("ibm_kernel", C.c_int)]
 
 
 class lbm_info(C.Structure):
@@ -176,7 +178,7 @@ class Lattice:
                   p.force_all, stream=stream)
         for s in p.solids:
             lat.add_solid(s.kind, s.centre, s.radius, s.velocity, s.omega, s.fluid_inside)
-        lat.set_scheme(p.scheme, p.ibm_iters, p.retraction, p.marker_density)
+        lat.set_scheme(p.scheme, p.ibm_iters, p.retraction, p.marker_density, p.ibm_kernel)
         return lat
 
     def _check(self, st: int):
@@ -209,8 +211,9 @@ class Lattice:
         args = [None if v is None else _v3(v) for v in (centre, velocity, omega)]
         self._check(lbm_set_solid_motion(self.h, sid, *[None if a is None else _dp(a) for a in args]))
 
-    def set_scheme(self, scheme, ibm_iters=1, retraction=0.0, marker_density=1.0):
-        s = lbm_scheme_desc(scheme, ibm_iters, retraction, marker_density)
+    def set_scheme(self, scheme, ibm_iters=1, retraction=0.0, marker_density=1.0,
+                   ibm_kernel=DELTA_PESKIN4):
+        s = lbm_scheme_desc(scheme, ibm_iters, retraction, marker_density, ibm_kernel)
         self._check(lbm_set_scheme(self.h, C.byref(s)))
 
     def init_equilibrium(self, rho=1.0, u=None):

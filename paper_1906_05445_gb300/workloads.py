@@ -21,6 +21,7 @@ BGK, MRT = 0, 1
 FP64, FP32, FP32_BF16, FP32_FP16 = 0, 1, 2, 3
 SPHERE, CYLINDER_Z = 0, 1
 NONE, BB, BOUZIDI_LIN, BOUZIDI_QUAD, YU_LIN, YU_QUAD, IBM = range(7)
+PESKIN4, ROMA3, LINEAR2, COSINE4 = range(4)  # IBM delta-function kernels
 SCHEME_NAMES = {NONE: "none", BB: "bounce_back", BOUZIDI_LIN: "bouzidi_linear",
                 BOUZIDI_QUAD: "bouzidi_quadratic", YU_LIN: "yu_linear",
                 YU_QUAD: "yu_quadratic", IBM: "ibm_direct_forcing"}
@@ -55,6 +56,7 @@ class Problem:
     retraction: float = 0.0
     marker_density: float = 1.0
     force_all: bool = False
+    ibm_kernel: int = 0  # PESKIN4, ROMA3, LINEAR2, COSINE4
 
     @property
     def nodes(self) -> int:
@@ -82,6 +84,36 @@ def couette_2d(n: int = 64, r1: float = 10.0, r2: float = 28.0,
                     Solid(CYLINDER_Z, (centre[0], centre[1], 0.0), r2,
                           fluid_inside=True)],
                    scheme, steps)
+
+
+def taylor_couette(r1: float, gamma: float = 2.0, re: float = 15.0, tau: float = 0.65,
+                   scheme: int = IBM, ibm_kernel: int = PESKIN4, retraction: float = 0.0,
+                   ibm_iters: int = 5, precision: int = FP64, seed: int = 1906,
+                   margin: int = 8, guard: int = 4) -> Problem:
+    """Sec. 3.1's Taylor-Couette flow: inner cylinder (radius r1) at rest,
+    outer cylinder (r2 = gamma r1) turning with tangential speed U2 such that
+    Re = (r2 - r1) U2 / nu; D2Q9 with a single relaxation time, the centre
+    at a seeded sub-grid offset in a periodic box of edge 2 r2 + 2 margin.
+    Under IBM the whole box holds fluid, and the paper holds the flow outside
+    the outer cylinder in rigid rotation (u_theta = Omega2 r at the edges of
+    its domain); here a third, enclosing cylinder of radius r2 + guard turns
+    with the outer one, so that the steady flow between the two is that
+    rigid rotation."""
+    r2 = gamma * r1
+    nu = (tau - 0.5) / 3.0
+    u2 = re * nu / (r2 - r1)
+    om2 = u2 / r2
+    n = int(2 * round(r2) + 2 * margin)
+    rng = np.random.default_rng(seed)
+    c = (n / 2 + float(rng.random()), n / 2 + float(rng.random()), 0.0)
+    solids = [Solid(CYLINDER_Z, c, r1),
+              Solid(CYLINDER_Z, c, r2, omega=(0.0, 0.0, om2), fluid_inside=True)]
+    if scheme == IBM:
+        solids.append(Solid(CYLINDER_Z, c, r2 + guard, omega=(0.0, 0.0, om2),
+                            fluid_inside=True))
+    return Problem(f"taylor_couette_r{r1:g}", D2Q9, n, n, 1, tau, BGK, precision,
+                   (0.0, 0.0, 0.0), solids, scheme, 0, ibm_iters=ibm_iters,
+                   retraction=retraction, ibm_kernel=ibm_kernel)
 
 
 def sphere_offset(seed: int, base=(64.0, 64.0, 64.0)) -> Tuple[float, float, float]:

@@ -135,6 +135,37 @@ def test_couette_ibm_fp64():
     compare(g, o, FP64_TOL, tol_F=1e-10, sids=(0, 1))
 
 
+@pytest.mark.parametrize("kernel", [W.ROMA3, W.LINEAR2, W.COSINE4])
+def test_ibm_delta_kernels_fp64(kernel):
+    """The other delta-function kernels of Sec. 3.1 (and Appendix B's cosine
+    kernel) on a fixed sphere with 2 forcing iterations and a retraction, and
+    on the 2D Couette geometry: every step of the path against the oracle."""
+    p = W.fixed_sphere(26, 6.1, seed=17, tau=0.7, g=2e-4, scheme=W.IBM,
+                       precision=W.FP64, collision=W.MRT, steps=15,
+                       ibm_iters=2, retraction=0.2).with_(ibm_kernel=kernel)
+    g, o = make_gpu(p), make_oracle(p)
+    f0 = random_populations(p, seed=9, amplitude=0.03)
+    g.set_f(f0)
+    o.set_f(f0)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10, what=("u", "rho", "f"))
+    c = W.couette_2d(48, 7.5, 21.0, (24.4, 23.7), 0.01, 0.9, W.IBM, 200).with_(
+        ibm_iters=5, retraction=0.1, ibm_kernel=kernel)
+    g, o = make_gpu(c), make_oracle(c)
+    g.step(c.steps)
+    o.step(c.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10, sids=(0, 1))
+
+
+def test_unknown_delta_kernel_is_rejected():
+    from paper_1906_05445_gb300 import lbm
+    lt = lbm.Lattice(W.D2Q9, 16, 16, 1, 0.8, W.BGK, W.FP64, (0, 0, 0))
+    with pytest.raises(lbm.LbmError):
+        lt.set_scheme(W.IBM, ibm_kernel=7)
+    lt.close()
+
+
 @pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.YU_QUAD, W.BB])
 def test_moving_sphere_ibb_refill_fp64(scheme):
     """A sphere translating across grid lines: geometry rebuilt every step,
@@ -157,6 +188,36 @@ def test_moving_sphere_ibm_fp64():
     g.step(p.steps)
     o.step(p.steps)
     compare(g, o, FP64_TOL, tol_F=1e-10, what=("u", "rho"))
+
+
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])
+def test_prefetched_geometry_equals_rebuild_in_step(scheme, monkeypatch):
+    """Moving solids get their next geometry built on a side stream during
+    the current step.  Against rebuilding in the step (LBM_GEOM_PREFETCH=0)
+    the fields and forces agree to FP64 summation order,
+    also when the caller changes the motion between steps (the prefetched
+    geometry is then discarded)."""
+    from paper_1906_05445_gb300 import lbm
+    p = W.translating_sphere(40, 24, 22, 5.2, seed=23, u=0.07, tau=0.7,
+                             scheme=scheme, precision=W.FP64, steps=12)
+    runs = []
+    for flag in ("1", "0"):
+        monkeypatch.setenv("LBM_GEOM_PREFETCH", flag)
+        g = make_gpu(p)
+        g.step(p.steps)
+        g.set_solid_motion(0, velocity=(0.03, -0.05, 0.02))
+        g.step(p.steps)
+        g.set_solid_motion(0, centre=(18.3, 11.6, 10.9))
+        g.step(p.steps)
+        runs.append((g.velocity(), g.force_history(0, 3 * p.steps), g.solid_centre(0)))
+        g.close()
+    (u0, F0, c0), (u1, F1, c1) = runs
+    assert np.array_equal(c0, c1)
+    # the IBM spreading and the forces are FP64 sums whose order across
+    # blocks varies from run to run: equal to rounding, not bit for bit
+    assert rel_l2(u0, u1) <= 1e-12
+    assert F0.shape == F1.shape
+    assert np.abs(F0 - F1).max() <= 1e-12 * np.abs(F1).max(), np.abs(F0 - F1).max()
 
 
 @pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])

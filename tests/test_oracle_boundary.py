@@ -111,8 +111,44 @@ def test_peskin_delta_identities(oracle):
         assert abs(oracle.phi(a - 1e-12) - oracle.phi(a + 1e-12)) < 1e-9
 
 
+# (kernel, phi(0), support, sum phi^2 or None, zero first moment)
+KERNELS = [(1, 2 / 3, 1.5, 1 / 2, True),     # Roma, Peskin & Berger 3-point
+           (2, 1.0, 1.0, None, True),        # 2-point linear
+           (3, 0.5, 2.0, 3 / 8, False)]      # 4-point cosine (Appendix B)
+
+
+@pytest.mark.parametrize("kernel,phi0,support,sq,moment", KERNELS)
+def test_other_delta_kernel_identities(oracle, kernel, phi0, support, sq, moment):
+    """The kernels compared with Eq. 6 in Sec. 3.1: each is a partition of
+    unity (sum_j phi(r-j) = 1 for every shift), vanishes beyond its support
+    and is continuous there.  The 3-point kernel also has a zero first moment
+    and sum phi^2 = 1/2 (the conditions it was built from); the linear kernel
+    has a zero first moment; the cosine kernel has sum phi^2 = 3/8 but not a
+    zero first moment, as Appendix B remarks."""
+    phi = np.vectorize(lambda r: oracle.phi(r, kernel))
+    assert abs(oracle.phi(0, kernel) - phi0) < 1e-15
+    assert oracle.phi(support, kernel) == 0 and oracle.phi(-support - 0.3, kernel) == 0
+    assert abs(oracle.phi(support - 1e-9, kernel)) < 1e-4
+    first = []
+    for r in np.random.default_rng(0).uniform(-3, 3, 50):
+        j = np.arange(-6, 7)
+        p = phi(r - j)
+        assert abs(p.sum() - 1) < 1e-14
+        first.append(((r - j) * p).sum())
+        if sq is not None:
+            assert abs((p ** 2).sum() - sq) < 1e-14
+    if moment:
+        assert np.abs(first).max() < 1e-14
+    else:
+        assert np.abs(first).max() > 1e-3
+    if kernel == 1:  # the two pieces meet at |r| = 1/2
+        for a in (0.5, -0.5):
+            assert abs(oracle.phi(a - 1e-12, kernel) - oracle.phi(a + 1e-12, kernel)) < 1e-9
+
+
+@pytest.mark.parametrize("kernel", [0, 1, 2, 3])
 @pytest.mark.parametrize("d", [2, 3])
-def test_interp_spread_adjoint_and_exact_for_linear(oracle, d):
+def test_interp_spread_adjoint_and_exact_for_linear(oracle, d, kernel):
     shape = (11, 9, 7) if d == 3 else (11, 9, 1)
     N = int(np.prod(shape))
     rng = np.random.default_rng(1)
@@ -123,20 +159,22 @@ def test_interp_spread_adjoint_and_exact_for_linear(oracle, d):
     u = rng.standard_normal((d, N))
     F = rng.standard_normal((d, n))
     dV = rng.uniform(0.5, 1.5, n)
-    U = oracle.ibm_interp(d, shape, u, X)
-    f = oracle.ibm_spread(d, shape, F, X, dV)
+    U = oracle.ibm_interp(d, shape, u, X, kernel)
+    f = oracle.ibm_spread(d, shape, F, X, dV, kernel)
     # <I u, F dV> = <u, S F> with h = 1 (Eq. 5 and Eq. 8 share the kernel)
     assert abs((U * F * dV).sum() - (u * f).sum()) < 1e-11
     # spreading conserves the total force
     assert np.abs(f.sum(axis=1) - (F * dV).sum(axis=1)).max() < 1e-12
     # a linear field is interpolated exactly (zero first moment of phi)
+    if kernel == 3:
+        return
     g = rng.standard_normal(d)
     idx = np.indices((shape[2], shape[1], shape[0]))[::-1]  # x, y, z
     lin = np.zeros((d, N))
     for a in range(d):
         lin[a] = 0.3 + sum(g[b] * idx[b].ravel() for b in range(d))
     inner = np.all([(X[a] > 2) & (X[a] < shape[a] - 3) for a in range(d)], axis=0)
-    Ul = oracle.ibm_interp(d, shape, lin, X)
+    Ul = oracle.ibm_interp(d, shape, lin, X, kernel)
     ref = 0.3 + sum(g[b] * X[b] for b in range(d))
     assert np.abs(Ul[:, inner] - ref[inner]).max() < 1e-12
 

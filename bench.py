@@ -329,11 +329,17 @@ SERVE_CFG = dict(count=24, seed=11, rate_hz=40.0, min_2d=48, max_2d=160, min_3d=
                  max_3d=48, tau_range=(0.7, 1.0), tol=1e-5, check_every=200)
 
 
-def run_batch_leg(lbm, stream):
-    """Grid-convergence batch (spheres R = 3..8, cube edge 8R, alternating
-    quadratic Bouzidi / IBM, FP32), every lattice to its own residual < tol:
-    one batch (graph-captured, autotuned) vs the same solves one at a time."""
-    c = BATCH_CFG
+# a larger grid-convergence sweep, 32 lattices (edges 32..96), run on request
+BATCH_CFG_C4 = dict(count=32, r_min=4.0, r_max=12.0, tau=0.8, re_p=2.0, tol=1e-6,
+                    check_every=500, max_steps=600000)
+
+
+def run_batch_leg(lbm, stream, c=None):
+    """Grid-convergence batch (spheres R = r_min..r_max, cube edge 8R,
+    alternating quadratic Bouzidi / IBM, FP32), every lattice to its own
+    residual < tol: one batch (graph-captured, autotuned) vs the same solves
+    one at a time."""
+    c = c or BATCH_CFG
     ps = W.convergence_batch(c["count"], tau=c["tau"], re_p=c["re_p"], r_min=c["r_min"],
                              r_max=c["r_max"])
     t0 = time.perf_counter()
@@ -502,7 +508,8 @@ def run_ours(args, rank, world, local):
             cpu = dict(single, all_cores_error=str(e))
     batch = serve_leg = None
     if rank == 0 and world == 1 and not args.no_batch and args.workload == "fixed":
-        batch = run_batch_leg(lbm, stream.cuda_stream)
+        batch = run_batch_leg(lbm, stream.cuda_stream,
+                              BATCH_CFG_C4 if args.batch_config == "c4" else BATCH_CFG)
         serve_leg = run_serve_leg(stream.cuda_stream)
 
     if rank == 0:
@@ -543,6 +550,8 @@ def main(argv=None):
     ap.add_argument("--workload", default="fixed", choices=["fixed", "moving"],
                     help="fixed: the 128^3 sphere (default); moving: the 256x128x128 "
                          "translating sphere")
+    ap.add_argument("--batch-config", default="small", choices=["small", "c4"],
+                    help="batch leg: 8 lattices R 3..8 (default) or 32 lattices R 4..12")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-solve and served-stream legs")
     args = ap.parse_args(argv)

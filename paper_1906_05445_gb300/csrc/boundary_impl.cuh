@@ -656,13 +656,13 @@ void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
     break;
   case OP_LIST_SWEEP:
     if (a.list_cap > 0) {
-      if constexpr (CM != CM_MRT) {
+      if (CM != CM_MRT && !a.list_thread) {
         // a warp per boundary node, list_block / 32 nodes per block
         const int lb = a.list_block >= 64 ? (a.list_block > 256 ? 256 : a.list_block) : 256;
-        k_list_warp<LAT, CM, S, T><<<div_up(lc, lb / 32), lb, 0, st>>>(a);
+        if constexpr (CM != CM_MRT) k_list_warp<LAT, CM, S, T><<<div_up(lc, lb / 32), lb, 0, st>>>(a);
       } else {
-        // general MRT rates: a thread per node (small blocks spread the few
-        // boundary nodes over many SMs)
+        // general MRT rates, or IBM band nodes (no cut links): a thread per
+        // node (small blocks spread the boundary nodes over many SMs)
         const int lb = a.list_block > 0 && a.list_block <= 128 ? a.list_block : 64;
         k_list<LAT, CM, S, T, T, 0><<<div_up(lc, lb), lb, 0, st>>>(a);
       }

@@ -79,6 +79,7 @@ struct KArgs {
   int bulk_block;    // threads per block of the bulk sweep (multiple of 32)
   int cache_hints;   // bulk sweep: bit 0 evict-first loads, bit 1 evict-first stores
   int list_block;    // threads per block of the boundary-node sweep (32, 64 or 128)
+  int list_thread;   // boundary-node sweep: 1 = a thread per node (IBM band), 0 = a warp per node
   int bulk_mode;       // bulk sweep: 0 one node per thread, 1 vectors of nodes per thread
                        // (where nx and the direction stride allow)
   int bulk_vec_words;  // vector sweep: 32-bit words per thread and direction (2 or 4; 0 = 2)

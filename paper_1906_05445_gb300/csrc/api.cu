@@ -68,6 +68,7 @@ struct lbm_ctx {
   int bulk_vec_words = 0;
   int bulk_vec_packed = -1;
   int ibm_list_thread = 1;  // IBM band nodes: a thread per node in the boundary sweep
+  int ibb_list_thread = 0;  // bounce-back boundary nodes too (measured slower: off)
   int coll_mode = 0;  // CM_BGK, CM_MRT or CM_MRT_Q
   cudaStream_t st = 0;
   // auxiliary high-priority stream: the boundary-node sweep and the IBM
@@ -292,7 +293,8 @@ KArgs base_args(lbm_ctx *ctx) {
   a.bulk_mode = ctx->bulk_mode;
   a.bulk_vec_words = ctx->bulk_vec_words;
   a.bulk_vec_packed = ctx->bulk_vec_packed;
-  a.list_thread = ctx->scheme.scheme == LBM_IBM_DIRECT && ctx->ibm_list_thread ? 1 : 0;
+  a.list_thread = (ctx->scheme.scheme == LBM_IBM_DIRECT && ctx->ibm_list_thread) ||
+                          ctx->ibb_list_thread ? 1 : 0;
   a.list_block = ctx->list_block;
   a.flags = ctx->flags;
   a.omega = ctx->omega;
@@ -1074,6 +1076,7 @@ lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_st
     if (const char *e = getenv("LBM_GEOM_PREFETCH")) ctx->geom_prefetch = atoi(e) != 0;
     if (const char *e = getenv("LBM_VEC_PACKED")) ctx->bulk_vec_packed = atoi(e);
     if (const char *e = getenv("LBM_IBM_LIST_THREAD")) ctx->ibm_list_thread = atoi(e) != 0;
+    if (const char *e = getenv("LBM_IBB_LIST_THREAD")) ctx->ibb_list_thread = atoi(e) != 0;
     if (const char *e = getenv("LBM_MRT_GENERAL"))
       if (atoi(e) && ctx->coll_mode == CM_MRT_Q) ctx->coll_mode = CM_MRT;
   }

@@ -244,6 +244,19 @@ def test_full_size_sphere_fp32(scheme):
     compare(g, o, FP32_U_TOL, tol_F=FP32_F_TOL)
 
 
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])
+def test_full_size_moving_sphere_fp32(scheme):
+    """The 256x128x128 translating sphere (R = 8, U = 0.01) of the moving
+    benchmark, FP32 with the prefetched geometry, a few steps from rest
+    against the oracle on every node."""
+    p = W.translating_sphere(256, 128, 128, 8.0, seed=1906, u=0.01, tau=0.6,
+                             scheme=scheme, precision=W.FP32, steps=3)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP32_U_TOL, tol_F=FP32_F_TOL)
+
+
 def test_sphere_across_periodic_wrap_and_tiny_lattices():
     # sphere centred near a corner: its solid nodes wrap through all faces
     p = W.Problem("wrap", W.D3Q19, 17, 15, 13, 0.8, W.MRT, W.FP64, (3e-4, 0, 0),

@@ -214,3 +214,23 @@ def test_run_to_steady_converges(oracle):
     s, _ = couette_sim(oracle, p)
     done, r = s.run_to_steady(1e-8, 20000, 100)
     assert r < 1e-8 and done < 20000 and done % 100 == 0
+
+
+def test_taylor_couette_study_error_metric():
+    """The kernel study's error (Eq. 18 over the annulus against Eq. 31) is
+    zero for the analytic field and equals a known relative perturbation."""
+    from paper_1906_05445_gb300 import workloads as W
+    from paper_1906_05445_gb300.ibm_study import annulus_error
+    p = W.taylor_couette(8)
+    inner, outer = p.solids[0], p.solids[1]
+    assert outer.radius == 16 and len(p.solids) == 3 and p.solids[2].omega == outer.omega
+    u2 = outer.omega[2] * outer.radius
+    assert abs(u2 * (outer.radius - inner.radius) / ((p.tau - 0.5) / 3) - 15) < 1e-12
+    y, x = np.mgrid[0:p.ny, 0:p.nx]
+    dx, dy = x - inner.centre[0], y - inner.centre[1]
+    r = np.hypot(dx, dy)
+    A = u2 * outer.radius / (outer.radius ** 2 - inner.radius ** 2)
+    ut = A * r - A * inner.radius ** 2 / np.maximum(r, 1e-12)
+    u = np.stack([-ut * dy / np.maximum(r, 1e-12), ut * dx / np.maximum(r, 1e-12)])
+    assert annulus_error(p, u.reshape(2, -1)) < 1e-14
+    assert abs(annulus_error(p, 1.03 * u.reshape(2, -1)) - 0.03) < 1e-12

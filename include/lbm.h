@@ -207,6 +207,14 @@ lbm_status lbm_get_solid_mask(lbm_ctx *ctx, unsigned char *host_out, size_t n);
  * sum of marker forces times their control volume at the current time. */
 lbm_status lbm_get_force_torque(lbm_ctx *ctx, int solid_id, double F[3],
                                 double T[3]);
+/* The same record (Fx Fy Fz Tx Ty Tz) copied to host_out without waiting:
+ * the copy is enqueued on the context's stream after the work already
+ * there, so a caller that reads the force every step can keep the GPU busy
+ * and wait once (lbm_sync, or an event on the stream) before reading the
+ * values.  host_out must stay valid until then, and should be page-locked
+ * (e.g. cudaHostAlloc) for the copy to be asynchronous.  CUDA errors are
+ * reported by the next synchronising call. */
+lbm_status lbm_copy_force_torque_async(lbm_ctx *ctx, int solid_id, double *host_out);
 /* The last min(max_steps, steps kept) records, oldest first, 6 doubles
  * (Fx Fy Fz Tx Ty Tz) per step; *n receives the count. */
 lbm_status lbm_get_force_history(lbm_ctx *ctx, int solid_id, double *host_out,

@@ -1304,6 +1304,14 @@ lbm_status lbm_get_force_torque(lbm_ctx *ctx, int id, double F[3], double T[3]) 
   return LBM_OK;
 }
 
+lbm_status lbm_copy_force_torque_async(lbm_ctx *ctx, int id, double *host_out) {
+  if (!ctx || !host_out || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
+  TRY(prepare(ctx));
+  CK(cudaMemcpyAsync(host_out, force_slot(ctx, ctx->slot) + 6 * id, 6 * sizeof(double),
+                     cudaMemcpyDeviceToHost, ctx->st));
+  return LBM_OK;
+}
+
 lbm_status lbm_get_force_history(lbm_ctx *ctx, int id, double *host_out, size_t max_steps, size_t *n) {
   if (!ctx || id < 0 || id >= (int)ctx->solids.size() || !n) return LBM_ERR_ARG;
   TRY(prepare(ctx));

@@ -89,6 +89,7 @@ def _load():
         "lbm_get_solid_mask": (st, [vp, C.POINTER(C.c_ubyte), sz]),
         "lbm_get_force_torque": (st, [vp, i, dp, dp]),
         "lbm_get_force_history": (st, [vp, i, dp, sz, C.POINTER(sz)]),
+        "lbm_copy_force_torque_async": (st, [vp, i, dp]),
         "lbm_get_residual": (st, [vp, dp]),
         "lbm_get_solid_centre": (st, [vp, i, dp]),
         "lbm_get_info": (st, [vp, C.POINTER(lbm_info)]),
@@ -122,6 +123,7 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_get_distributions", "lbm_step", "lbm_run_to_steady", "lbm_get_density",
     "lbm_get_velocity", "lbm_get_strain_rate", "lbm_get_stress",
     "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
+    "lbm_copy_force_torque_async",
     "lbm_get_residual", "lbm_get_solid_centre", "lbm_get_info",
     "lbm_device_field", "lbm_save", "lbm_load", "lbm_set_timing",
     "lbm_get_kernel_time", "lbm_get_velocity_noalloc", "lbm_sync", "lbm_last_error",
@@ -263,6 +265,13 @@ class Lattice:
         F, T = np.zeros(3), np.zeros(3)
         self._check(lbm_get_force_torque(self.h, sid, _dp(F), _dp(T)))
         return F, T
+
+    def copy_force_torque_async(self, out, sid=0):
+        """Enqueue the copy of the current (Fx Fy Fz Tx Ty Tz) into `out`, a
+        float64 array of 6 (page-locked for the copy to be asynchronous);
+        valid after sync()."""
+        assert out.dtype == np.float64 and out.size >= 6 and out.flags.c_contiguous
+        self._check(lbm_copy_force_torque_async(self.h, sid, _dp(out)))
 
     def force_history(self, sid=0, max_steps=4096):
         out = np.zeros((max_steps, 6))

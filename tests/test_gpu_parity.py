@@ -368,3 +368,22 @@ def test_mrt_general_rates_fp64(lat):
         g.step(p.steps)
         o.step(p.steps)
         compare(g, o, FP64_TOL, tol_F=1e-10, what=("u", "rho", "f"))
+
+
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])
+def test_async_force_copy_matches_history(scheme):
+    """lbm_copy_force_torque_async, called after every step into page-locked
+    memory and read after one lbm_sync, gives each step's record as the
+    (synchronising) force history does."""
+    import torch
+    p = W.fixed_sphere(32, 5.3, seed=2, tau=0.7, g=1e-4, scheme=scheme,
+                       precision=W.FP64, collision=W.MRT, steps=6)
+    g = make_gpu(p)
+    buf = torch.empty((p.steps, 6), dtype=torch.float64, pin_memory=True).numpy()
+    for k in range(p.steps):
+        g.step(1)
+        g.copy_force_torque_async(buf[k])
+    g.sync()
+    hist = g.force_history(0, p.steps)
+    assert np.array_equal(buf, hist)
+    g.close()

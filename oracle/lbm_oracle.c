@@ -383,7 +383,7 @@ struct ora_sim {
   int scheme, ibm_iters, ibm_kernel;
   double retraction, density;
   long steps;
-  long link_counts[7];
+  long link_counts[8];
   coll_t coll;
 };
 
@@ -402,7 +402,9 @@ static void coords(const ora_sim *s, long n, long *x, long *y, long *z) {
 /* nearest periodic image of a separation along an axis of length L */
 static double mimage(double d, double L) { return d - L * round(d / L); }
 
-static int is_ibb(int scheme) { return scheme >= ORA_BB && scheme <= ORA_YU_QUAD; }
+static int is_ibb(int scheme) {
+  return (scheme >= ORA_BB && scheme <= ORA_YU_QUAD) || scheme == ORA_ZHAO_YONG;
+}
 
 ora_sim *ora_create(int lattice, int nx, int ny, int nz, double tau,
                     int collision, const double *rates, const double g[3],
@@ -860,6 +862,10 @@ static void one_step(ora_sim *s) {
     if (!simulated(s, n)) continue;
     long x, y, z;
     coords(s, n, &x, &y, &z);
+    /* this node's pre-collision values f(t), before streaming replaces them
+     * (Eq. 16 uses the one travelling towards the wall) */
+    double fpre[MAXQ];
+    for (int i = 0; i < Q; i++) fpre[i] = s->f[(long)i * N + n];
     for (int i = 0; i < Q; i++) {
       long src = node(s, x - s->e[i][0], y - s->e[i][1], z - s->e[i][2]);
       if (simulated(s, src)) {
@@ -874,7 +880,8 @@ static void one_step(ora_sim *s) {
           node(s, x + 2 * s->e[i][0], y + 2 * s->e[i][1], z + 2 * s->e[i][2]);
       int hff = simulated(s, nff), hfff = hff && simulated(s, nfff);
       double q = link_q(s, b, n, i), c[6];
-      int used = ora_ibb_coeffs(s->scheme, q, hff, hfff, c);
+      int used = s->scheme == ORA_ZHAO_YONG ? ORA_ZHAO_YONG
+                                            : ora_ibb_coeffs(s->scheme, q, hff, hfff, c);
       s->link_counts[used]++;
       double r[3], xw[3], uw[3];
       rel(s, b, (double)x, (double)y, (double)z, r);
@@ -883,12 +890,21 @@ static void one_step(ora_sim *s) {
       wall_velocity(b, xw, uw);
       if (s->d == 2) uw[2] = 0;
       double eu = s->e[i][0] * uw[0] + s->e[i][1] * uw[1] + s->e[i][2] * uw[2];
-      double fin = c[0] * s->fpost[(long)ib * N + n] +
-                   (c[1] != 0 ? c[1] * s->fpost[(long)ib * N + nff] : 0) +
-                   (c[2] != 0 ? c[2] * s->fpost[(long)ib * N + nfff] : 0) +
-                   (c[3] != 0 ? c[3] * s->fpost[(long)i * N + n] : 0) +
-                   (c[4] != 0 ? c[4] * s->fpost[(long)i * N + nff] : 0) +
-                   c[5] * 2 * RHO0 * s->w[i] * eu / CS2;
+      double fin;
+      if (s->scheme == ORA_ZHAO_YONG) {
+        /* Eq. 16 as printed: the post-collision value leaving the wall at
+         * x_f, the pre-collision value arriving at x_f towards the wall, and
+         * the moving-wall term, weighted 2q, 1 and 2 over 1 + 2q */
+        fin = (2 * q * s->fpost[(long)i * N + n] + fpre[ib] + 2 * RHO0 * s->w[i] * eu / CS2) /
+              (1 + 2 * q);
+      } else {
+        fin = c[0] * s->fpost[(long)ib * N + n] +
+              (c[1] != 0 ? c[1] * s->fpost[(long)ib * N + nff] : 0) +
+              (c[2] != 0 ? c[2] * s->fpost[(long)ib * N + nfff] : 0) +
+              (c[3] != 0 ? c[3] * s->fpost[(long)i * N + n] : 0) +
+              (c[4] != 0 ? c[4] * s->fpost[(long)i * N + nff] : 0) +
+              c[5] * 2 * RHO0 * s->w[i] * eu / CS2;
+      }
       s->f[(long)i * N + n] = fin;
       /* Eq. 17: F dt += f*_ib (e_ib - u_w) - f_i(t+1) (e_i - u_w) */
       double fs = s->fpost[(long)ib * N + n], dp[3];
@@ -1032,6 +1048,6 @@ void ora_solid_centre(const ora_sim *s, int id, double c[3]) {
   for (int a = 0; a < 3; a++) c[a] = s->sol[id].c[a];
 }
 
-void ora_link_stats(const ora_sim *s, long counts[7]) {
-  for (int k = 0; k < 7; k++) counts[k] = s->link_counts[k];
+void ora_link_stats(const ora_sim *s, long counts[8]) {
+  for (int k = 0; k < 8; k++) counts[k] = s->link_counts[k];
 }

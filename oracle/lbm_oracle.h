@@ -45,6 +45,7 @@ extern "C" {
 #define ORA_YU_LIN 4        /* linear analogue of Eqs. 12-14 */
 #define ORA_YU_QUAD 5       /* Eqs. 12-14 (combined: Eq. 15, corrected) */
 #define ORA_IBM 6           /* direct-forcing IBM, Sec. 2.1 (Eqs. 4-9) */
+#define ORA_ZHAO_YONG 7     /* single-node bounce-back, Eq. 16 */
 
 typedef struct ora_sim ora_sim;
 
@@ -109,8 +110,8 @@ double ora_residual(ora_sim *s);
 long ora_steps_done(const ora_sim *s);
 void ora_solid_centre(const ora_sim *s, int id, double c[3]);
 /* number of cut links last handled by each scheme (fallback statistics):
- * counts[0..6] indexed by scheme selector */
-void ora_link_stats(const ora_sim *s, long counts[7]);
+ * counts[0..7] indexed by scheme selector */
+void ora_link_stats(const ora_sim *s, long counts[8]);
 
 /* ---- immersed-boundary primitives on a bare periodic grid (pin tests) ----
  * u: [d][N] Eulerian field, X: [3][n] marker positions.

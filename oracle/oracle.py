@@ -295,7 +295,7 @@ class OracleSim:
         return c
 
     def link_stats(self):
-        c = (C.c_long * 7)()
+        c = (C.c_long * 8)()
         self.L.ora_link_stats(self.h, c)
         return list(c)
 

@@ -293,3 +293,22 @@ def test_moving_sphere_in_comoving_fluid_feels_small_force(oracle):
     assert abs(c[0] - (8.2 + 60 * 0.02)) < 1e-12
     u = s.velocity()[0][~s.solid_mask()]
     assert np.abs(u - 0.02).max() < 2e-3
+
+
+@pytest.mark.parametrize("scheme", [7, 3, 2])
+def test_comoving_wall_keeps_uniform_flow(oracle, scheme):
+    """A fluid moving uniformly at U past a wall moving at the same U is an
+    exact solution: one step of any consistent bounce-back rule leaves every
+    population at f^eq(U).  For Eq. 16 this pins the index placement as
+    printed (post-collision f*_i leaving the wall, pre-collision f_ib arriving
+    at it): with f*_ib in the first term the step would not return f^eq(U)."""
+    U = (0.03, -0.02, 0.0)
+    s = oracle.OracleSim(0, 40, 36, 1, 0.8, 0, g=(0, 0, 0))
+    s.add_solid(1, (19.3, 17.6, 0.0), 7.2, velocity=U)
+    s.set_scheme(scheme)
+    s.init_equilibrium(1.0, U)
+    s.step(1)
+    u = s.velocity()[:, 0]
+    fl = ~s.solid_mask()[0]
+    assert np.abs(u[0][fl] - U[0]).max() < 1e-13
+    assert np.abs(u[1][fl] - U[1]).max() < 1e-13

@@ -94,7 +94,8 @@ def test_couette_c1_profile_and_torque(oracle):
 
 
 @pytest.mark.slow
-@pytest.mark.parametrize("scheme", [W.BOUZIDI_LIN, W.BOUZIDI_QUAD, W.YU_LIN, W.YU_QUAD])
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_LIN, W.BOUZIDI_QUAD, W.YU_LIN, W.YU_QUAD,
+                                    W.ZHAO_YONG])
 def test_couette_ibb_second_order(oracle, scheme):
     errs = []
     for k in (0.5, 1.0):

@@ -76,7 +76,12 @@ enum {
   LBM_BOUZIDI_QUAD = 3,   /* Eq. 11 */
   LBM_YU_LIN = 4,         /* two-point form of Eqs. 12-14 */
   LBM_YU_QUAD = 5,        /* Eqs. 12-14 (the combined Eq. 15) */
-  LBM_IBM_DIRECT = 6      /* direct-forcing IBM, Eqs. 4-9 */
+  LBM_IBM_DIRECT = 6,     /* direct-forcing IBM, Eqs. 4-9 */
+  LBM_ZHAO_YONG = 7       /* single-node bounce-back, Eq. 16 (solids at rest or
+                             rotating in place; translating solids are
+                             LBM_ERR_UNSUPPORTED, and so is lbm_save; select
+                             it before stepping or after an initialisation,
+                             else LBM_ERR_STATE) */
 };
 /* fields for lbm_device_field */
 enum { LBM_FIELD_F_POST = 0, LBM_FIELD_FLAGS = 1 };

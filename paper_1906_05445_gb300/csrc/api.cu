@@ -113,6 +113,9 @@ struct lbm_ctx {
     uint8_t *refill_sid = nullptr;
   } spare;
   bool spare_ready = false, prefetched = false, geom_prefetch = true;
+  // Eq. 16: pre-collision populations kept at the boundary nodes ([Q][fs],
+  // compute type; allocated when the scheme is first selected)
+  void *zy_pre = nullptr;
   double pf_c[kMaxSolids][3] = {};
   cudaStream_t gst = nullptr;
   cudaEvent_t ev_geom = nullptr, ev_gfree = nullptr;
@@ -202,7 +205,7 @@ void dfree(lbm_ctx *ctx, void *p) {
   cudaFree(p);
 }
 
-bool is_ibb(int s) { return s >= LBM_BOUNCE_BACK && s <= LBM_YU_QUAD; }
+bool is_ibb(int s) { return (s >= LBM_BOUNCE_BACK && s <= LBM_YU_QUAD) || s == LBM_ZHAO_YONG; }
 
 // ---- timing helpers (CUDA events on the context's stream)
 cudaEvent_t take_event(lbm_ctx *ctx) {
@@ -296,6 +299,7 @@ KArgs base_args(lbm_ctx *ctx) {
   a.list_thread = (ctx->scheme.scheme == LBM_IBM_DIRECT && ctx->ibm_list_thread) ||
                           ctx->ibb_list_thread ? 1 : 0;
   a.list_block = ctx->list_block;
+  a.zy_pre = ctx->scheme.scheme == LBM_ZHAO_YONG ? ctx->zy_pre : nullptr;
   a.flags = ctx->flags;
   a.omega = ctx->omega;
   for (int k = 0; k < 19; k++) a.ds[k] = ctx->ds[k];
@@ -829,6 +833,7 @@ lbm_status init_collide(lbm_ctx *ctx) {
   a.src = ctx->f[prev];
   a.dst = ctx->f[ctx->cur];
   sweep(ctx, OP_LOCAL_INIT, a);
+  if (ctx->scheme.scheme == LBM_ZHAO_YONG) sweep(ctx, OP_ZY_SEED, a);
   ctx->need_collide = false;
   ctx->prev_local = true;
   ctx->records = std::min<long long>(ctx->records + 1, kHistCap);
@@ -844,6 +849,9 @@ lbm_status prepare(lbm_ctx *ctx) {
 lbm_status step_once(lbm_ctx *ctx) {
   const bool moving = any_moving(ctx);
   const bool ibm = ctx->scheme.scheme == LBM_IBM_DIRECT;
+  if (moving && ctx->scheme.scheme == LBM_ZHAO_YONG)
+    return fail(ctx, LBM_ERR_UNSUPPORTED,
+                "Eq. 16 keeps pre-collision values per boundary node: solids must not translate");
   if (ibm && moving)
     for (auto &s : ctx->solids)
       for (int a = 0; a < 3; a++) s.c[a] += s.d.velocity[a];
@@ -1185,14 +1193,25 @@ lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int id, const double centre[3], co
 
 lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme) {
   if (!ctx || !scheme) return LBM_ERR_ARG;
-  if (scheme->scheme < LBM_SCHEME_NONE || scheme->scheme > LBM_IBM_DIRECT)
+  if (scheme->scheme < LBM_SCHEME_NONE || scheme->scheme > LBM_ZHAO_YONG)
     return fail(ctx, LBM_ERR_ARG, "unknown scheme");
   if (scheme->ibm_iters < 0 || scheme->ibm_retraction < 0 || scheme->ibm_marker_density < 0)
     return fail(ctx, LBM_ERR_ARG, "negative IBM parameter");
   if (scheme->ibm_kernel < LBM_DELTA_PESKIN4 || scheme->ibm_kernel > LBM_DELTA_COSINE4)
     return fail(ctx, LBM_ERR_ARG, "unknown delta-function kernel");
+  if (scheme->scheme == LBM_ZHAO_YONG && !ctx->need_collide && !ctx->prev_local)
+    return fail(ctx, LBM_ERR_STATE,
+                "select Eq. 16 before stepping, or after lbm_init_equilibrium / "
+                "lbm_set_distributions (its boundary state starts from a pre-collision state)");
+  if (scheme->scheme == LBM_ZHAO_YONG && !ctx->zy_pre) {
+    TRY(dalloc(ctx, &ctx->zy_pre, (size_t)ctx->Q * ctx->fs * ctx->tsz));
+    CK(cudaMemsetAsync(ctx->zy_pre, 0, (size_t)ctx->Q * ctx->fs * ctx->tsz, ctx->st));
+  }
   ctx->scheme = *scheme;
   ctx->geom_dirty = true;
+  // the boundary nodes' pre-collision values are seeded by the next
+  // initial collision, from the pre-collision state held locally
+  if (scheme->scheme == LBM_ZHAO_YONG) ctx->need_collide = true;
   return LBM_OK;
 }
 
@@ -1391,6 +1410,8 @@ struct SaveHeader {
 
 lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size) {
   if (!ctx || !size) return LBM_ERR_ARG;
+  if (ctx->scheme.scheme == LBM_ZHAO_YONG)
+    return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints do not carry the Eq. 16 boundary state");
   const size_t fb = (size_t)ctx->Q * ctx->fs * ctx->ssz;
   const size_t total = sizeof(SaveHeader) + sizeof(SolidHost) * ctx->solids.size() + 2 * fb + ctx->N;
   if (!host_buf) {

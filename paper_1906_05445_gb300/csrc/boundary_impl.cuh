@@ -26,6 +26,14 @@ __device__ __forceinline__ T ibb_value(const KArgs &a, const S *__restrict__ src
   const long long N = a.fs;
   const int ex = L::ex(i), ey = L::ey(i), ez = L::ez(i);
   fs = Store<S>::ld(src + (long long)ib * N + n, isc);
+  if (a.zy_pre) {
+    // Eq. 16: the post-collision value leaving the wall at x_f (c3), the
+    // pre-collision value arriving at x_f from the previous step (c1) and
+    // the moving-wall term
+    const LT *pre = (const LT *)a.zy_pre;
+    return (T)c3[link] * Store<S>::ld(src + (long long)i * N + n, isc) +
+           (T)c1[link] * (T)pre[(long long)ib * N + n] + (T)mw[link];
+  }
   T v = (T)c0[link] * fs + (T)mw[link];
   const T k1 = (T)c1[link], k2 = (T)c2[link], k3 = (T)c3[link], k4 = (T)c4[link];
   if (k1 != (T)0 || k2 != (T)0 || k4 != (T)0) {
@@ -146,11 +154,14 @@ __global__ void __launch_bounds__(128) k_list(const KArgs a) {
     int x, y, z;
     node_xyz(n, a.nx, a.ny, x, y, z);
     T f[Q];
+    const bool zy_query = MODE == 1 && a.zy_pre && !a.local_gather;
     if (a.local_gather)
       gather_local<LAT, S, T>(src, a.fs, n, isc, f);
+    else if (zy_query)  // Eq. 16 keeps the current pre-collision values here
+      for (int i = 0; i < Q; i++) f[i] = (T)((const LT *)a.zy_pre)[(long long)i * a.fs + n];
     else
       gather_pull<LAT, S, T>(src, a.fs, x, y, z, a.nx, a.ny, a.nz, isc, f);
-    if (mask && !a.local_gather) {
+    if (mask && !a.local_gather && !zy_query) {
 #pragma unroll
       for (int i = 1; i < Q; i++) {
         if (!((mask >> i) & 1u)) continue;
@@ -199,6 +210,8 @@ __global__ void __launch_bounds__(128) k_list(const KArgs a) {
       if (MODE == 0 && sa >= 0)
         for (int c = 0; c < 6; c++) acc[c] = a.list_cst[c * a.list_cap + t] + (double)dacc[c];
     }
+    if (MODE == 0 && a.zy_pre)  // the next step's Eq. 16 reads them
+      for (int i = 0; i < Q; i++) ((LT *)a.zy_pre)[(long long)i * a.fs + n] = (LT)f[i];
     const uint8_t fl = a.flags[n];
     T Fx, Fy, Fz;
     node_force<T, LT>(a, n, fl, Fx, Fy, Fz);
@@ -325,6 +338,11 @@ __global__ void __launch_bounds__(256) k_list_warp(const KArgs a) {
       const long long sn = wrap(x - ex, a.nx) +
                            (long long)a.nx * (wrap(y - ey, a.ny) + (long long)a.ny * wrap(z - ez, a.nz));
       fi = Store<S>::ld(src + (long long)lane * a.fs + sn, isc);
+    }
+    if (a.zy_pre) {
+      // every lane has read its Eq. 16 input before any lane replaces it
+      __syncwarp();
+      if (dir) ((T *)a.zy_pre)[(long long)lane * a.fs + n] = fi;
     }
     const uint8_t fl = a.flags[n];
     T Fx, Fy, Fz;
@@ -607,6 +625,21 @@ __global__ void __launch_bounds__(256) k_fill_eq(const KArgs a) {
                  (T)feq_dev<LAT, double>(i, a.omega - 1.0, ux, uy, uz, uu), isc);
 }
 
+// Eq. 16: the pre-collision populations of the boundary nodes, read from a
+// state held locally (right after an initialisation).
+template <int LAT, typename S, typename T>
+__global__ void __launch_bounds__(128) k_zy_seed(const KArgs a) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int cnt = a.counts[0];
+  if (cnt > a.list_cap) cnt = a.list_cap;
+  if (t >= cnt) return;
+  const long long n = a.list_node[t];
+  const T isc = kisc<T>(a);
+  for (int i = 0; i < Lat<LAT>::Q; i++)
+    ((T *)a.zy_pre)[(long long)i * a.fs + n] =
+        Store<S>::ld((const S *)a.src + (long long)i * a.fs + n, isc);
+}
+
 // ---------------------------------------------------------------- launch
 inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 
@@ -667,6 +700,9 @@ void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
         k_list<LAT, CM, S, T, T, 0><<<div_up(lc, lb), lb, 0, st>>>(a);
       }
     }
+    break;
+  case OP_ZY_SEED:
+    if (a.list_cap > 0 && a.zy_pre) k_zy_seed<LAT, S, T><<<div_up(lc, 128), 128, 0, st>>>(a);
     break;
   case OP_LIST_QUERY:
     if (a.list_cap > 0) k_list<LAT, CM, S, double, T, 1><<<div_up(lc, 64), 64, 0, st>>>(a);

@@ -86,7 +86,8 @@ __global__ void k_geom_flags(const GeomArgs g, uint8_t *sid_new) {
         break;
       }
   uint8_t fl = 0;
-  const bool ibb = g.scheme >= LBM_BOUNCE_BACK && g.scheme <= LBM_YU_QUAD;
+  const bool ibb =
+      (g.scheme >= LBM_BOUNCE_BACK && g.scheme <= LBM_YU_QUAD) || g.scheme == LBM_ZHAO_YONG;
   if (ibb) {
     if (s_in)
       fl |= FL_SOLID;
@@ -138,7 +139,8 @@ __global__ void __launch_bounds__(256) k_geom_list(const GeomArgs g, const uint8
     n = box_node(g, t, x, y, z);
     fl = g.flags[n];
   }
-  const bool ibb = g.scheme >= LBM_BOUNCE_BACK && g.scheme <= LBM_YU_QUAD;
+  const bool ibb =
+      (g.scheme >= LBM_BOUNCE_BACK && g.scheme <= LBM_YU_QUAD) || g.scheme == LBM_ZHAO_YONG;
   uint32_t mask = 0;
   if (valid && !(fl & FL_SOLID) && ibb) {
 #pragma unroll
@@ -190,6 +192,16 @@ __global__ void __launch_bounds__(256) k_geom_list(const GeomArgs g, const uint8
 template <typename T>
 __device__ int ibb_rule_t(int scheme, T q, bool ff, bool fff, T c[6]) {
   for (int k = 0; k < 6; k++) c[k] = (T)0;
+  if (scheme == LBM_ZHAO_YONG) {
+    // Eq. 16 (single node, no fallback): c3 weighs the post-collision value
+    // leaving the wall at x_f, c1 the pre-collision value arriving at x_f
+    // (read from the previous step), c5 the moving-wall term
+    const T d = (T)1 / ((T)1 + (T)2 * q);
+    c[3] = (T)2 * q * d;
+    c[1] = d;
+    c[5] = d;
+    return scheme;
+  }
   int s = scheme;
   if (s == LBM_BOUZIDI_QUAD && !(ff && fff)) s = LBM_BOUZIDI_LIN;
   if (s == LBM_YU_QUAD && !(ff && fff)) s = LBM_YU_LIN;

@@ -80,6 +80,7 @@ struct KArgs {
   int cache_hints;   // bulk sweep: bit 0 evict-first loads, bit 1 evict-first stores
   int list_block;    // threads per block of the boundary-node sweep (32, 64 or 128)
   int list_thread;   // boundary-node sweep: 1 = a thread per node (IBM band), 0 = a warp per node
+  void *zy_pre;      // Eq. 16: T [Q][fs] pre-collision populations at the boundary nodes, or null
   int bulk_mode;       // bulk sweep: 0 one node per thread, 1 vectors of nodes per thread
                        // (where nx and the direction stride allow)
   int bulk_vec_words;  // vector sweep: 32-bit words per thread and direction (2 or 4; 0 = 2)
@@ -94,6 +95,7 @@ enum TimedKernel { TK_BULK = 0, TK_LIST = 1, TK_IBM = 2, TK_GEOM = 3, TK_COUNT =
 enum SweepOp {
   OP_BULK_SWEEP,   // pull + collide + store, plain fluid nodes
   OP_LIST_SWEEP,   // pull + bounce-back + collide + store + Eq. 17
+  OP_ZY_SEED,      // Eq. 16: boundary nodes' pre-collision populations from a local state
   OP_BULK_QUERY,   // pull, fields to FP64 outputs
   OP_LIST_QUERY,
   OP_LOCAL_INIT,   // local read of a pre-collision state + collide + store

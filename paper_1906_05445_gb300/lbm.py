@@ -28,7 +28,7 @@ FP64, FP32, FP32_BF16STORE, FP32_FP16STORE = 0, 1, 2, 3
 FORCE_FLUID_ONLY, FORCE_ALL = 0, 1
 SPHERE, CYLINDER_Z = 0, 1
 (SCHEME_NONE, BOUNCE_BACK, BOUZIDI_LIN, BOUZIDI_QUAD, YU_LIN, YU_QUAD,
- IBM_DIRECT) = range(7)
+ IBM_DIRECT, ZHAO_YONG) = range(8)
 TK_BULK, TK_LIST, TK_IBM, TK_GEOM = range(4)
 DELTA_PESKIN4, DELTA_ROMA3, DELTA_LINEAR2, DELTA_COSINE4 = range(4)
 # lbm_set_timing masks: every kind, or bit (kind + 1) per kind

@@ -67,7 +67,8 @@ def test_periodic_sweep_fp32(lat, shape, coll):
     compare(g, o, FP32_U_TOL, what=("u", "rho"), rho_tol=1e-7)
 
 
-@pytest.mark.parametrize("scheme", [W.BB, W.BOUZIDI_LIN, W.BOUZIDI_QUAD, W.YU_LIN, W.YU_QUAD])
+@pytest.mark.parametrize("scheme", [W.BB, W.BOUZIDI_LIN, W.BOUZIDI_QUAD, W.YU_LIN, W.YU_QUAD,
+                                    W.ZHAO_YONG])
 def test_fixed_sphere_ibb_fp64(scheme):
     """Sec. 2.2 rules and Eq. 17 on a fixed sphere (MRT, body force), from a
     random state so that every link carries a distinct value."""
@@ -99,7 +100,7 @@ def test_couette_c1_fp64():
     assert rel_l2(g.strain_rate(), o.strain_rate(), o.solid_mask()) < 1e-10
 
 
-@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.YU_LIN])
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.YU_LIN, W.ZHAO_YONG])
 def test_couette_fp64_other_rules(scheme):
     p = W.couette_2d(48, 7.5, 21.0, (24.4, 23.7), 0.01, 0.9, scheme, 400)
     g, o = make_gpu(p), make_oracle(p)
@@ -295,6 +296,45 @@ def test_fallback_rules_and_link_counts():
     compare(g, o, FP64_TOL, tol_F=1e-10, sids=(0, 1))
     st = o.link_stats()
     assert st[W.BOUZIDI_LIN] > 0 and st[W.BB] > 0
+
+
+def test_zhao_yong_narrow_gap_and_fp32():
+    """Eq. 16 in the narrow gap between two spheres (links whose opposite
+    link is cut too, where the pre-collision value comes from the previous
+    step's rule) in FP64, and the same flow in FP32 storage."""
+    p = W.Problem("gap", W.D3Q19, 30, 20, 20, 0.75, W.MRT, W.FP64, (3e-4, 0, 0),
+                  [W.Solid(W.SPHERE, (9.3, 10.2, 9.7), 5.1),
+                   W.Solid(W.SPHERE, (20.6, 9.9, 10.3), 5.2)], W.ZHAO_YONG, 12)
+    g, o = make_gpu(p), make_oracle(p)
+    g.step(p.steps)
+    o.step(p.steps)
+    compare(g, o, FP64_TOL, tol_F=1e-10, sids=(0, 1), what=("u", "rho"))
+    p32 = p.with_(precision=W.FP32, steps=40)
+    g, o = make_gpu(p32), make_oracle(p32)
+    g.step(p32.steps)
+    o.step(p32.steps)
+    compare(g, o, FP32_U_TOL, tol_F=FP32_F_TOL, sids=(0, 1))
+
+
+def test_zhao_yong_limits():
+    """Translating solids and switching to Eq. 16 mid-run are refused with
+    the statuses the header states."""
+    from paper_1906_05445_gb300 import lbm
+    p = W.translating_sphere(24, 16, 16, 4.1, seed=3, u=0.05, scheme=W.ZHAO_YONG,
+                             precision=W.FP64, steps=2)
+    g = make_gpu(p)
+    with pytest.raises(lbm.LbmError, match="UNSUPPORTED"):
+        g.step(1)
+    g.close()
+    q = W.fixed_sphere(24, 4.1, seed=3, scheme=W.BOUZIDI_QUAD, precision=W.FP64, steps=2)
+    g = make_gpu(q)
+    g.step(2)
+    with pytest.raises(lbm.LbmError, match="STATE"):
+        g.set_scheme(W.ZHAO_YONG)
+    g.init_equilibrium()
+    g.set_scheme(W.ZHAO_YONG)
+    g.step(2)
+    g.close()
 
 
 def test_run_to_steady_matches_oracle():

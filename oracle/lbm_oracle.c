@@ -365,6 +365,10 @@ typedef struct {
   double *dV;  /* [nm] */
   double *Fm;  /* [3][nm] marker force density */
   double F[3], T[3];
+  /* free motion (Eq. 20 under bounce-back, Eq. 23 under IBM): density ratio
+   * rho_p / rho_f, gravity, and the velocities of the previous step */
+  int free_;
+  double rho_p, g[3], Up[3], Omp[3];
 } solid_t;
 
 struct ora_sim {
@@ -836,6 +840,45 @@ static double link_q(const ora_sim *s, const solid_t *b, long nf, int i) {
   return q;
 }
 
+/* Volume and moment of inertia (about the centre, the z axis for cylinders)
+ * per unit solid density: a sphere 4/3 pi R^3 and 2/5 R^2 of its mass, a
+ * cylinder pi R^2 times its length (1 in 2D, nz along z in 3D) and 1/2 R^2. */
+static void solid_volume(const ora_sim *s, const solid_t *b, double *V, double *Ir2) {
+  const double pi = 3.14159265358979323846;
+  if (s->d == 2 || b->kind == ORA_CYLINDER_Z) {
+    *V = pi * b->R * b->R * (s->d == 2 ? 1.0 : (double)s->nz);
+    *Ir2 = 0.5 * b->R * b->R;
+  } else {
+    *V = 4.0 / 3.0 * pi * b->R * b->R * b->R;
+    *Ir2 = 0.4 * b->R * b->R;
+  }
+}
+
+/* New velocities of a free solid from this step's hydrodynamic force and
+ * torque (dt = 1, rho_f = rho0):
+ *  - bounce-back (Eq. 20): rho_p V dv = F + (rho_p - rho_f) V g, I dw = T;
+ *  - IBM (Eq. 23): rho_p V dv = rho_f V (v - v_prev) + F + (rho_p - rho_f) V g,
+ *    I dw = I (rho_f / rho_p)(w - w_prev) + T.
+ * Cylinders turn about z only. */
+static void free_motion(const ora_sim *s, const solid_t *b, double Un[3], double On[3]) {
+  double V, Ir2;
+  solid_volume(s, b, &V, &Ir2);
+  const double m = b->rho_p * RHO0 * V, I = m * Ir2;
+  const int ibm = s->scheme == ORA_IBM;
+  for (int a = 0; a < 3; a++) {
+    double dv = b->F[a] + (b->rho_p - 1.0) * RHO0 * V * b->g[a];
+    double dw = b->T[a];
+    if (ibm) {
+      dv += RHO0 * V * (b->U[a] - b->Up[a]);
+      dw += I / b->rho_p * (b->Om[a] - b->Omp[a]);
+    }
+    Un[a] = b->U[a] + dv / m;
+    On[a] = b->Om[a] + dw / I;
+  }
+  if (s->d == 2) Un[2] = 0;
+  if (s->d == 2 || b->kind == ORA_CYLINDER_Z) On[0] = On[1] = 0;
+}
+
 /* Collision at every simulated node, then streaming (pull of post-collision
  * values) with the interpolated bounce-back rule on links whose upstream
  * node is solid, accumulating the momentum exchange of Eq. 17. */
@@ -917,9 +960,24 @@ static void one_step(ora_sim *s) {
       b->T[2] += xw[0] * dp[1] - xw[1] * dp[0];
     }
   }
-  /* prescribed motion: X(t+1) = X(t) + U dt */
-  for (int k = 0; k < s->nsol; k++)
-    for (int a = 0; a < 3; a++) s->sol[k].c[a] += s->sol[k].U[a];
+  /* motion: prescribed, X(t+1) = X(t) + U dt; or free, new velocities from
+   * this step's force and torque, then X(t+1) = X(t) + (U(t) + U(t+1))/2 */
+  for (int k = 0; k < s->nsol; k++) {
+    solid_t *b = &s->sol[k];
+    if (b->free_) {
+      double Un[3], On[3];
+      free_motion(s, b, Un, On);
+      for (int a = 0; a < 3; a++) {
+        b->c[a] += 0.5 * (b->U[a] + Un[a]);
+        b->Up[a] = b->U[a];
+        b->Omp[a] = b->Om[a];
+        b->U[a] = Un[a];
+        b->Om[a] = On[a];
+      }
+    } else {
+      for (int a = 0; a < 3; a++) b->c[a] += b->U[a];
+    }
+  }
   s->steps++;
 }
 
@@ -1046,6 +1104,25 @@ long ora_steps_done(const ora_sim *s) { return s->steps; }
 
 void ora_solid_centre(const ora_sim *s, int id, double c[3]) {
   for (int a = 0; a < 3; a++) c[a] = s->sol[id].c[a];
+}
+
+void ora_solid_velocity(const ora_sim *s, int id, double U[3], double Om[3]) {
+  for (int a = 0; a < 3; a++) {
+    U[a] = s->sol[id].U[a];
+    Om[a] = s->sol[id].Om[a];
+  }
+}
+
+void ora_set_solid_dynamics(ora_sim *s, int id, double rho_ratio, const double g[3]) {
+  solid_t *b = &s->sol[id];
+  b->free_ = rho_ratio > 0;
+  b->rho_p = rho_ratio;
+  for (int a = 0; a < 3; a++) {
+    b->g[a] = g ? g[a] : 0;
+    b->Up[a] = b->U[a];
+    b->Omp[a] = b->Om[a];
+  }
+  if (s->d == 2) b->g[2] = 0;
 }
 
 void ora_link_stats(const ora_sim *s, long counts[8]) {

@@ -112,6 +112,11 @@ void ora_solid_centre(const ora_sim *s, int id, double c[3]);
 /* number of cut links last handled by each scheme (fallback statistics):
  * counts[0..7] indexed by scheme selector */
 void ora_link_stats(const ora_sim *s, long counts[8]);
+/* free motion (Sec. 3.2): density ratio rho_p / rho_f (<= 0: prescribed
+ * motion) and gravity; the solid's velocities then follow Eq. 20
+ * (bounce-back) or Eq. 23 (IBM) every step */
+void ora_set_solid_dynamics(ora_sim *s, int id, double rho_ratio, const double g[3]);
+void ora_solid_velocity(const ora_sim *s, int id, double U[3], double Om[3]);
 
 /* ---- immersed-boundary primitives on a bare periodic grid (pin tests) ----
  * u: [d][N] Eulerian field, X: [3][n] marker positions.

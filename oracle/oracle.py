@@ -60,6 +60,8 @@ def lib():
                 "ora_phi": (d, [d]),
                 "ora_phi_kernel": (d, [i, d]),
                 "ora_set_ibm_kernel": (None, [vp, i]),
+                "ora_set_solid_dynamics": (None, [vp, i, d, dp]),
+                "ora_solid_velocity": (None, [vp, i, dp, dp]),
                 "ora_create": (vp, [i, i, i, i, d, i, dp, dp, i]),
                 "ora_destroy": (None, [vp]),
                 "ora_add_solid": (i, [vp, i, dp, d, dp, dp, i]),
@@ -293,6 +295,14 @@ class OracleSim:
         c = np.zeros(3)
         self.L.ora_solid_centre(self.h, sid, _p(c))
         return c
+
+    def set_solid_dynamics(self, sid, rho_ratio, gravity=None):
+        self.L.ora_set_solid_dynamics(self.h, sid, float(rho_ratio), _p(_vec3(gravity)))
+
+    def solid_velocity(self, sid=0):
+        U, Om = np.zeros(3), np.zeros(3)
+        self.L.ora_solid_velocity(self.h, sid, _p(U), _p(Om))
+        return U, Om
 
     def link_stats(self):
         c = (C.c_long * 8)()

@@ -235,3 +235,41 @@ def test_taylor_couette_study_error_metric():
     u = np.stack([-ut * dy / np.maximum(r, 1e-12), ut * dx / np.maximum(r, 1e-12)])
     assert annulus_error(p, u.reshape(2, -1)) < 1e-14
     assert abs(annulus_error(p, 1.03 * u.reshape(2, -1)) - 0.03) < 1e-12
+
+
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_LIN, W.IBM])
+def test_free_cylinder_settles_at_the_periodic_array_velocity(oracle, scheme):
+    """A free cylinder (Eq. 20 under bounce-back, Eq. 23 under IBM) settling
+    through a periodic box whose fluid carries the opposite body force
+    reaches the creeping-flow slip velocity of a square array of cylinders:
+    4 pi mu U / F = 1 / (-ln(c)/2 - 0.738 + c - 0.887 c^2 + 2.039 c^3), c the
+    solid fraction (Hasimoto's expansion with Sangani & Acrivos' terms), at
+    Re = 0.05.  Bounds 15%: the 4-node radius carries the schemes'
+    discretisation errors."""
+    L, R, tau, rho_p, g0 = 32, 4.0, 1.0, 1.5, 1e-4
+    nu = (tau - 0.5) / 3
+    c = np.pi * R * R / (L * L)
+    weight = (rho_p - 1) * np.pi * R * R * g0
+    s = oracle.OracleSim(0, L, L, 1, tau, 0, g=(0, weight / (L * L - np.pi * R * R), 0))
+    sid = s.add_solid(1, (16.3, 15.7, 0), R)
+    s.set_scheme(scheme)
+    s.set_solid_dynamics(sid, rho_p, (0, -g0, 0))
+    s.step(12000)
+    U, Om = s.solid_velocity(sid)
+    u = s.velocity()[:, 0]
+    fluid = ~s.solid_mask()[0]
+    slip = u[1][fluid].mean() - U[1]
+    K = -0.5 * np.log(c) - 0.738 + c - 0.887 * c ** 2 + 2.039 * c ** 3
+    assert abs(slip / (weight * K / (4 * np.pi * nu)) - 1) < 0.15
+    # no sideways drift, and only the staircase of the surface turns it
+    assert abs(U[0]) < 1e-3 * abs(U[1]) and abs(Om[2]) * R < 2e-2 * abs(U[1])
+
+
+def test_free_solid_in_fluid_at_rest_stays_at_rest(oracle):
+    s = oracle.OracleSim(1, 20, 18, 16, 0.8, 1, g=(0, 0, 0))
+    sid = s.add_solid(0, (10.3, 9.1, 7.7), 3.6)
+    s.set_scheme(W.BOUZIDI_QUAD)
+    s.set_solid_dynamics(sid, 2.0, (0, 0, 0))
+    s.step(30)
+    U, Om = s.solid_velocity(sid)
+    assert np.abs(U).max() < 1e-15 and np.abs(Om).max() < 1e-15

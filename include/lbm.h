@@ -212,6 +212,21 @@ lbm_status lbm_get_solid_mask(lbm_ctx *ctx, unsigned char *host_out, size_t n);
  * sum of marker forces times their control volume at the current time. */
 lbm_status lbm_get_force_torque(lbm_ctx *ctx, int solid_id, double F[3],
                                 double T[3]);
+/* Free motion of a solid (Sec. 3.2): density_ratio = rho_p / rho_f > 0
+ * makes the solid free, <= 0 returns it to prescribed motion; gravity acts
+ * on it (the fluid feels only the lattice body force).  Every step then sets
+ * its velocities from its hydrodynamic force and torque: Eq. 20 under
+ * bounce-back, the Feng & Michaelides discretisation of Eq. 23 under IBM
+ * (dt = 1, rho_f = 1); its centre moves by the mean of the old and new
+ * velocity.  Spheres have V = 4/3 pi R^3 and I = 2/5 m R^2; cylinders
+ * V = pi R^2 (times nz in 3D) and I = 1/2 m R^2 about z, turning about z
+ * only.  LBM_ERR_STATE without a bounce-back or IBM scheme;
+ * LBM_ERR_UNSUPPORTED under LBM_ZHAO_YONG.  Each step of a lattice with a
+ * free solid reads the force record back to the host (a wait per step). */
+lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int solid_id, double density_ratio,
+                                  const double gravity[3]);
+/* The solid's current velocity and angular velocity. */
+lbm_status lbm_get_solid_velocity(lbm_ctx *ctx, int solid_id, double U[3], double Om[3]);
 /* The same record (Fx Fy Fz Tx Ty Tz) copied to host_out without waiting:
  * the copy is enqueued on the context's stream after the work already
  * there, so a caller that reads the force every step can keep the GPU busy

@@ -50,6 +50,9 @@ struct SolidHost {
   lbm_solid_desc d;
   double c[3];   // centre now
   double cg[3];  // centre of the current geometry
+  // free motion: density ratio rho_p / rho_f (0: prescribed), gravity, and
+  // the velocities of the previous step (Eq. 23)
+  double rho_p = 0, g[3] = {0, 0, 0}, Up[3] = {0, 0, 0}, Omp[3] = {0, 0, 0};
 };
 
 const double PI = 3.14159265358979323846;
@@ -355,11 +358,65 @@ void solid_box(const lbm_ctx *ctx, const SolidHost &s, GeomBox &b) {
   b = {o[0], o[1], o[2], w[0], w[1], w[2]};
 }
 
+bool any_free(const lbm_ctx *ctx) {
+  for (auto &s : ctx->solids)
+    if (s.rho_p > 0) return true;
+  return false;
+}
+
 bool any_moving(const lbm_ctx *ctx) {
   for (auto &s : ctx->solids)
-    if (s.d.velocity[0] != 0 || s.d.velocity[1] != 0 || (ctx->D == 3 && s.d.velocity[2] != 0))
+    if (s.d.velocity[0] != 0 || s.d.velocity[1] != 0 || (ctx->D == 3 && s.d.velocity[2] != 0) ||
+        s.rho_p > 0)
       return true;
   return false;
+}
+
+// Free solids (Sec. 3.2): new velocities from the force record `slot` (this
+// step's momentum exchange under bounce-back, the current IBM force under
+// IBM) and gravity, dt = 1, rho_f = rho0 = 1:
+//  - bounce-back, Eq. 20: rho_p V dv = F + (rho_p - rho_f) V g, I dw = T;
+//  - IBM, Eq. 23: rho_p V dv = rho_f V (v - v_prev) + F + (rho_p - rho_f) V g,
+//    I dw = I (rho_f / rho_p)(w - w_prev) + T.
+// The centre moves by the mean of the old and new velocity.  V and I are
+// those of a sphere (4/3 pi R^3, 2/5 m R^2) or a cylinder (pi R^2 times its
+// length: 1 in 2D, nz in 3D; 1/2 m R^2 about z).
+lbm_status advance_free(lbm_ctx *ctx, int slot) {
+  double rec[kMaxSolids * 6];
+  CK(cudaMemcpyAsync(rec, ctx->hist + (size_t)slot * kMaxSolids * 6, sizeof(rec),
+                     cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  const bool ibm = ctx->scheme.scheme == LBM_IBM_DIRECT;
+  for (size_t k = 0; k < ctx->solids.size(); k++) {
+    SolidHost &h = ctx->solids[k];
+    if (!(h.rho_p > 0)) continue;
+    const double R = h.d.radius;
+    const bool cyl = ctx->D == 2 || h.d.kind == LBM_CYLINDER_Z;
+    const double V = cyl ? PI * R * R * (ctx->D == 2 ? 1.0 : (double)ctx->d.nz)
+                         : 4.0 / 3.0 * PI * R * R * R;
+    const double m = h.rho_p * V, I = m * (cyl ? 0.5 : 0.4) * R * R;
+    double Un[3], On[3];
+    for (int a = 0; a < 3; a++) {
+      double dv = rec[6 * k + a] + (h.rho_p - 1.0) * V * h.g[a];
+      double dw = rec[6 * k + 3 + a];
+      if (ibm) {
+        dv += V * (h.d.velocity[a] - h.Up[a]);
+        dw += I / h.rho_p * (h.d.omega[a] - h.Omp[a]);
+      }
+      Un[a] = h.d.velocity[a] + dv / m;
+      On[a] = h.d.omega[a] + dw / I;
+    }
+    if (ctx->D == 2) Un[2] = 0;
+    if (cyl) On[0] = On[1] = 0;
+    for (int a = 0; a < 3; a++) {
+      h.c[a] += 0.5 * (h.d.velocity[a] + Un[a]);
+      h.Up[a] = h.d.velocity[a];
+      h.Omp[a] = h.d.omega[a];
+      h.d.velocity[a] = Un[a];
+      h.d.omega[a] = On[a];
+    }
+  }
+  return LBM_OK;
 }
 
 // link records: c0..c4, mw, uw[3], arm[3] in the compute type, then the solid id
@@ -852,10 +909,16 @@ lbm_status step_once(lbm_ctx *ctx) {
   if (moving && ctx->scheme.scheme == LBM_ZHAO_YONG)
     return fail(ctx, LBM_ERR_UNSUPPORTED,
                 "Eq. 16 keeps pre-collision values per boundary node: solids must not translate");
+  const bool free_ = any_free(ctx);
+  // IBM: the force of the previous step's pre-pass moves the free solids;
+  // the others move with their prescribed velocity
+  if (ibm && free_) TRY(advance_free(ctx, ctx->slot));
   if (ibm && moving)
     for (auto &s : ctx->solids)
-      for (int a = 0; a < 3; a++) s.c[a] += s.d.velocity[a];
-  const bool prefetch = moving && ctx->geom_prefetch;
+      if (!(s.rho_p > 0))
+        for (int a = 0; a < 3; a++) s.c[a] += s.d.velocity[a];
+  // free solids' next velocities are not known ahead: no prefetch
+  const bool prefetch = moving && ctx->geom_prefetch && !free_;
   if (prefetch && ctx->gst) CK(cudaEventRecord(ctx->ev_gfree, ctx->st));
   if (moving && !take_prefetched(ctx)) TRY(rebuild_boxes(ctx));
   if (prefetch && !ctx->gst) {
@@ -901,7 +964,10 @@ lbm_status step_once(lbm_ctx *ctx) {
   ctx->prev_local = false;
   if (!ibm && moving)
     for (auto &s : ctx->solids)
-      for (int k = 0; k < 3; k++) s.c[k] += s.d.velocity[k];
+      if (!(s.rho_p > 0))
+        for (int k = 0; k < 3; k++) s.c[k] += s.d.velocity[k];
+  // bounce-back: this step's momentum exchange moves the free solids
+  if (!ibm && free_) TRY(advance_free(ctx, ctx->slot));
   if (prefetch) {
     // the next step's geometry: bounce-back uses the centres just reached,
     // IBM moves first and uses them plus one step
@@ -1352,6 +1418,35 @@ lbm_status lbm_get_residual(lbm_ctx *ctx, double *r) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int id, double density_ratio,
+                                  const double gravity[3]) {
+  if (!ctx || id < 0 || id >= (int)ctx->solids.size() || !(density_ratio == density_ratio))
+    return LBM_ERR_ARG;
+  if (density_ratio > 0 && ctx->scheme.scheme != LBM_IBM_DIRECT && !is_ibb(ctx->scheme.scheme))
+    return fail(ctx, LBM_ERR_STATE, "free solids need a bounce-back or IBM scheme (set it first)");
+  if (density_ratio > 0 && ctx->scheme.scheme == LBM_ZHAO_YONG)
+    return fail(ctx, LBM_ERR_UNSUPPORTED, "Eq. 16 does not take translating solids");
+  SolidHost &h = ctx->solids[id];
+  h.rho_p = density_ratio > 0 ? density_ratio : 0;
+  for (int a = 0; a < 3; a++) {
+    h.g[a] = gravity ? gravity[a] : 0;
+    h.Up[a] = h.d.velocity[a];
+    h.Omp[a] = h.d.omega[a];
+  }
+  if (ctx->D == 2) h.g[2] = 0;
+  ctx->prefetched = false;
+  return LBM_OK;
+}
+
+lbm_status lbm_get_solid_velocity(lbm_ctx *ctx, int id, double U[3], double Om[3]) {
+  if (!ctx || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
+  for (int a = 0; a < 3; a++) {
+    if (U) U[a] = ctx->solids[id].d.velocity[a];
+    if (Om) Om[a] = ctx->solids[id].d.omega[a];
+  }
+  return LBM_OK;
+}
+
 lbm_status lbm_get_solid_centre(lbm_ctx *ctx, int id, double c[3]) {
   if (!ctx || id < 0 || id >= (int)ctx->solids.size() || !c) return LBM_ERR_ARG;
   memcpy(c, ctx->solids[id].c, 3 * sizeof(double));
@@ -1423,7 +1518,7 @@ lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size) {
   SaveHeader h;
   memset(&h, 0, sizeof(h));
   memcpy(h.magic, "LBMGB300", 8);
-  h.version = 2;  // 2: the scheme carries the delta-function kernel
+  h.version = 3;  // 2: the scheme carries the delta-function kernel; 3: solids their free motion
   h.lattice = ctx->d.lattice;
   h.nx = ctx->d.nx;
   h.ny = ctx->d.ny;
@@ -1454,7 +1549,7 @@ lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size) {
   if (!ctx || !host_buf || size < sizeof(SaveHeader)) return LBM_ERR_ARG;
   SaveHeader h;
   memcpy(&h, host_buf, sizeof(h));
-  if (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 2) return fail(ctx, LBM_ERR_ARG, "not a checkpoint of this version");
+  if (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 3) return fail(ctx, LBM_ERR_ARG, "not a checkpoint of this version");
   if (h.lattice != ctx->d.lattice || h.nx != ctx->d.nx || h.ny != ctx->d.ny || h.nz != ctx->d.nz ||
       h.precision != ctx->d.precision || h.nsolids < 0 || h.nsolids > kMaxSolids ||
       h.fs != ctx->fs)

@@ -90,6 +90,8 @@ def _load():
         "lbm_get_force_torque": (st, [vp, i, dp, dp]),
         "lbm_get_force_history": (st, [vp, i, dp, sz, C.POINTER(sz)]),
         "lbm_copy_force_torque_async": (st, [vp, i, dp]),
+        "lbm_set_solid_dynamics": (st, [vp, i, d, dp]),
+        "lbm_get_solid_velocity": (st, [vp, i, dp, dp]),
         "lbm_get_residual": (st, [vp, dp]),
         "lbm_get_solid_centre": (st, [vp, i, dp]),
         "lbm_get_info": (st, [vp, C.POINTER(lbm_info)]),
@@ -123,7 +125,7 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_get_distributions", "lbm_step", "lbm_run_to_steady", "lbm_get_density",
     "lbm_get_velocity", "lbm_get_strain_rate", "lbm_get_stress",
     "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
-    "lbm_copy_force_torque_async",
+    "lbm_copy_force_torque_async", "lbm_set_solid_dynamics", "lbm_get_solid_velocity",
     "lbm_get_residual", "lbm_get_solid_centre", "lbm_get_info",
     "lbm_device_field", "lbm_save", "lbm_load", "lbm_set_timing",
     "lbm_get_kernel_time", "lbm_get_velocity_noalloc", "lbm_sync", "lbm_last_error",
@@ -283,6 +285,15 @@ class Lattice:
         c = np.zeros(3)
         self._check(lbm_get_solid_centre(self.h, sid, _dp(c)))
         return c
+
+    def set_solid_dynamics(self, sid, density_ratio, gravity=None):
+        self._check(lbm_set_solid_dynamics(self.h, sid, float(density_ratio),
+                                           _dp(_v3(gravity))))
+
+    def solid_velocity(self, sid=0):
+        U, Om = np.zeros(3), np.zeros(3)
+        self._check(lbm_get_solid_velocity(self.h, sid, _dp(U), _dp(Om)))
+        return U, Om
 
     def info(self) -> lbm_info:
         i = lbm_info()

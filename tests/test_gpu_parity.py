@@ -427,3 +427,77 @@ def test_async_force_copy_matches_history(scheme):
     hist = g.force_history(0, p.steps)
     assert np.array_equal(buf, hist)
     g.close()
+
+
+def _free_problem(dim, scheme):
+    if dim == 3:
+        return W.Problem("free_sphere", W.D3Q19, 36, 30, 28, 0.7, W.MRT, W.FP64, (4e-5, 0, 0),
+                         [W.Solid(W.SPHERE, (17.3, 14.6, 13.8), 5.4,
+                                  velocity=(0.02, -0.015, 0.01), omega=(0.002, -0.001, 0.003))],
+                         scheme, 40)
+    return W.Problem("free_cylinder", W.D2Q9, 52, 44, 1, 0.7, W.BGK, W.FP64, (4e-5, 0, 0),
+                     [W.Solid(W.CYLINDER_Z, (24.3, 21.6, 0), 6.1,
+                              velocity=(0.02, -0.015, 0), omega=(0, 0, 0.003))],
+                     scheme, 60)
+
+
+@pytest.mark.parametrize("dim", [2, 3])
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.YU_LIN, W.IBM])
+def test_free_solid_fp64(dim, scheme):
+    """A free solid (Eq. 20 under bounce-back, Eq. 23 under IBM), heavier
+    than the fluid, moved across grid lines by its weight, the body-forced
+    flow, a random initial flow and its initial velocity and spin: the
+    fields, the force record, the centre and the velocities follow the
+    oracle."""
+    p = _free_problem(dim, scheme)
+    g, o = make_gpu(p), make_oracle(p)
+    gravity = (0.0, -4e-4, 2e-4 if dim == 3 else 0.0)
+    g.set_solid_dynamics(0, 1.5, gravity)
+    o.set_solid_dynamics(0, 1.5, gravity)
+    f0 = random_populations(p, seed=31, amplitude=0.02)
+    g.set_f(f0)
+    o.set_f(f0)
+    for chunk in (1, p.steps // 2 - 1, p.steps - p.steps // 2):
+        g.step(chunk)
+        o.step(chunk)
+        compare(g, o, FP64_TOL, tol_F=1e-10, what=("u", "rho"))
+        assert np.allclose(g.solid_centre(0), o.solid_centre(0), rtol=0, atol=1e-11)
+        (Ug, Og), (Uo, Oo) = g.solid_velocity(0), o.solid_velocity(0)
+        assert np.allclose(Ug, Uo, rtol=0, atol=1e-13 + 1e-10 * np.abs(Uo).max())
+        assert np.allclose(Og, Oo, rtol=0, atol=1e-13 + 1e-10 * np.abs(Oo).max())
+    # it has moved across grid lines and turned
+    assert np.linalg.norm(g.solid_centre(0) - np.array(p.solids[0].centre)) > 0.15
+    assert abs(Og[2]) > 5e-5
+    g.close()
+
+
+def test_free_solid_limits_and_release():
+    """Free motion wants a bounce-back or IBM scheme and refuses Eq. 16; a
+    density ratio <= 0 returns the solid to prescribed motion at its current
+    velocity; a free solid in fluid at rest stays at rest."""
+    from paper_1906_05445_gb300 import lbm
+    p = W.fixed_sphere(24, 4.3, seed=4, tau=0.8, g=0.0, scheme=W.NONE, precision=W.FP64, steps=4)
+    g = make_gpu(p)
+    with pytest.raises(lbm.LbmError, match="STATE"):
+        g.set_solid_dynamics(0, 2.0)
+    g.set_scheme(W.ZHAO_YONG)
+    with pytest.raises(lbm.LbmError, match="UNSUPPORTED"):
+        g.set_solid_dynamics(0, 2.0)
+    g.set_scheme(W.BOUZIDI_QUAD)
+    g.set_solid_dynamics(0, 2.0, (0, 0, 0))
+    g.step(20)
+    U, Om = g.solid_velocity(0)
+    assert np.abs(U).max() < 1e-15 and np.abs(Om).max() < 1e-15
+    c0 = g.solid_centre(0)
+    g.set_solid_dynamics(0, 2.0, (0, 0, -1e-3))
+    g.step(3)
+    U, _ = g.solid_velocity(0)
+    assert U[2] < 0
+    g.set_solid_dynamics(0, 0.0)
+    c1 = g.solid_centre(0)
+    g.step(5)
+    U2, _ = g.solid_velocity(0)
+    assert np.array_equal(U, U2)
+    assert np.allclose(g.solid_centre(0), c1 + 5 * U, rtol=0, atol=1e-12)
+    assert c1[2] < c0[2]
+    g.close()

@@ -27,6 +27,7 @@
 #include "lbm_oracle.h"
 
 #include <math.h>
+#include <stdio.h>
 #include <stdlib.h>
 #include <string.h>
 
@@ -389,6 +390,12 @@ struct ora_sim {
   long steps;
   long link_counts[8];
   coll_t coll;
+  /* domain faces x-, x+, y-, y+, z-, z+ (ORA_FACE_*), the velocity of each
+   * velocity face, and the pre-collision populations of the previous time
+   * level (outflow faces) */
+  int face[6], open;
+  double u_face[6][3];
+  double *fprev;
 };
 
 static long wrapi(long v, long n) {
@@ -467,6 +474,7 @@ void ora_destroy(ora_sim *s) {
   free(s->inside_prev);
   free(s->fibm);
   free(s->usnap);
+  free(s->fprev);
   free(s);
 }
 
@@ -879,6 +887,127 @@ static void free_motion(const ora_sim *s, const solid_t *b, double Un[3], double
   if (s->d == 2 || b->kind == ORA_CYLINDER_Z) On[0] = On[1] = 0;
 }
 
+/* ---- domain faces (Sec. 6: uniform flow past a sphere) ----
+ * A non-periodic face lies half a spacing outside the outermost nodes.  A
+ * pull from (x, y, z) along e_i that leaves the domain crosses one face, or
+ * two at an edge; bit 2a marks the low face of axis a, bit 2a + 1 the high
+ * one. */
+static int crossed(const ora_sim *s, long x, long y, long z, int i) {
+  const long src[3] = {x - s->e[i][0], y - s->e[i][1], z - s->e[i][2]};
+  const long len[3] = {s->nx, s->ny, s->nz};
+  int m = 0;
+  for (int a = 0; a < s->d; a++) {
+    if (src[a] < 0 && s->face[2 * a] != ORA_FACE_PERIODIC) m |= 1 << (2 * a);
+    if (src[a] >= len[a] && s->face[2 * a + 1] != ORA_FACE_PERIODIC) m |= 1 << (2 * a + 1);
+  }
+  return m;
+}
+
+static int crosses_type(const ora_sim *s, int m, int type) {
+  for (int k = 0; k < 6; k++)
+    if (((m >> k) & 1) && s->face[k] == type) return k;
+  return -1;
+}
+
+static void domain_abort(const char *what) {
+  fprintf(stderr, "oracle: %s\n", what);
+  abort();
+}
+
+/* f_i(x, t+1) when the pull along e_i leaves through velocity or free-slip
+ * faces only:
+ *  - a velocity face is a plane wall moving with its velocity u_f: the
+ *    population bounces back at the node, f_i = f*_ib + 2 rho0 w_i e_i.u_f
+ *    / cs^2 (the moving-wall term of the bounce-back rules, q = 1/2);
+ *  - free-slip faces reflect specularly: the value is f*_r at the node that
+ *    keeps x's coordinates on the crossed axes and x - e_i's on the others,
+ *    r being e_i with its crossed components reversed (no normal velocity
+ *    and no shear stress at the face: the stress-free condition). */
+static double wall_pull(const ora_sim *s, long x, long y, long z, int i, int m) {
+  const long N = s->N;
+  const int vf = crosses_type(s, m, ORA_FACE_VELOCITY);
+  if (vf >= 0) {
+    const double *u = s->u_face[vf];
+    const double eu = s->e[i][0] * u[0] + s->e[i][1] * u[1] + s->e[i][2] * u[2];
+    return s->fpost[(long)s->opp[i] * N + node(s, x, y, z)] + 2 * RHO0 * s->w[i] * eu / CS2;
+  }
+  int r[3] = {s->e[i][0], s->e[i][1], s->e[i][2]};
+  long src[3] = {x - s->e[i][0], y - s->e[i][1], z - s->e[i][2]};
+  const long at[3] = {x, y, z};
+  for (int a = 0; a < 3; a++)
+    if ((m >> (2 * a)) & 3) {
+      r[a] = -r[a];
+      src[a] = at[a];
+    }
+  int j = -1;
+  for (int k = 0; k < s->Q; k++)
+    if (s->e[k][0] == r[0] && s->e[k][1] == r[1] && s->e[k][2] == r[2]) j = k;
+  const long n = node(s, src[0], src[1], src[2]);
+  if (j < 0 || !simulated(s, n)) domain_abort("solid too close to a free-slip face");
+  return s->fpost[(long)j * N + n];
+}
+
+/* f_i(x, t+1) of plain streaming, or through velocity / free-slip faces. */
+static double side_pull(const ora_sim *s, long x, long y, long z, int i) {
+  const int m = crossed(s, x, y, z, i);
+  if (m == 0) {
+    const long n = node(s, x - s->e[i][0], y - s->e[i][1], z - s->e[i][2]);
+    if (!simulated(s, n)) domain_abort("solid too close to an outflow face");
+    return s->fpost[(long)i * s->N + n];
+  }
+  if (crosses_type(s, m, ORA_FACE_CONVECTIVE) >= 0) domain_abort("two outflow faces meet");
+  return wall_pull(s, x, y, z, i, m);
+}
+
+/* f_i(x, t+1) at a node whose pull along e_i leaves the domain (m != 0).
+ * A velocity face decides first, then an outflow face, then free slip.  At
+ * an outflow face with outward normal n the convective condition
+ * d(rho0 u)/dt + U_o d(rho0 u)/dn = 0 is imposed on each unknown population,
+ * upwind in space and implicit in the neighbour:
+ *   f_i(x, t+1) = [f_i(x, t) + U_o f_i(x - n, t+1)] / (1 + U_o),
+ * U_o = max(0, u(x, t).n), the outward velocity at the node at time t. */
+static double face_value(const ora_sim *s, long n, long x, long y, long z, int i, int m) {
+  if (crosses_type(s, m, ORA_FACE_VELOCITY) >= 0) return wall_pull(s, x, y, z, i, m);
+  const int cf = crosses_type(s, m, ORA_FACE_CONVECTIVE);
+  if (cf < 0) return wall_pull(s, x, y, z, i, m);
+  const int a = cf / 2;
+  const int sg = (cf & 1) ? 1 : -1;
+  long in[3] = {x, y, z};
+  in[a] -= sg;
+  const double vin = side_pull(s, in[0], in[1], in[2], i);
+  double j = 0, F[3];
+  for (int k = 0; k < s->Q; k++) j += s->fprev[(long)k * s->N + n] * s->e[k][a];
+  gext(s, n, F);
+  F[a] += s->fibm[a * s->N + n];
+  double U = sg * (j + 0.5 * F[a]) / RHO0;
+  if (U < 0) U = 0;
+  return (s->fprev[(long)i * s->N + n] + U * vin) / (1 + U);
+}
+
+int ora_set_domain(ora_sim *s, const int face[6], const double *u_face) {
+  for (int k = 0; k < 6; k++) {
+    const int t = face ? face[k] : ORA_FACE_PERIODIC;
+    if (t < ORA_FACE_PERIODIC || t > ORA_FACE_CONVECTIVE) return -1;
+    if (k >= 2 * s->d && t != ORA_FACE_PERIODIC) return -1;
+  }
+  int conv = 0;
+  for (int a = 0; a < 3; a++) {
+    const int lo = face ? face[2 * a] : 0, hi = face ? face[2 * a + 1] : 0;
+    if ((lo == ORA_FACE_PERIODIC) != (hi == ORA_FACE_PERIODIC)) return -1;
+    conv += (lo == ORA_FACE_CONVECTIVE) + (hi == ORA_FACE_CONVECTIVE);
+  }
+  if (conv > 1) return -1;
+  s->open = 0;
+  for (int k = 0; k < 6; k++) {
+    s->face[k] = face ? face[k] : ORA_FACE_PERIODIC;
+    s->open |= s->face[k] != ORA_FACE_PERIODIC;
+    for (int a = 0; a < 3; a++) s->u_face[k][a] = u_face ? u_face[3 * k + a] : 0;
+    if (s->d == 2) s->u_face[k][2] = 0;
+  }
+  if (conv && !s->fprev) s->fprev = (double *)calloc((size_t)s->Q * s->N, sizeof(double));
+  return 0;
+}
+
 /* Collision at every simulated node, then streaming (pull of post-collision
  * values) with the interpolated bounce-back rule on links whose upstream
  * node is solid, accumulating the momentum exchange of Eq. 17. */
@@ -900,7 +1029,8 @@ static void one_step(ora_sim *s) {
   if (is_ibb(s->scheme))
     for (int k = 0; k < s->nsol; k++)
       for (int a = 0; a < 3; a++) s->sol[k].F[a] = s->sol[k].T[a] = 0;
-  /* streaming */
+  /* streaming (outflow faces read the pre-collision populations of time t) */
+  if (s->fprev) memcpy(s->fprev, s->f, sizeof(double) * (size_t)Q * N);
   for (long n = 0; n < N; n++) {
     if (!simulated(s, n)) continue;
     long x, y, z;
@@ -910,6 +1040,11 @@ static void one_step(ora_sim *s) {
     double fpre[MAXQ];
     for (int i = 0; i < Q; i++) fpre[i] = s->f[(long)i * N + n];
     for (int i = 0; i < Q; i++) {
+      const int m = s->open ? crossed(s, x, y, z, i) : 0;
+      if (m) {
+        s->f[(long)i * N + n] = face_value(s, n, x, y, z, i, m);
+        continue;
+      }
       long src = node(s, x - s->e[i][0], y - s->e[i][1], z - s->e[i][2]);
       if (simulated(s, src)) {
         s->f[(long)i * N + n] = s->fpost[(long)i * N + src];

@@ -116,6 +116,16 @@ void ora_link_stats(const ora_sim *s, long counts[8]);
  * motion) and gravity; the solid's velocities then follow Eq. 20
  * (bounce-back) or Eq. 23 (IBM) every step */
 void ora_set_solid_dynamics(ora_sim *s, int id, double rho_ratio, const double g[3]);
+/* Domain faces x-, x+, y-, y+, z-, z+ (Sec. 6): periodic pairs, plane walls
+ * moving with u_face[3k..3k+2] (velocity inlet or no-slip wall), stress-free
+ * (specular) faces, and at most one convective outflow face.  Returns 0, or
+ * -1 for an unpaired periodic face, a z face on a 2D lattice or a second
+ * outflow face.  Solids must keep clear of non-periodic faces. */
+#define ORA_FACE_PERIODIC 0
+#define ORA_FACE_VELOCITY 1
+#define ORA_FACE_FREE_SLIP 2
+#define ORA_FACE_CONVECTIVE 3
+int ora_set_domain(ora_sim *s, const int face[6], const double *u_face);
 void ora_solid_velocity(const ora_sim *s, int id, double U[3], double Om[3]);
 
 /* ---- immersed-boundary primitives on a bare periodic grid (pin tests) ----

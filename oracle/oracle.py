@@ -62,6 +62,7 @@ def lib():
                 "ora_set_ibm_kernel": (None, [vp, i]),
                 "ora_set_solid_dynamics": (None, [vp, i, d, dp]),
                 "ora_solid_velocity": (None, [vp, i, dp, dp]),
+                "ora_set_domain": (i, [vp, C.POINTER(C.c_int), dp]),
                 "ora_create": (vp, [i, i, i, i, d, i, dp, dp, i]),
                 "ora_destroy": (None, [vp]),
                 "ora_add_solid": (i, [vp, i, dp, d, dp, dp, i]),
@@ -295,6 +296,14 @@ class OracleSim:
         c = np.zeros(3)
         self.L.ora_solid_centre(self.h, sid, _p(c))
         return c
+
+    def set_domain(self, faces, u_face=None):
+        """Face types x-, x+, y-, y+, z-, z+ and the velocity of each face
+        ([6][3]); raises ValueError where the oracle refuses them."""
+        fc = (C.c_int * 6)(*[int(t) for t in faces])
+        u = np.zeros((6, 3)) if u_face is None else np.ascontiguousarray(u_face, dtype=np.float64)
+        if self.L.ora_set_domain(self.h, fc, _p(u)) != 0:
+            raise ValueError(f"domain refused: {list(faces)}")
 
     def set_solid_dynamics(self, sid, rho_ratio, gravity=None):
         self.L.ora_set_solid_dynamics(self.h, sid, float(rho_ratio), _p(_vec3(gravity)))

@@ -176,6 +176,41 @@ lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int solid_id,
                                 const double omega[3]);
 lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme);
 
+/* Domain faces (Sec. 6, the uniform flow past a sphere in an open box).
+ * type[k] for the faces x-, x+, y-, y+, z-, z+; u[k] the velocity of a
+ * LBM_FACE_VELOCITY face.  A non-periodic face lies half a spacing outside
+ * the outermost nodes:
+ *  - LBM_FACE_VELOCITY: a plane wall moving with u[k] (a velocity inlet, or a
+ *    no-slip wall with u = 0): the populations leaving the domain bounce back
+ *    with the moving-wall term, f_i = f*_ib + 2 rho0 w_i e_i.u / cs^2;
+ *  - LBM_FACE_FREE_SLIP: stress-free (no normal velocity, no shear stress):
+ *    specular reflection;
+ *  - LBM_FACE_CONVECTIVE: outflow, d(rho0 u)/dt + U_o d(rho0 u)/dn = 0 on each
+ *    unknown population, upwind and implicit in the inner neighbour, U_o the
+ *    outward velocity at the face node in the previous step (clamped at 0).
+ * A link crossing two faces takes a velocity face's rule first, then the
+ * outflow's, then free slip.  The default is periodic on every face.
+ * Errors: LBM_ERR_ARG for an unknown type, a periodic face whose opposite
+ * face is not, a z face on a 2D lattice, a second outflow face or a
+ * non-periodic axis shorter than 3 nodes; LBM_ERR_STATE for an outflow face
+ * set after stepping (set it first, or right after lbm_init_equilibrium /
+ * lbm_set_distributions).  Solids must keep R + 5 nodes clear of every
+ * non-periodic face, and be neither fluid-inside nor z-cylinders crossing
+ * non-periodic z faces: else the next step or query returns
+ * LBM_ERR_UNSUPPORTED.  Checkpoints of a lattice with an outflow face are
+ * LBM_ERR_UNSUPPORTED.  NULL restores the periodic box. */
+enum {
+  LBM_FACE_PERIODIC = 0,
+  LBM_FACE_VELOCITY = 1,
+  LBM_FACE_FREE_SLIP = 2,
+  LBM_FACE_CONVECTIVE = 3
+};
+typedef struct {
+  int type[6];
+  double u[6][3];
+} lbm_domain_desc;
+lbm_status lbm_set_domain(lbm_ctx *ctx, const lbm_domain_desc *domain);
+
 /* Set the state to the equilibrium at (rho, u) on every fluid node. */
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, double rho, const double u[3]);
 /* Set / read the pre-collision distributions f(x, t) (full f, not f - w):

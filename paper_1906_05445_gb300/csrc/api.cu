@@ -119,6 +119,14 @@ struct lbm_ctx {
   // Eq. 16: pre-collision populations kept at the boundary nodes ([Q][fs],
   // compute type; allocated when the scheme is first selected)
   void *zy_pre = nullptr;
+  // domain faces: types and wall velocities, the nodes next to a
+  // non-periodic face, and the outflow face's kept populations
+  lbm_domain_desc dom{};
+  int *face_node = nullptr;
+  int nface = 0;
+  void *outlet = nullptr;
+  int out_face = -1;
+  long long out_area = 0;
   double pf_c[kMaxSolids][3] = {};
   cudaStream_t gst = nullptr;
   cudaEvent_t ev_geom = nullptr, ev_gfree = nullptr;
@@ -303,6 +311,18 @@ KArgs base_args(lbm_ctx *ctx) {
                           ctx->ibb_list_thread ? 1 : 0;
   a.list_block = ctx->list_block;
   a.zy_pre = ctx->scheme.scheme == LBM_ZHAO_YONG ? ctx->zy_pre : nullptr;
+  for (int k = 0; k < 6; k++) {
+    a.face[k] = ctx->dom.type[k];
+    for (int c = 0; c < 3; c++) {
+      a.u_face[k][c] = ctx->D == 2 && c == 2 ? 0.0 : ctx->dom.u[k][c];
+      a.u_face_f[k][c] = (float)a.u_face[k][c];
+    }
+  }
+  a.face_node = ctx->face_node;
+  a.nface = ctx->nface;
+  a.outlet = ctx->outlet;
+  a.out_face = ctx->out_face;
+  a.out_area = ctx->out_area;
   a.flags = ctx->flags;
   a.omega = ctx->omega;
   for (int k = 0; k < 19; k++) a.ds[k] = ctx->ds[k];
@@ -572,7 +592,28 @@ GeomArgs geom_args(lbm_ctx *ctx) {
   g.refill_sid = ctx->refill_sid;
   g.refill_cap = ctx->refill_cap;
   g.band_w = 2.0 * sqrt((double)ctx->D) + 1e-6;
+  for (int k = 0; k < 6; k++) g.face[k] = ctx->dom.type[k];
   return g;
+}
+
+// Solids keep R + 5 nodes clear of every non-periodic face: the
+// interpolation stencils of the bounce-back rules (x_f + 2 e_i), the IBM
+// band and delta stencils and the refilled nodes then never meet the face
+// nodes, which run in their own kernel.
+lbm_status check_clearance(lbm_ctx *ctx) {
+  const int len[3] = {ctx->d.nx, ctx->d.ny, ctx->D == 2 ? 1 : ctx->d.nz};
+  for (auto &h : ctx->solids)
+    for (int a = 0; a < ctx->D; a++) {
+      if (ctx->dom.type[2 * a] == LBM_FACE_PERIODIC) continue;
+      if (h.d.fluid_inside)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "a fluid-inside solid fills the domain up to its non-periodic faces");
+      if (a == 2 && h.d.kind == LBM_CYLINDER_Z)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "a z-cylinder meets the non-periodic z faces");
+      const double m = h.d.radius + 5.0;
+      if (h.c[a] - m < 0 || h.c[a] + m > len[a] - 1)
+        return fail(ctx, LBM_ERR_UNSUPPORTED, "solid within R + 5 nodes of a non-periodic face");
+    }
+  return LBM_OK;
 }
 
 void set_boxes(lbm_ctx *ctx, GeomArgs &g, bool full) {
@@ -797,6 +838,7 @@ bool take_prefetched(lbm_ctx *ctx) {
 }
 
 lbm_status ensure_geometry(lbm_ctx *ctx) {
+  if (ctx->nface) TRY(check_clearance(ctx));
   if (ctx->geom_dirty) return rebuild_full(ctx);
   return LBM_OK;
 }
@@ -891,6 +933,7 @@ lbm_status init_collide(lbm_ctx *ctx) {
   a.dst = ctx->f[ctx->cur];
   sweep(ctx, OP_LOCAL_INIT, a);
   if (ctx->scheme.scheme == LBM_ZHAO_YONG) sweep(ctx, OP_ZY_SEED, a);
+  if (ctx->outlet) sweep(ctx, OP_FACE_SEED, a);
   ctx->need_collide = false;
   ctx->prev_local = true;
   ctx->records = std::min<long long>(ctx->records + 1, kHistCap);
@@ -919,6 +962,7 @@ lbm_status step_once(lbm_ctx *ctx) {
         for (int a = 0; a < 3; a++) s.c[a] += s.d.velocity[a];
   // free solids' next velocities are not known ahead: no prefetch
   const bool prefetch = moving && ctx->geom_prefetch && !free_;
+  if (moving && ctx->nface) TRY(check_clearance(ctx));
   if (prefetch && ctx->gst) CK(cudaEventRecord(ctx->ev_gfree, ctx->st));
   if (moving && !take_prefetched(ctx)) TRY(rebuild_boxes(ctx));
   if (prefetch && !ctx->gst) {
@@ -953,6 +997,8 @@ lbm_status step_once(lbm_ctx *ctx) {
     Timed tm(ctx, TK_LIST, ctx->list_count >= 0 ? ctx->list_count : 0, ctx->aux);
     sweep(ctx, OP_LIST_SWEEP, a, ctx->aux);
   }
+  // nodes next to non-periodic domain faces
+  if (ctx->nface) sweep(ctx, OP_FACE_SWEEP, a, ctx->aux);
   {
     Timed tm(ctx, TK_BULK, ctx->bulk_nodes, ctx->st);
     sweep(ctx, OP_BULK_SWEEP, a, ctx->st);
@@ -1001,6 +1047,7 @@ void run_query(lbm_ctx *ctx, KArgs a) {
     a.local_gather = 0;
     sweep(ctx, OP_BULK_QUERY, a);
     sweep(ctx, OP_LIST_QUERY, a);
+    if (ctx->nface) sweep(ctx, OP_FACE_QUERY, a);
   }
 }
 
@@ -1418,6 +1465,72 @@ lbm_status lbm_get_residual(lbm_ctx *ctx, double *r) {
   return LBM_OK;
 }
 
+lbm_status lbm_set_domain(lbm_ctx *ctx, const lbm_domain_desc *dom) {
+  if (!ctx) return LBM_ERR_ARG;
+  lbm_domain_desc d{};
+  if (dom) d = *dom;
+  const int len[3] = {ctx->d.nx, ctx->d.ny, ctx->D == 2 ? 1 : ctx->d.nz};
+  int conv = -1, open_axes = 0;
+  for (int k = 0; k < 6; k++) {
+    if (d.type[k] < LBM_FACE_PERIODIC || d.type[k] > LBM_FACE_CONVECTIVE)
+      return fail(ctx, LBM_ERR_ARG, "unknown face type");
+    for (int c = 0; c < 3; c++)
+      if (!(d.u[k][c] == d.u[k][c])) return fail(ctx, LBM_ERR_ARG, "face velocity is NaN");
+    if (d.type[k] == LBM_FACE_CONVECTIVE) {
+      if (conv >= 0) return fail(ctx, LBM_ERR_ARG, "at most one convective outflow face");
+      conv = k;
+    }
+  }
+  for (int a = 0; a < 3; a++) {
+    const bool lo = d.type[2 * a] != LBM_FACE_PERIODIC, hi = d.type[2 * a + 1] != LBM_FACE_PERIODIC;
+    if (lo != hi) return fail(ctx, LBM_ERR_ARG, "periodic faces come in pairs");
+    if (!lo) continue;
+    if (a == 2 && ctx->D == 2) return fail(ctx, LBM_ERR_ARG, "a 2D lattice has no z faces");
+    if (len[a] < 3) return fail(ctx, LBM_ERR_ARG, "a non-periodic axis needs at least 3 nodes");
+    open_axes |= 1 << a;
+  }
+  if (conv >= 0 && !ctx->need_collide)
+    return fail(ctx, LBM_ERR_STATE,
+                "an outflow face is set before stepping or right after an initialisation");
+  CK(cudaStreamSynchronize(ctx->st));
+  // nodes next to a non-periodic face, in node order
+  std::vector<int> nodes;
+  if (open_axes)
+    for (long long n = 0; n < ctx->N; n++) {
+      const int x = (int)(n % len[0]), y = (int)((n / len[0]) % len[1]),
+                z = (int)(n / ((long long)len[0] * len[1]));
+      const int c[3] = {x, y, z};
+      bool on = false;
+      for (int a = 0; a < 3 && !on; a++)
+        on = ((open_axes >> a) & 1) && (c[a] == 0 || c[a] == len[a] - 1);
+      if (on) nodes.push_back((int)n);
+    }
+  dfree(ctx, ctx->face_node);
+  dfree(ctx, ctx->outlet);
+  ctx->face_node = nullptr;
+  ctx->outlet = nullptr;
+  ctx->nface = 0;
+  ctx->out_face = -1;
+  ctx->out_area = 0;
+  if (!nodes.empty()) {
+    TRY(dalloc(ctx, (void **)&ctx->face_node, nodes.size() * sizeof(int)));
+    CK(cudaMemcpy(ctx->face_node, nodes.data(), nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
+    ctx->nface = (int)nodes.size();
+  }
+  if (conv >= 0) {
+    const int a = conv / 2;
+    ctx->out_face = conv;
+    ctx->out_area = a == 0 ? (long long)len[1] * len[2] : a == 1 ? (long long)len[0] * len[2]
+                                                                  : (long long)len[0] * len[1];
+    const size_t bytes = (size_t)(ctx->Q + 1) * ctx->out_area * ctx->tsz;
+    TRY(dalloc(ctx, &ctx->outlet, bytes));
+    CK(cudaMemset(ctx->outlet, 0, bytes));
+  }
+  ctx->dom = d;
+  ctx->geom_dirty = true;
+  return LBM_OK;
+}
+
 lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int id, double density_ratio,
                                   const double gravity[3]) {
   if (!ctx || id < 0 || id >= (int)ctx->solids.size() || !(density_ratio == density_ratio))
@@ -1507,6 +1620,8 @@ lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size) {
   if (!ctx || !size) return LBM_ERR_ARG;
   if (ctx->scheme.scheme == LBM_ZHAO_YONG)
     return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints do not carry the Eq. 16 boundary state");
+  if (ctx->outlet)
+    return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints do not carry the outflow face's state");
   const size_t fb = (size_t)ctx->Q * ctx->fs * ctx->ssz;
   const size_t total = sizeof(SaveHeader) + sizeof(SolidHost) * ctx->solids.size() + 2 * fb + ctx->N;
   if (!host_buf) {
@@ -1547,6 +1662,8 @@ lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size) {
 
 lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size) {
   if (!ctx || !host_buf || size < sizeof(SaveHeader)) return LBM_ERR_ARG;
+  if (ctx->outlet)
+    return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints do not carry the outflow face's state");
   SaveHeader h;
   memcpy(&h, host_buf, sizeof(h));
   if (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 3) return fail(ctx, LBM_ERR_ARG, "not a checkpoint of this version");

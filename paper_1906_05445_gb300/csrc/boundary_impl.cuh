@@ -640,6 +640,182 @@ __global__ void __launch_bounds__(128) k_zy_seed(const KArgs a) {
         Store<S>::ld((const S *)a.src + (long long)i * a.fs + n, isc);
 }
 
+// ---------------------------------------------------------------- domain
+// faces (the open box of the uniform flow past a sphere, Sec. 6).  A
+// non-periodic face lies half a spacing outside the outermost nodes; the
+// nodes next to one (flag FL_FACE) run in k_face, a thread per node, which
+// pulls like the bulk sweep except on links that leave the domain:
+//  - velocity face (plane wall moving with u_f): f_i = f*_ib(x) + 6 w_i e_i.u_f
+//    (the moving-wall bounce-back with q = 1/2, rho0 = 1);
+//  - stress-free face: specular reflection, f_i = f*_r(x'), r = e_i with the
+//    crossed components reversed and x' = x - e_i with x's coordinates on the
+//    crossed axes;
+//  - convective outflow face (outward normal n): f_i(x, t+1) =
+//    [f_i(x, t) + U_o f_i(x - n, t+1)] / (1 + U_o), U_o = max(0, u(x, t).n),
+//    from the node's pre-collision populations and velocity kept from the
+//    previous step (a.outlet, [Q + 1][face area] in the compute type).
+// A velocity face decides a link that crosses two faces, then an outflow
+// face, then free slip.
+
+// bit 2a: the low face of axis a is crossed, bit 2a + 1: the high face
+template <int LAT>
+__device__ __forceinline__ int face_cross(const KArgs &a, int x, int y, int z, int i) {
+  using L = Lat<LAT>;
+  const int sx = x - L::ex(i), sy = y - L::ey(i), sz = z - L::ez(i);
+  int m = 0;
+  if (sx < 0 && a.face[0]) m |= 1;
+  if (sx >= a.nx && a.face[1]) m |= 2;
+  if (sy < 0 && a.face[2]) m |= 4;
+  if (sy >= a.ny && a.face[3]) m |= 8;
+  if (L::D == 3) {
+    if (sz < 0 && a.face[4]) m |= 16;
+    if (sz >= a.nz && a.face[5]) m |= 32;
+  }
+  return m;
+}
+
+__device__ __forceinline__ int face_of_type(const KArgs &a, int m, int type) {
+  for (int k = 0; k < 6; k++)
+    if (((m >> k) & 1) && a.face[k] == type) return k;
+  return -1;
+}
+
+template <typename T> __device__ __forceinline__ T face_u(const KArgs &a, int k, int c) {
+  if constexpr (is_f32<T>()) return a.u_face_f[k][c];
+  else return (T)a.u_face[k][c];
+}
+
+// f_i(x, t+1) of a link that leaves through velocity / stress-free faces
+template <int LAT, typename S, typename T>
+__device__ __forceinline__ T face_wall(const KArgs &a, const S *__restrict__ src, int x, int y,
+                                       int z, int i, int m, T isc) {
+  using L = Lat<LAT>;
+  const long long fs = a.fs;
+  const int vf = face_of_type(a, m, LBM_FACE_VELOCITY);
+  if (vf >= 0) {
+    const long long n = x + (long long)a.nx * (y + (long long)a.ny * z);
+    const T eu = (T)L::ex(i) * face_u<T>(a, vf, 0) + (T)L::ey(i) * face_u<T>(a, vf, 1) +
+                 (T)L::ez(i) * face_u<T>(a, vf, 2);
+    return Store<S>::ld(src + (long long)L::opp(i) * fs + n, isc) + (T)(6.0 * L::w(i)) * eu;
+  }
+  int r[3] = {L::ex(i), L::ey(i), L::ez(i)};
+  int p[3] = {x - r[0], y - r[1], z - r[2]};
+  const int at[3] = {x, y, z};
+#pragma unroll
+  for (int c = 0; c < 3; c++)
+    if ((m >> (2 * c)) & 3) {
+      r[c] = -r[c];
+      p[c] = at[c];
+    }
+  int j = 0;
+#pragma unroll
+  for (int k = 1; k < L::Q; k++)
+    if (L::ex(k) == r[0] && L::ey(k) == r[1] && L::ez(k) == r[2]) j = k;
+  const long long ns = wrap(p[0], a.nx) +
+                       (long long)a.nx * (wrap(p[1], a.ny) + (long long)a.ny * wrap(p[2], a.nz));
+  return Store<S>::ld(src + (long long)j * fs + ns, isc);
+}
+
+// f_i(x, t+1) of a node: plain pull, or through velocity / stress-free faces
+template <int LAT, typename S, typename T>
+__device__ __forceinline__ T face_pull(const KArgs &a, const S *__restrict__ src, int x, int y,
+                                       int z, int i, T isc) {
+  using L = Lat<LAT>;
+  const int m = face_cross<LAT>(a, x, y, z, i);
+  if (m) return face_wall<LAT, S, T>(a, src, x, y, z, i, m, isc);
+  const long long ns = wrap(x - L::ex(i), a.nx) +
+                       (long long)a.nx * (wrap(y - L::ey(i), a.ny) +
+                                          (long long)a.ny * wrap(z - L::ez(i), a.nz));
+  return Store<S>::ld(src + (long long)i * a.fs + ns, isc);
+}
+
+// index of a node of the outflow face in the outlet arrays
+__device__ __forceinline__ int outlet_index(const KArgs &a, int x, int y, int z) {
+  const int ax = a.out_face >> 1;
+  return ax == 0 ? y + a.ny * z : ax == 1 ? x + a.nx * z : x + a.nx * y;
+}
+__device__ __forceinline__ bool on_outlet(const KArgs &a, int x, int y, int z) {
+  if (a.out_face < 0) return false;
+  const int ax = a.out_face >> 1, hi = a.out_face & 1;
+  const int c = ax == 0 ? x : ax == 1 ? y : z;
+  const int len = ax == 0 ? a.nx : ax == 1 ? a.ny : a.nz;
+  return c == (hi ? len - 1 : 0);
+}
+
+// MODE 0: sweep (src f*(t) -> dst f*(t+1)); MODE 1: query of f(t) from
+// src = f*(t - 1); MODE 2: keep the outflow face's populations and velocity
+// from a state held locally in src (right after an initialisation).
+template <int LAT, int CM, typename S, typename T, typename LT, int MODE>
+__global__ void __launch_bounds__(128) k_face(const KArgs a) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q;
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= a.nface) return;
+  const long long n = a.face_node[t];
+  int x, y, z;
+  node_xyz(n, a.nx, a.ny, x, y, z);
+  const T isc = kisc<T>(a);
+  const S *__restrict__ src = (const S *)a.src;
+  const bool out = on_outlet(a, x, y, z);
+  const long long A = a.out_area;
+  LT *keep = (LT *)a.outlet;
+  const int oi = out ? outlet_index(a, x, y, z) : 0;
+  const uint8_t fl = a.flags[n];
+  T Fx, Fy, Fz;
+  node_force<T, LT>(a, n, fl, Fx, Fy, Fz);
+  T f[Q];
+  if (MODE == 2) {
+    if (!out) return;
+    gather_local<LAT, S, T>(src, a.fs, n, isc, f);
+  } else {
+    const int ax = a.out_face >> 1, sg = (a.out_face & 1) ? 1 : -1;
+#pragma unroll
+    for (int i = 0; i < Q; i++) {
+      const int m = face_cross<LAT>(a, x, y, z, i);
+      if (m == 0) {
+        const long long ns = wrap(x - L::ex(i), a.nx) +
+                             (long long)a.nx * (wrap(y - L::ey(i), a.ny) +
+                                                (long long)a.ny * wrap(z - L::ez(i), a.nz));
+        f[i] = Store<S>::ld(src + (long long)i * a.fs + ns, isc);
+      } else if (face_of_type(a, m, LBM_FACE_VELOCITY) < 0 &&
+                 face_of_type(a, m, LBM_FACE_CONVECTIVE) >= 0) {
+        if (MODE == 1) {
+          f[i] = (T)keep[(long long)i * A + oi];  // f_i(x, t), kept by the last step
+        } else {
+          const int xi = x - (ax == 0 ? sg : 0), yi = y - (ax == 1 ? sg : 0),
+                    zi = z - (ax == 2 ? sg : 0);
+          const T vin = face_pull<LAT, S, T>(a, src, xi, yi, zi, i, isc);
+          T U = (T)keep[(long long)Q * A + oi];
+          if (U < (T)0) U = (T)0;
+          f[i] = ((T)keep[(long long)i * A + oi] + U * vin) / ((T)1 + U);
+        }
+      } else {
+        f[i] = face_wall<LAT, S, T>(a, src, x, y, z, i, m, isc);
+      }
+    }
+  }
+  if (MODE != 1 && out) {
+    // this step's pre-collision populations and outward velocity, read by
+    // the next step's outflow update
+    T j = (T)0;
+#pragma unroll
+    for (int i = 0; i < Q; i++) keep[(long long)i * A + oi] = (LT)f[i];
+    const int ax = a.out_face >> 1;
+#pragma unroll
+    for (int i = 0; i < Q; i++)
+      j += (T)(ax == 0 ? L::ex(i) : ax == 1 ? L::ey(i) : L::ez(i)) * f[i];
+    const T Fa = ax == 0 ? Fx : ax == 1 ? Fy : Fz;
+    keep[(long long)Q * A + oi] = (LT)(((a.out_face & 1) ? (T)1 : (T)-1) * (j + (T)0.5 * Fa));
+  }
+  if (MODE == 0) {
+    const Coll<T> c = make_coll<LAT, T>(a);
+    collide<LAT, CM, T>(f, Fx, Fy, Fz, c);
+    scatter<LAT, S, T>((S *)a.dst, a.fs, n, isc, f);
+  } else if (MODE == 1) {
+    write_fields<LAT, T>(a, n, f, Fx, Fy, Fz);
+  }
+}
+
 // ---------------------------------------------------------------- launch
 inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 
@@ -729,6 +905,15 @@ void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
     break;
   case OP_FILL_EQ:
     k_fill_eq<LAT, S, T><<<div_up(a.N, 256), 256, 0, st>>>(a);
+    break;
+  case OP_FACE_SWEEP:
+    if (a.nface > 0) k_face<LAT, CM, S, T, T, 0><<<div_up(a.nface, 128), 128, 0, st>>>(a);
+    break;
+  case OP_FACE_QUERY:
+    if (a.nface > 0) k_face<LAT, CM, S, double, T, 1><<<div_up(a.nface, 128), 128, 0, st>>>(a);
+    break;
+  case OP_FACE_SEED:
+    if (a.nface > 0 && a.outlet) k_face<LAT, CM, S, T, T, 2><<<div_up(a.nface, 128), 128, 0, st>>>(a);
     break;
   }
 }

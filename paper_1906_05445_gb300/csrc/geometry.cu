@@ -104,6 +104,9 @@ __global__ void k_geom_flags(const GeomArgs g, uint8_t *sid_new) {
       if (r2 <= hi * hi && (lo <= 0 || r2 >= lo * lo)) fl |= FL_BAND;
     }
   }
+  if ((g.face[0] && x == 0) || (g.face[1] && x == g.nx - 1) || (g.face[2] && y == 0) ||
+      (g.face[3] && y == g.ny - 1) || (g.face[4] && z == 0) || (g.face[5] && z == g.nz - 1))
+    fl |= FL_FACE;
   g.flags[n] = fl;
   sid_new[n] = (uint8_t)s_in;
 }

@@ -356,7 +356,8 @@ enum : uint8_t {
   FL_LIST = 2,   // handled by the boundary-node kernel
   FL_NOG = 4,    // the external body force does not act
   FL_BAND = 8,   // the IBM force may be non-zero
-  FL_NEW = 16    // uncovered by a moving solid; refilled before the sweep
+  FL_NEW = 16,   // uncovered by a moving solid; refilled before the sweep
+  FL_FACE = 32   // next to a non-periodic domain face (the face kernel)
 };
 
 }  // namespace lbm

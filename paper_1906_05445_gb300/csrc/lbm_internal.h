@@ -86,6 +86,17 @@ struct KArgs {
   int bulk_vec_words;  // vector sweep: 32-bit words per thread and direction (2 or 4; 0 = 2)
   int bulk_vec_packed; // vector sweep: 1 packed FP32x2 collision of node pairs, 0 node by
                        // node, -1 by storage type
+  // domain faces x-, x+, y-, y+, z-, z+ (LBM_FACE_*), their wall velocities,
+  // the nodes next to a non-periodic face, and the outflow face's kept
+  // populations and outward velocity (LT [Q + 1][out_area]; out_face -1: none)
+  int face[6];
+  double u_face[6][3];
+  float u_face_f[6][3];
+  const int *face_node;
+  int nface;
+  void *outlet;
+  int out_face;
+  long long out_area;
 };
 
 // kernel families timed by lbm_set_timing
@@ -103,7 +114,10 @@ enum SweepOp {
   OP_REFILL,       // equilibrium refill of uncovered nodes (+ collide)
   OP_BAND_VEL,     // IBM: unforced velocity at band nodes, zero the IBM force
   OP_FROM_DOUBLE,  // convert a full-f FP64 array (out_f) into deviations (dst)
-  OP_FILL_EQ       // fill dst with equilibrium deviations (g[] = u, omega = rho)
+  OP_FILL_EQ,      // fill dst with equilibrium deviations (g[] = u, omega = rho)
+  OP_FACE_SWEEP,   // nodes next to a non-periodic domain face: pull with the face rules + collide
+  OP_FACE_QUERY,   // the same nodes, fields
+  OP_FACE_SEED     // outflow face: keep the populations of a state held locally
 };
 
 // Launch one operation for the given lattice/collision/precision.  grid
@@ -134,6 +148,7 @@ struct GeomArgs {
   uint8_t *refill_sid;
   int refill_cap;
   int track_new;  // mark nodes uncovered since the previous geometry
+  int face[6];    // domain face types (FL_FACE on the nodes next to a non-periodic face)
   double band_w;  // IBM band half width
   GeomBox box[kMaxSolids];
   int nbox;

@@ -31,6 +31,7 @@ SPHERE, CYLINDER_Z = 0, 1
  IBM_DIRECT, ZHAO_YONG) = range(8)
 TK_BULK, TK_LIST, TK_IBM, TK_GEOM = range(4)
 DELTA_PESKIN4, DELTA_ROMA3, DELTA_LINEAR2, DELTA_COSINE4 = range(4)
+FACE_PERIODIC, FACE_VELOCITY, FACE_FREE_SLIP, FACE_CONVECTIVE = range(4)
 # lbm_set_timing masks: every kind, or bit (kind + 1) per kind
 TIME_ALL = 1
 TIME_BULK, TIME_LIST, TIME_IBM, TIME_GEOM = (2 << k for k in range(4))
@@ -53,6 +54,10 @@ class lbm_scheme_desc(C.Structure):
     _fields_ = [("scheme", C.c_int), ("ibm_iters", C.c_int),
                 ("ibm_retraction", C.c_double), ("ibm_marker_density", C.c_double),
                 ("ibm_kernel", C.c_int)]
+
+
+class lbm_domain_desc(C.Structure):
+    _fields_ = [("type", C.c_int * 6), ("u", (C.c_double * 3) * 6)]
 
 
 class lbm_info(C.Structure):
@@ -91,6 +96,7 @@ def _load():
         "lbm_get_force_history": (st, [vp, i, dp, sz, C.POINTER(sz)]),
         "lbm_copy_force_torque_async": (st, [vp, i, dp]),
         "lbm_set_solid_dynamics": (st, [vp, i, d, dp]),
+        "lbm_set_domain": (st, [vp, C.POINTER(lbm_domain_desc)]),
         "lbm_get_solid_velocity": (st, [vp, i, dp, dp]),
         "lbm_get_residual": (st, [vp, dp]),
         "lbm_get_solid_centre": (st, [vp, i, dp]),
@@ -126,6 +132,7 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_get_velocity", "lbm_get_strain_rate", "lbm_get_stress",
     "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
     "lbm_copy_force_torque_async", "lbm_set_solid_dynamics", "lbm_get_solid_velocity",
+    "lbm_set_domain",
     "lbm_get_residual", "lbm_get_solid_centre", "lbm_get_info",
     "lbm_device_field", "lbm_save", "lbm_load", "lbm_set_timing",
     "lbm_get_kernel_time", "lbm_get_velocity_noalloc", "lbm_sync", "lbm_last_error",
@@ -183,6 +190,8 @@ class Lattice:
         for s in p.solids:
             lat.add_solid(s.kind, s.centre, s.radius, s.velocity, s.omega, s.fluid_inside)
         lat.set_scheme(p.scheme, p.ibm_iters, p.retraction, p.marker_density, p.ibm_kernel)
+        if p.faces is not None:
+            lat.set_domain(p.faces, p.u_face)
         return lat
 
     def _check(self, st: int):
@@ -285,6 +294,20 @@ class Lattice:
         c = np.zeros(3)
         self._check(lbm_get_solid_centre(self.h, sid, _dp(c)))
         return c
+
+    def set_domain(self, faces=None, u_face=None):
+        """Face types x-, x+, y-, y+, z-, z+ (FACE_*) and the [6][3] wall
+        velocities of the velocity faces; None restores the periodic box."""
+        if faces is None:
+            self._check(lbm_set_domain(self.h, None))
+            return
+        d = lbm_domain_desc()
+        u = np.zeros((6, 3)) if u_face is None else np.asarray(u_face, dtype=np.float64)
+        for k in range(6):
+            d.type[k] = int(faces[k])
+            for c in range(3):
+                d.u[k][c] = float(u[k][c])
+        self._check(lbm_set_domain(self.h, C.byref(d)))
 
     def set_solid_dynamics(self, sid, density_ratio, gravity=None):
         self._check(lbm_set_solid_dynamics(self.h, sid, float(density_ratio),

@@ -58,6 +58,10 @@ class Problem:
     marker_density: float = 1.0
     force_all: bool = False
     ibm_kernel: int = 0  # PESKIN4, ROMA3, LINEAR2, COSINE4
+    # domain faces x-, x+, y-, y+, z-, z+ (PERIODIC, VELOCITY, FREE_SLIP,
+    # CONVECTIVE) and the [6][3] velocities of the velocity faces; None: periodic
+    faces: Optional[Tuple[int, ...]] = None
+    u_face: Optional[Tuple[Tuple[float, float, float], ...]] = None
 
     @property
     def nodes(self) -> int:
@@ -145,6 +149,28 @@ def translating_sphere(nx: int = 256, ny: int = 128, nz: int = 128,
                    precision, (0.0, 0.0, 0.0),
                    [Solid(SPHERE, c, radius, velocity=(u, 0.0, 0.0))],
                    scheme, steps)
+
+
+def open_sphere(D: float = 8.0, re: float = 20.0, nu: float = 0.02, seed: int = 1906,
+                scheme: int = BOUZIDI_QUAD, precision: int = FP64, collision: int = MRT,
+                steps: int = 4000, length=(24, 12, 12), centre=(6, 6, 6),
+                ibm_iters: int = 1, retraction: float = 0.0) -> Problem:
+    """Uniform flow past a fixed sphere in an open box (Sec. 6): a box of
+    length x (24D, 12D, 12D), the sphere of diameter D at (6D, 6D, 6D) plus a
+    sub-node offset drawn from the seed, a velocity inlet U = Re nu / D at
+    x = 0, stress-free sides and a convective outflow at x = Lx (the caller
+    starts the fluid as the uniform stream, lbm_init_equilibrium(1, U))."""
+    n = [int(round(k * D)) for k in length]
+    rng = np.random.default_rng(seed)
+    c = tuple(float(k * D + rng.uniform(-0.5, 0.5)) for k in centre)
+    U = re * nu / D
+    tau = 3 * nu + 0.5
+    u_face = ((U, 0.0, 0.0),) + ((0.0, 0.0, 0.0),) * 5
+    return Problem(f"open_sphere_D{D:g}_Re{re:g}", D3Q19, n[0], n[1], n[2], tau, collision,
+                   precision, (0.0, 0.0, 0.0), [Solid(SPHERE, c, D / 2)], scheme, steps,
+                   ibm_iters=ibm_iters, retraction=retraction,
+                   faces=(VELOCITY, CONVECTIVE, FREE_SLIP, FREE_SLIP, FREE_SLIP, FREE_SLIP),
+                   u_face=u_face)
 
 
 def convergence_batch(count: int = 32, seed: int = 1906, tau: float = 0.6,

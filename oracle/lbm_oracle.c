@@ -370,6 +370,10 @@ typedef struct {
    * rho_p / rho_f, gravity, and the velocities of the previous step */
   int free_;
   double rho_p, g[3], Up[3], Omp[3];
+  /* Kempe's treatment (Eq. 24): the fluid momentum and angular momentum
+   * inside the solid at the previous step, once one has been taken */
+  int have_Ip;
+  double Ip[6], In[6];
 } solid_t;
 
 struct ora_sim {
@@ -385,7 +389,7 @@ struct ora_sim {
   double *usnap;               /* [3][N] */
   int nsol;
   solid_t sol[MAXS];
-  int scheme, ibm_iters, ibm_kernel;
+  int scheme, ibm_iters, ibm_kernel, ibm_inertia;
   double retraction, density;
   long steps;
   long link_counts[8];
@@ -606,6 +610,11 @@ void ora_set_scheme(ora_sim *s, int scheme, int ibm_iters, double retraction,
   for (int k = 0; k < s->nsol; k++) build_markers(s, &s->sol[k]);
   compute_inside(s, s->inside);
   s->have_prev = 0;
+}
+
+void ora_set_ibm_inertia(ora_sim *s, int inertia) {
+  s->ibm_inertia = inertia == ORA_INERTIA_KEMPE ? ORA_INERTIA_KEMPE : ORA_INERTIA_FENG;
+  for (int k = 0; k < s->nsol; k++) s->sol[k].have_Ip = 0;
 }
 
 void ora_set_ibm_kernel(ora_sim *s, int kernel) {
@@ -862,13 +871,69 @@ static void solid_volume(const ora_sim *s, const solid_t *b, double *V, double *
   }
 }
 
+static void node_velocity(const ora_sim *s, long n, double u[3], double F[3]);
+static void current_forces(ora_sim *s);
+
+/* Fraction of the cell around node (x, y, z) inside solid b (Eq. 25):
+ * sum over the cell's corners (x +- 1/2, ...; 8 in 3D, 4 in 2D) of
+ * -phi H(-phi) over the sum of |phi|, with the signed distance function of
+ * Eq. 26 for a sphere (a = b = c = R) or a circle / z-cylinder (the z term
+ * dropped). */
+static double cell_fraction(const ora_sim *s, const solid_t *b, long x, long y, long z) {
+  const int flat = s->d == 2 || b->kind == ORA_CYLINDER_Z;
+  double num = 0, den = 0;
+  for (int c = 0; c < (s->d == 2 ? 4 : 8); c++) {
+    double r[3];
+    rel(s, b, x + ((c & 1) ? 0.5 : -0.5), y + ((c & 2) ? 0.5 : -0.5),
+        z + ((c & 4) ? 0.5 : -0.5), r);
+    if (flat) r[2] = 0;
+    const double phi = sqrt(r[0] * r[0] + r[1] * r[1] + r[2] * r[2]) / b->R - 1;
+    if (phi < 0) num += -phi;
+    den += fabs(phi);
+  }
+  return den > 0 ? num / den : 0;
+}
+
+/* Eq. 24: the fluid momentum and angular momentum inside solid b,
+ * sum over nodes of u alpha and r x u alpha (h = 1), u the velocity at the
+ * current time (with this step's forces) and r the node's separation from
+ * the centre. */
+static void internal_fluid(const ora_sim *s, const solid_t *b, double I[6]) {
+  for (int k = 0; k < 6; k++) I[k] = 0;
+  for (long n = 0; n < s->N; n++) {
+    long x, y, z;
+    coords(s, n, &x, &y, &z);
+    const double al = cell_fraction(s, b, x, y, z);
+    if (al == 0) continue;
+    double u[3], F[3], r[3];
+    node_velocity(s, n, u, F);
+    if (s->d == 2) u[2] = 0;
+    rel(s, b, (double)x, (double)y, (double)z, r);
+    if (s->d == 2 || b->kind == ORA_CYLINDER_Z) r[2] = 0;
+    for (int a = 0; a < 3; a++) I[a] += al * u[a];
+    I[3] += al * (r[1] * u[2] - r[2] * u[1]);
+    I[4] += al * (r[2] * u[0] - r[0] * u[2]);
+    I[5] += al * (r[0] * u[1] - r[1] * u[0]);
+  }
+}
+
+double ora_cell_fraction(ora_sim *s, int id, long x, long y, long z) {
+  return cell_fraction(s, &s->sol[id], x, y, z);
+}
+
+void ora_internal_fluid(ora_sim *s, int id, double I[6]) {
+  current_forces(s);
+  internal_fluid(s, &s->sol[id], I);
+}
+
 /* New velocities of a free solid from this step's hydrodynamic force and
  * torque (dt = 1, rho_f = rho0):
  *  - bounce-back (Eq. 20): rho_p V dv = F + (rho_p - rho_f) V g, I dw = T;
  *  - IBM (Eq. 23): rho_p V dv = rho_f V (v - v_prev) + F + (rho_p - rho_f) V g,
  *    I dw = I (rho_f / rho_p)(w - w_prev) + T.
  * Cylinders turn about z only. */
-static void free_motion(const ora_sim *s, const solid_t *b, double Un[3], double On[3]) {
+static void free_motion(const ora_sim *s, const solid_t *b, const double Inow[6], double Un[3],
+                        double On[3]) {
   double V, Ir2;
   solid_volume(s, b, &V, &Ir2);
   const double m = b->rho_p * RHO0 * V, I = m * Ir2;
@@ -876,7 +941,12 @@ static void free_motion(const ora_sim *s, const solid_t *b, double Un[3], double
   for (int a = 0; a < 3; a++) {
     double dv = b->F[a] + (b->rho_p - 1.0) * RHO0 * V * b->g[a];
     double dw = b->T[a];
-    if (ibm) {
+    if (ibm && s->ibm_inertia == ORA_INERTIA_KEMPE) {
+      /* Eq. 21 with Eq. 24: rho_f times the change of the inside fluid's
+       * momentum (angular momentum) over the last step */
+      dv += RHO0 * (Inow[a] - b->Ip[a]);
+      dw += RHO0 * (Inow[3 + a] - b->Ip[3 + a]);
+    } else if (ibm) {
       dv += RHO0 * V * (b->U[a] - b->Up[a]);
       dw += I / b->rho_p * (b->Om[a] - b->Omp[a]);
     }
@@ -1016,6 +1086,9 @@ static void one_step(ora_sim *s) {
   int Q = s->Q;
   update_geometry(s);
   ibm_forces(s);
+  if (s->scheme == ORA_IBM && s->ibm_inertia == ORA_INERTIA_KEMPE)
+    for (int k = 0; k < s->nsol; k++)
+      if (s->sol[k].free_) internal_fluid(s, &s->sol[k], s->sol[k].In);
   /* collision */
   for (long n = 0; n < N; n++) {
     if (!simulated(s, n)) continue;
@@ -1100,8 +1173,19 @@ static void one_step(ora_sim *s) {
   for (int k = 0; k < s->nsol; k++) {
     solid_t *b = &s->sol[k];
     if (b->free_) {
-      double Un[3], On[3];
-      free_motion(s, b, Un, On);
+      double Un[3], On[3], Inow[6] = {0, 0, 0, 0, 0, 0};
+      if (s->scheme == ORA_IBM && s->ibm_inertia == ORA_INERTIA_KEMPE) {
+        /* Eq. 24 at time n, taken after ibm_forces and before the
+         * streaming replaced f */
+        for (int a = 0; a < 6; a++) Inow[a] = b->In[a];
+        if (!b->have_Ip)
+          for (int a = 0; a < 6; a++) b->Ip[a] = Inow[a];
+      }
+      free_motion(s, b, Inow, Un, On);
+      if (s->scheme == ORA_IBM && s->ibm_inertia == ORA_INERTIA_KEMPE) {
+        for (int a = 0; a < 6; a++) b->Ip[a] = Inow[a];
+        b->have_Ip = 1;
+      }
       for (int a = 0; a < 3; a++) {
         b->c[a] += 0.5 * (b->U[a] + Un[a]);
         b->Up[a] = b->U[a];
@@ -1250,6 +1334,7 @@ void ora_solid_velocity(const ora_sim *s, int id, double U[3], double Om[3]) {
 
 void ora_set_solid_dynamics(ora_sim *s, int id, double rho_ratio, const double g[3]) {
   solid_t *b = &s->sol[id];
+  b->have_Ip = 0;
   b->free_ = rho_ratio > 0;
   b->rho_p = rho_ratio;
   for (int a = 0; a < 3; a++) {

@@ -126,6 +126,16 @@ void ora_set_solid_dynamics(ora_sim *s, int id, double rho_ratio, const double g
 #define ORA_FACE_FREE_SLIP 2
 #define ORA_FACE_CONVECTIVE 3
 int ora_set_domain(ora_sim *s, const int face[6], const double *u_face);
+/* Inertia of the fluid inside a free solid under IBM (Sec. 4.1): the
+ * rigid-body form of Feng & Michaelides (Eq. 23, default) or Kempe et al.'s
+ * volume integrals with level-set cell fractions (Eqs. 24-26). */
+#define ORA_INERTIA_FENG 0
+#define ORA_INERTIA_KEMPE 1
+void ora_set_ibm_inertia(ora_sim *s, int inertia);
+/* Eq. 25 at node (x, y, z) for solid id, and Eq. 24 for solid id at the
+ * current time (momentum, then angular momentum about the centre). */
+double ora_cell_fraction(ora_sim *s, int id, long x, long y, long z);
+void ora_internal_fluid(ora_sim *s, int id, double I[6]);
 void ora_solid_velocity(const ora_sim *s, int id, double U[3], double Om[3]);
 
 /* ---- immersed-boundary primitives on a bare periodic grid (pin tests) ----

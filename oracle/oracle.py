@@ -60,6 +60,9 @@ def lib():
                 "ora_phi": (d, [d]),
                 "ora_phi_kernel": (d, [i, d]),
                 "ora_set_ibm_kernel": (None, [vp, i]),
+                "ora_set_ibm_inertia": (None, [vp, i]),
+                "ora_cell_fraction": (d, [vp, i, C.c_long, C.c_long, C.c_long]),
+                "ora_internal_fluid": (None, [vp, i, dp]),
                 "ora_set_solid_dynamics": (None, [vp, i, d, dp]),
                 "ora_solid_velocity": (None, [vp, i, dp, dp]),
                 "ora_set_domain": (i, [vp, C.POINTER(C.c_int), dp]),
@@ -234,8 +237,9 @@ class OracleSim:
         return sid
 
     def set_scheme(self, scheme, ibm_iters=1, retraction=0.0, marker_density=1.0,
-                   ibm_kernel=PESKIN4):
+                   ibm_kernel=PESKIN4, ibm_inertia=0):
         self.L.ora_set_ibm_kernel(self.h, int(ibm_kernel))
+        self.L.ora_set_ibm_inertia(self.h, int(ibm_inertia))
         self.L.ora_set_scheme(self.h, scheme, ibm_iters, retraction, marker_density)
 
     def init_equilibrium(self, rho=1.0, u=None):
@@ -304,6 +308,14 @@ class OracleSim:
         u = np.zeros((6, 3)) if u_face is None else np.ascontiguousarray(u_face, dtype=np.float64)
         if self.L.ora_set_domain(self.h, fc, _p(u)) != 0:
             raise ValueError(f"domain refused: {list(faces)}")
+
+    def cell_fraction(self, sid, x, y, z=0):
+        return self.L.ora_cell_fraction(self.h, sid, int(x), int(y), int(z))
+
+    def internal_fluid(self, sid=0):
+        I = np.zeros(6)
+        self.L.ora_internal_fluid(self.h, sid, _p(I))
+        return I[:3], I[3:]
 
     def set_solid_dynamics(self, sid, rho_ratio, gravity=None):
         self.L.ora_set_solid_dynamics(self.h, sid, float(rho_ratio), _p(_vec3(gravity)))

@@ -23,6 +23,7 @@ SPHERE, CYLINDER_Z = 0, 1
 NONE, BB, BOUZIDI_LIN, BOUZIDI_QUAD, YU_LIN, YU_QUAD, IBM, ZHAO_YONG = range(8)
 PESKIN4, ROMA3, LINEAR2, COSINE4 = range(4)  # IBM delta-function kernels
 PERIODIC, VELOCITY, FREE_SLIP, CONVECTIVE = range(4)  # domain face types
+FENG, KEMPE = range(2)  # inertia of the fluid inside a free solid under IBM
 SCHEME_NAMES = {NONE: "none", BB: "bounce_back", BOUZIDI_LIN: "bouzidi_linear",
                 BOUZIDI_QUAD: "bouzidi_quadratic", YU_LIN: "yu_linear",
                 YU_QUAD: "yu_quadratic", IBM: "ibm_direct_forcing", ZHAO_YONG: "zhao_yong"}
@@ -58,6 +59,7 @@ class Problem:
     marker_density: float = 1.0
     force_all: bool = False
     ibm_kernel: int = 0  # PESKIN4, ROMA3, LINEAR2, COSINE4
+    ibm_inertia: int = 0  # FENG (Eq. 23) or KEMPE (Eqs. 24-26), free solids under IBM
     # domain faces x-, x+, y-, y+, z-, z+ (PERIODIC, VELOCITY, FREE_SLIP,
     # CONVECTIVE) and the [6][3] velocities of the velocity faces; None: periodic
     faces: Optional[Tuple[int, ...]] = None

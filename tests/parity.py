@@ -11,7 +11,8 @@ def make_oracle(p: W.Problem) -> "O.OracleSim":
                     force_all=p.force_all)
     for b in p.solids:
         s.add_solid(b.kind, b.centre, b.radius, b.velocity, b.omega, b.fluid_inside)
-    s.set_scheme(p.scheme, p.ibm_iters, p.retraction, p.marker_density, p.ibm_kernel)
+    s.set_scheme(p.scheme, p.ibm_iters, p.retraction, p.marker_density, p.ibm_kernel,
+                 p.ibm_inertia)
     if p.faces is not None:
         s.set_domain(p.faces, p.u_face)
     return s

@@ -273,3 +273,74 @@ def test_free_solid_in_fluid_at_rest_stays_at_rest(oracle):
     s.step(30)
     U, Om = s.solid_velocity(sid)
     assert np.abs(U).max() < 1e-15 and np.abs(Om).max() < 1e-15
+
+
+@pytest.mark.parametrize("d,radii", [(2, (4.0, 8.0, 16.0)), (3, (3.0, 6.0))])
+def test_kempe_cell_fractions_sum_to_the_volume(oracle, d, radii):
+    """Eqs. 25-26: the level-set cell fractions are 1 inside, 0 outside, and
+    sum to the circle's area (sphere's volume) with an error that falls at
+    second order under refinement."""
+    errs = []
+    for R in radii:
+        n = int(2 * R + 8)
+        nz = n if d == 3 else 1
+        s = oracle.OracleSim(d - 2, n, n, nz, 0.8, W.BGK)
+        c = (n / 2 + 0.31, n / 2 - 0.17, n / 2 + 0.07 if d == 3 else 0)
+        sid = s.add_solid(W.SPHERE, c, R)
+        s.set_scheme(W.IBM)
+        al = np.array([[[s.cell_fraction(sid, x, y, z) for x in range(n)] for y in range(n)]
+                       for z in range(nz)])
+        z, y, x = np.meshgrid(np.arange(nz), np.arange(n), np.arange(n), indexing="ij")
+        r = np.sqrt((x - c[0]) ** 2 + (y - c[1]) ** 2 + (z - c[2]) ** 2)
+        assert np.all(al[r < R - 1] == 1) and np.all(al[r > R + 1] == 0)
+        assert al.min() >= 0 and al.max() <= 1
+        vol = np.pi * R * R if d == 2 else 4 / 3 * np.pi * R ** 3
+        errs.append(abs(al.sum() / vol - 1))
+    assert errs[-1] < 1e-2
+    assert all(b < a / 3 for a, b in zip(errs, errs[1:]))
+
+
+def test_kempe_angular_momentum_of_rigid_rotation(oracle):
+    """Eq. 24 on a rigidly rotating fluid u = Omega x r: the angular momentum
+    inside a circle of radius R is Omega pi R^4 / 2 (its polar moment), the
+    momentum about zero."""
+    R, n, Om = 8.0, 28, 1e-3
+    c = (14.3, 13.8, 0)
+    s = oracle.OracleSim(W.D2Q9, n, n, 1, 0.8, W.BGK)
+    sid = s.add_solid(W.SPHERE, c, R, (0, 0, 0), (0, 0, Om))
+    s.set_scheme(W.IBM)
+    e, w = oracle.lattice(W.D2Q9)
+    y, x = np.mgrid[0:n, 0:n]
+    ux, uy = -Om * (y - c[1]), Om * (x - c[0])
+    f = np.zeros((9, 1, n, n))
+    for i in range(9):
+        eu = e[i, 0] * ux + e[i, 1] * uy
+        f[i, 0] = w[i] * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (ux ** 2 + uy ** 2))
+    s.set_f(f)
+    I, L = s.internal_fluid(sid)
+    assert abs(L[2] / (Om * np.pi * R ** 4 / 2) - 1) < 1e-2
+    assert np.abs(I).max() < 1e-3 * Om * R * np.pi * R * R
+
+
+def test_kempe_and_feng_settle_alike_near_neutral_density(oracle):
+    """At rho_p / rho_f = 1.03 (the density ratio of the settling cylinder of
+    Sec. 4.1) both treatments of the inside fluid stay stable, reach the
+    periodic-array slip velocity within 15% and agree within 1%."""
+    L, R, tau, rho_p, g0 = 32, 4.0, 1.0, 1.03, 1e-4
+    nu = (tau - 0.5) / 3
+    c = np.pi * R * R / (L * L)
+    weight = (rho_p - 1) * np.pi * R * R * g0
+    K = -0.5 * np.log(c) - 0.738 + c - 0.887 * c ** 2 + 2.039 * c ** 3
+    slips = []
+    for inertia in (W.FENG, W.KEMPE):
+        s = oracle.OracleSim(0, L, L, 1, tau, 0, g=(0, weight / (L * L - np.pi * R * R), 0))
+        sid = s.add_solid(1, (16.3, 15.7, 0), R)
+        s.set_scheme(W.IBM, ibm_inertia=inertia)
+        s.set_solid_dynamics(sid, rho_p, (0, -g0, 0))
+        s.step(12000)
+        U, _ = s.solid_velocity(sid)
+        u = s.velocity()[:, 0]
+        fluid = ~s.solid_mask()[0]
+        slips.append(u[1][fluid].mean() - U[1])
+        assert abs(slips[-1] / (weight * K / (4 * np.pi * nu)) - 1) < 0.15
+    assert abs(slips[1] / slips[0] - 1) < 1e-2

@@ -131,18 +131,27 @@ enum {
   LBM_DELTA_COSINE4 = 3  /* 4-point cosine kernel (Appendix B) */
 };
 
+/* inertia of the fluid inside a free solid under IBM (Sec. 4.1) */
+enum {
+  LBM_INERTIA_FENG = 0, /* rigid-body inside fluid, Feng & Michaelides, Eq. 23 (default) */
+  LBM_INERTIA_KEMPE = 1 /* Kempe et al.: volume integrals over level-set cell fractions,
+                           Eqs. 24-26 */
+};
+
 /* Scheme.  For LBM_IBM_DIRECT: ibm_iters >= 1 forcing iterations (Eq. 9
  * applied to the spread force), ibm_retraction = R_d (markers at R - R_d, or
  * R + R_d for an enclosing wall), ibm_marker_density = markers per unit
  * surface area (per unit length in 2D), 0 -> 1, ibm_kernel = LBM_DELTA_*
- * (zero-initialised descriptors get Peskin's kernel).  An unknown kernel is
- * LBM_ERR_ARG. */
+ * (zero-initialised descriptors get Peskin's kernel), ibm_inertia =
+ * LBM_INERTIA_* for free solids (lbm_set_solid_dynamics).  An unknown kernel
+ * or inertia treatment is LBM_ERR_ARG. */
 typedef struct {
   int scheme;
   int ibm_iters;
   double ibm_retraction;
   double ibm_marker_density;
   int ibm_kernel;
+  int ibm_inertia;
 } lbm_scheme_desc;
 
 typedef struct {
@@ -194,10 +203,12 @@ lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme);
  * face is not, a z face on a 2D lattice, a second outflow face or a
  * non-periodic axis shorter than 3 nodes; LBM_ERR_STATE for an outflow face
  * set after stepping (set it first, or right after lbm_init_equilibrium /
- * lbm_set_distributions).  Solids must keep R + 5 nodes clear of every
- * non-periodic face, and be neither fluid-inside nor z-cylinders crossing
- * non-periodic z faces: else the next step or query returns
- * LBM_ERR_UNSUPPORTED.  Checkpoints of a lattice with an outflow face are
+ * lbm_set_distributions).  A solid's surface must keep 1.5 spacings clear
+ * of the outermost nodes at a velocity or stress-free face (interpolation
+ * nodes of the bounce-back rules beyond the face count as missing) and
+ * R + 5 nodes at an outflow face, and solids may be neither fluid-inside
+ * nor z-cylinders crossing non-periodic z faces: else the next step or
+ * query returns LBM_ERR_UNSUPPORTED.  Checkpoints of a lattice with an outflow face are
  * LBM_ERR_UNSUPPORTED.  NULL restores the periodic box. */
 enum {
   LBM_FACE_PERIODIC = 0,
@@ -251,8 +262,11 @@ lbm_status lbm_get_force_torque(lbm_ctx *ctx, int solid_id, double F[3],
  * makes the solid free, <= 0 returns it to prescribed motion; gravity acts
  * on it (the fluid feels only the lattice body force).  Every step then sets
  * its velocities from its hydrodynamic force and torque: Eq. 20 under
- * bounce-back, the Feng & Michaelides discretisation of Eq. 23 under IBM
- * (dt = 1, rho_f = 1); its centre moves by the mean of the old and new
+ * bounce-back, under IBM the Feng & Michaelides discretisation of Eq. 23
+ * or, with ibm_inertia = LBM_INERTIA_KEMPE, rho_f times the change over the
+ * last step of the inside fluid's momentum and angular momentum summed with
+ * the level-set cell fractions of Eqs. 24-26 (dt = 1, rho_f = 1); its
+ * centre moves by the mean of the old and new
  * velocity.  Spheres have V = 4/3 pi R^3 and I = 2/5 m R^2; cylinders
  * V = pi R^2 (times nz in 3D) and I = 1/2 m R^2 about z, turning about z
  * only.  LBM_ERR_STATE without a bounce-back or IBM scheme;

@@ -973,6 +973,18 @@ static int crossed(const ora_sim *s, long x, long y, long z, int i) {
   return m;
 }
 
+/* whether x - k e_i lies beyond a non-periodic face (k < 0: downstream) */
+static int crossed_at(const ora_sim *s, long x, long y, long z, int i, int k) {
+  if (!s->open) return 0;
+  const long p[3] = {x - k * s->e[i][0], y - k * s->e[i][1], z - k * s->e[i][2]};
+  const long len[3] = {s->nx, s->ny, s->nz};
+  for (int a = 0; a < s->d; a++) {
+    if (p[a] < 0 && s->face[2 * a] != ORA_FACE_PERIODIC) return 1;
+    if (p[a] >= len[a] && s->face[2 * a + 1] != ORA_FACE_PERIODIC) return 1;
+  }
+  return 0;
+}
+
 static int crosses_type(const ora_sim *s, int m, int type) {
   for (int k = 0; k < 6; k++)
     if (((m >> k) & 1) && s->face[k] == type) return k;
@@ -1129,7 +1141,9 @@ static void one_step(ora_sim *s) {
       long nff = node(s, x + s->e[i][0], y + s->e[i][1], z + s->e[i][2]);
       long nfff =
           node(s, x + 2 * s->e[i][0], y + 2 * s->e[i][1], z + 2 * s->e[i][2]);
-      int hff = simulated(s, nff), hfff = hff && simulated(s, nfff);
+      /* a stencil node beyond a non-periodic face does not exist */
+      int hff = !crossed_at(s, x, y, z, i, -1) && simulated(s, nff);
+      int hfff = hff && !crossed_at(s, x, y, z, i, -2) && simulated(s, nfff);
       double q = link_q(s, b, n, i), c[6];
       int used = s->scheme == ORA_ZHAO_YONG ? ORA_ZHAO_YONG
                                             : ora_ibb_coeffs(s->scheme, q, hff, hfff, c);

@@ -53,6 +53,10 @@ struct SolidHost {
   // free motion: density ratio rho_p / rho_f (0: prescribed), gravity, and
   // the velocities of the previous step (Eq. 23)
   double rho_p = 0, g[3] = {0, 0, 0}, Up[3] = {0, 0, 0}, Omp[3] = {0, 0, 0};
+  // Kempe's treatment under IBM (Eq. 24): the inside fluid's momentum and
+  // angular momentum at the previous step, once one has been taken
+  bool have_Ip = false;
+  double Ip[6] = {0, 0, 0, 0, 0, 0};
 };
 
 const double PI = 3.14159265358979323846;
@@ -119,6 +123,7 @@ struct lbm_ctx {
   // Eq. 16: pre-collision populations kept at the boundary nodes ([Q][fs],
   // compute type; allocated when the scheme is first selected)
   void *zy_pre = nullptr;
+  double *kempe = nullptr;  // [kMaxSolids][6] Eq. 24 sums of the current step
   // domain faces: types and wall velocities, the nodes next to a
   // non-periodic face, and the outflow face's kept populations
   lbm_domain_desc dom{};
@@ -392,6 +397,39 @@ bool any_moving(const lbm_ctx *ctx) {
   return false;
 }
 
+// Eq. 24 for every free solid from the current state f*(t) and the forces
+// of its collision, into ctx->kempe (FP64, zeroed first).
+lbm_status kempe_integrals(lbm_ctx *ctx) {
+  if (!ctx->kempe) TRY(dalloc(ctx, (void **)&ctx->kempe, sizeof(double) * kMaxSolids * 6));
+  CK(cudaMemsetAsync(ctx->kempe, 0, sizeof(double) * kMaxSolids * 6, ctx->st));
+  const int len[3] = {ctx->d.nx, ctx->d.ny, ctx->D == 2 ? 1 : ctx->d.nz};
+  for (size_t k = 0; k < ctx->solids.size(); k++) {
+    const SolidHost &h = ctx->solids[k];
+    if (!(h.rho_p > 0)) continue;
+    KArgs a = base_args(ctx);
+    a.src = ctx->f[ctx->cur];
+    a.solids = solids_dev(ctx, false);
+    a.kempe_out = ctx->kempe + 6 * k;
+    a.kempe_solid = (int)k;
+    for (int c = 0; c < 3; c++) {
+      // every node with a cell corner inside lies within R + 1 of the centre
+      const bool whole = c >= ctx->D || (c == 2 && h.d.kind == LBM_CYLINDER_Z);
+      const int lo = (int)floor(h.c[c] - h.d.radius - 1.0);
+      const int hi = (int)ceil(h.c[c] + h.d.radius + 1.0);
+      const int ext = hi - lo + 1;
+      if (whole || ext >= len[c]) {
+        a.kbox[c] = 0;
+        a.kbox[3 + c] = len[c];
+      } else {
+        a.kbox[c] = lo;
+        a.kbox[3 + c] = ext;
+      }
+    }
+    sweep(ctx, OP_KEMPE, a);
+  }
+  return LBM_OK;
+}
+
 // Free solids (Sec. 3.2): new velocities from the force record `slot` (this
 // step's momentum exchange under bounce-back, the current IBM force under
 // IBM) and gravity, dt = 1, rho_f = rho0 = 1:
@@ -402,11 +440,14 @@ bool any_moving(const lbm_ctx *ctx) {
 // those of a sphere (4/3 pi R^3, 2/5 m R^2) or a cylinder (pi R^2 times its
 // length: 1 in 2D, nz in 3D; 1/2 m R^2 about z).
 lbm_status advance_free(lbm_ctx *ctx, int slot) {
-  double rec[kMaxSolids * 6];
+  const bool ibm = ctx->scheme.scheme == LBM_IBM_DIRECT;
+  const bool kempe = ibm && ctx->scheme.ibm_inertia == LBM_INERTIA_KEMPE;
+  double rec[kMaxSolids * 6], In[kMaxSolids * 6];
+  if (kempe) TRY(kempe_integrals(ctx));
   CK(cudaMemcpyAsync(rec, ctx->hist + (size_t)slot * kMaxSolids * 6, sizeof(rec),
                      cudaMemcpyDeviceToHost, ctx->st));
+  if (kempe) CK(cudaMemcpyAsync(In, ctx->kempe, sizeof(In), cudaMemcpyDeviceToHost, ctx->st));
   CK(cudaStreamSynchronize(ctx->st));
-  const bool ibm = ctx->scheme.scheme == LBM_IBM_DIRECT;
   for (size_t k = 0; k < ctx->solids.size(); k++) {
     SolidHost &h = ctx->solids[k];
     if (!(h.rho_p > 0)) continue;
@@ -419,7 +460,16 @@ lbm_status advance_free(lbm_ctx *ctx, int slot) {
     for (int a = 0; a < 3; a++) {
       double dv = rec[6 * k + a] + (h.rho_p - 1.0) * V * h.g[a];
       double dw = rec[6 * k + 3 + a];
-      if (ibm) {
+      if (kempe) {
+        // Eq. 21 with Eq. 24: the change of the inside fluid's momentum
+        // (angular momentum) over the last step
+        if (!h.have_Ip) {
+          h.Ip[a] = In[6 * k + a];
+          h.Ip[3 + a] = In[6 * k + 3 + a];
+        }
+        dv += In[6 * k + a] - h.Ip[a];
+        dw += In[6 * k + 3 + a] - h.Ip[3 + a];
+      } else if (ibm) {
         dv += V * (h.d.velocity[a] - h.Up[a]);
         dw += I / h.rho_p * (h.d.omega[a] - h.Omp[a]);
       }
@@ -428,6 +478,10 @@ lbm_status advance_free(lbm_ctx *ctx, int slot) {
     }
     if (ctx->D == 2) Un[2] = 0;
     if (cyl) On[0] = On[1] = 0;
+    if (kempe) {
+      for (int c = 0; c < 6; c++) h.Ip[c] = In[6 * k + c];
+      h.have_Ip = true;
+    }
     for (int a = 0; a < 3; a++) {
       h.c[a] += 0.5 * (h.d.velocity[a] + Un[a]);
       h.Up[a] = h.d.velocity[a];
@@ -596,10 +650,14 @@ GeomArgs geom_args(lbm_ctx *ctx) {
   return g;
 }
 
-// Solids keep R + 5 nodes clear of every non-periodic face: the
-// interpolation stencils of the bounce-back rules (x_f + 2 e_i), the IBM
-// band and delta stencils and the refilled nodes then never meet the face
-// nodes, which run in their own kernel.
+// Solids keep clear of the non-periodic faces:
+//  - of a velocity or stress-free face by 1.5 spacings between the surface
+//    and the outermost nodes: no node next to the face then has a cut link
+//    (links are at most sqrt(2) long), and every IBM delta stencil stays
+//    inside the domain.  IBM band nodes next to the face run in the face
+//    kernel; bounce-back stencil nodes beyond the face count as missing;
+//  - of an outflow face by R + 5 nodes, so that neither a face node nor the
+//    inner neighbour its update reads is a boundary or band node.
 lbm_status check_clearance(lbm_ctx *ctx) {
   const int len[3] = {ctx->d.nx, ctx->d.ny, ctx->D == 2 ? 1 : ctx->d.nz};
   for (auto &h : ctx->solids)
@@ -609,9 +667,14 @@ lbm_status check_clearance(lbm_ctx *ctx) {
         return fail(ctx, LBM_ERR_UNSUPPORTED, "a fluid-inside solid fills the domain up to its non-periodic faces");
       if (a == 2 && h.d.kind == LBM_CYLINDER_Z)
         return fail(ctx, LBM_ERR_UNSUPPORTED, "a z-cylinder meets the non-periodic z faces");
-      const double m = h.d.radius + 5.0;
-      if (h.c[a] - m < 0 || h.c[a] + m > len[a] - 1)
-        return fail(ctx, LBM_ERR_UNSUPPORTED, "solid within R + 5 nodes of a non-periodic face");
+      const bool conv_lo = ctx->dom.type[2 * a] == LBM_FACE_CONVECTIVE;
+      const bool conv_hi = ctx->dom.type[2 * a + 1] == LBM_FACE_CONVECTIVE;
+      const double R = h.d.radius;
+      const double mlo = conv_lo ? R + 5.0 : R + 1.5, mhi = conv_hi ? R + 5.0 : R + 1.5;
+      if (h.c[a] - mlo < 0 || h.c[a] + mhi > len[a] - 1)
+        return fail(ctx, LBM_ERR_UNSUPPORTED,
+                    "solid too close to a non-periodic face (1.5 nodes from a wall or "
+                    "stress-free face, R + 5 from an outflow face)");
     }
   return LBM_OK;
 }
@@ -1312,6 +1375,8 @@ lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme) {
     return fail(ctx, LBM_ERR_ARG, "negative IBM parameter");
   if (scheme->ibm_kernel < LBM_DELTA_PESKIN4 || scheme->ibm_kernel > LBM_DELTA_COSINE4)
     return fail(ctx, LBM_ERR_ARG, "unknown delta-function kernel");
+  if (scheme->ibm_inertia != LBM_INERTIA_FENG && scheme->ibm_inertia != LBM_INERTIA_KEMPE)
+    return fail(ctx, LBM_ERR_ARG, "unknown inside-fluid treatment");
   if (scheme->scheme == LBM_ZHAO_YONG && !ctx->need_collide && !ctx->prev_local)
     return fail(ctx, LBM_ERR_STATE,
                 "select Eq. 16 before stepping, or after lbm_init_equilibrium / "
@@ -1322,6 +1387,7 @@ lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme) {
   }
   ctx->scheme = *scheme;
   ctx->geom_dirty = true;
+  for (auto &h : ctx->solids) h.have_Ip = false;
   // the boundary nodes' pre-collision values are seeded by the next
   // initial collision, from the pre-collision state held locally
   if (scheme->scheme == LBM_ZHAO_YONG) ctx->need_collide = true;
@@ -1541,6 +1607,7 @@ lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int id, double density_ratio,
     return fail(ctx, LBM_ERR_UNSUPPORTED, "Eq. 16 does not take translating solids");
   SolidHost &h = ctx->solids[id];
   h.rho_p = density_ratio > 0 ? density_ratio : 0;
+  h.have_Ip = false;
   for (int a = 0; a < 3; a++) {
     h.g[a] = gravity ? gravity[a] : 0;
     h.Up[a] = h.d.velocity[a];
@@ -1633,7 +1700,7 @@ lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size) {
   SaveHeader h;
   memset(&h, 0, sizeof(h));
   memcpy(h.magic, "LBMGB300", 8);
-  h.version = 3;  // 2: the scheme carries the delta-function kernel; 3: solids their free motion
+  h.version = 4;  // 2: delta-function kernel; 3: free motion; 4: inside-fluid treatment
   h.lattice = ctx->d.lattice;
   h.nx = ctx->d.nx;
   h.ny = ctx->d.ny;
@@ -1666,7 +1733,7 @@ lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size) {
     return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints do not carry the outflow face's state");
   SaveHeader h;
   memcpy(&h, host_buf, sizeof(h));
-  if (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 3) return fail(ctx, LBM_ERR_ARG, "not a checkpoint of this version");
+  if (memcmp(h.magic, "LBMGB300", 8) != 0 || h.version != 4) return fail(ctx, LBM_ERR_ARG, "not a checkpoint of this version");
   if (h.lattice != ctx->d.lattice || h.nx != ctx->d.nx || h.ny != ctx->d.ny || h.nz != ctx->d.nz ||
       h.precision != ctx->d.precision || h.nsolids < 0 || h.nsolids > kMaxSolids ||
       h.fs != ctx->fs)

@@ -136,7 +136,8 @@ __global__ void __launch_bounds__(128) k_list(const KArgs a) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   int cnt = a.counts[0];
   if (cnt > a.list_cap) cnt = a.list_cap;
-  const bool active = t < cnt;
+  // IBM band nodes next to a domain face run in the face kernel
+  const bool active = t < cnt && !(a.flags[a.list_node[t]] & FL_FACE);
   const T isc = kisc<T>(a);
   const S *__restrict__ src = (const S *)a.src;
   // momentum exchange (Eq. 17) of this thread for solid `sa` (the solid of
@@ -309,7 +310,7 @@ __global__ void __launch_bounds__(256) k_list_warp(const KArgs a) {
   const int t = blockIdx.x * (blockDim.x >> 5) + warp;  // list entry of this warp
   int cnt = a.counts[0];
   if (cnt > a.list_cap) cnt = a.list_cap;
-  const bool active = t < cnt;
+  const bool active = t < cnt && !(a.flags[a.list_node[t]] & FL_FACE);
   const bool dir = lane < Q;
   const T isc = kisc<T>(a);
   const S *__restrict__ src = (const S *)a.src;
@@ -561,6 +562,10 @@ __global__ void __launch_bounds__(128) k_refill(const KArgs a) {
 // IBM: unforced velocity u~ = (sum f e + g/2)/rho0 at band nodes (the
 // external half force only, no IBM half force) and zero the IBM force there.
 template <int LAT, typename S, typename T>
+__device__ __forceinline__ T face_pull(const KArgs &a, const S *__restrict__ src, int x, int y,
+                                       int z, int i, T isc);
+
+template <int LAT, typename S, typename T>
 __global__ void __launch_bounds__(64) k_band_vel(const KArgs a) {
   using L = Lat<LAT>;
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
@@ -579,6 +584,8 @@ __global__ void __launch_bounds__(64) k_band_vel(const KArgs a) {
   const T isc = kisc<T>(a);
   if (a.local_gather)
     gather_local<LAT, S, T>((const S *)a.src, a.fs, n, isc, f);
+  else if (fl & FL_FACE)  // next to a velocity or stress-free domain face
+    for (int i = 0; i < L::Q; i++) f[i] = face_pull<LAT, S, T>(a, (const S *)a.src, x, y, z, i, isc);
   else
     gather_pull<LAT, S, T>((const S *)a.src, a.fs, x, y, z, a.nx, a.ny, a.nz, isc, f);
   T j[3] = {0, 0, 0};
@@ -816,6 +823,72 @@ __global__ void __launch_bounds__(128) k_face(const KArgs a) {
   }
 }
 
+// ---------------------------------------------------------------- Eq. 24
+// The fluid momentum and angular momentum inside solid a.kempe_solid at the
+// time of the state in src (post-collision f*, so u = sum e f* - F/2 with
+// the force of that collision), weighted by the fraction alpha of the cell
+// around each node inside the solid (Eq. 25: sum over the cell's corners at
+// +-1/2 of -phi H(-phi) over the sum of |phi|, phi the signed distance
+// function of Eq. 26 for a sphere, or a circle / z-cylinder).  A thread per
+// node of the box around the solid; FP64 sums.
+__device__ __forceinline__ double kimage(double d, int L) {
+  return d - L * rint(d * (1.0 / L));
+}
+
+template <int LAT, typename S, typename T>
+__global__ void __launch_bounds__(256) k_kempe(const KArgs a) {
+  using L = Lat<LAT>;
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const int bx = a.kbox[3], by = a.kbox[4], bz = a.kbox[5];
+  double acc[6] = {0, 0, 0, 0, 0, 0};
+  if (t < (long long)bx * by * bz) {
+    const int x = wrap(a.kbox[0] + (int)(t % bx), a.nx);
+    const int y = wrap(a.kbox[1] + (int)((t / bx) % by), a.ny);
+    const int z = wrap(a.kbox[2] + (int)(t / ((long long)bx * by)), a.nz);
+    const SolidDev &b = a.solids.s[a.kempe_solid];
+    const bool flat = L::D == 2 || b.kind == LBM_CYLINDER_Z;
+    double num = 0, den = 0;
+    for (int c = 0; c < (L::D == 2 ? 4 : 8); c++) {
+      const double r0 = kimage(x + ((c & 1) ? 0.5 : -0.5) - b.c[0], a.nx);
+      const double r1 = kimage(y + ((c & 2) ? 0.5 : -0.5) - b.c[1], a.ny);
+      const double r2 = flat ? 0.0 : kimage(z + ((c & 4) ? 0.5 : -0.5) - b.c[2], a.nz);
+      const double phi = sqrt(r0 * r0 + r1 * r1 + r2 * r2) / b.R - 1.0;
+      if (phi < 0) num -= phi;
+      den += fabs(phi);
+    }
+    const double al = den > 0 ? num / den : 0.0;
+    if (al > 0) {
+      const long long n = x + (long long)a.nx * (y + (long long)a.ny * z);
+      const T isc = kisc<T>(a);
+      T Fx, Fy, Fz;
+      node_force<T, T>(a, n, a.flags[n], Fx, Fy, Fz);
+      T j[3] = {(T)0, (T)0, (T)0};
+#pragma unroll
+      for (int i = 1; i < L::Q; i++) {
+        const T v = Store<S>::ld((const S *)a.src + (long long)i * a.fs + n, isc);
+        j[0] += (T)L::ex(i) * v;
+        j[1] += (T)L::ey(i) * v;
+        j[2] += (T)L::ez(i) * v;
+      }
+      const double u[3] = {(double)(j[0] - (T)0.5 * Fx), (double)(j[1] - (T)0.5 * Fy),
+                           L::D == 2 ? 0.0 : (double)(j[2] - (T)0.5 * Fz)};
+      const double r[3] = {kimage(x - b.c[0], a.nx), kimage(y - b.c[1], a.ny),
+                           flat ? 0.0 : kimage(z - b.c[2], a.nz)};
+      acc[0] = al * u[0];
+      acc[1] = al * u[1];
+      acc[2] = al * u[2];
+      acc[3] = al * (r[1] * u[2] - r[2] * u[1]);
+      acc[4] = al * (r[2] * u[0] - r[0] * u[2]);
+      acc[5] = al * (r[0] * u[1] - r[1] * u[0]);
+    }
+  }
+  const int lane = threadIdx.x & 31;
+  for (int c = 0; c < 6; c++) {
+    const double v = warp_sum(acc[c]);
+    if (lane == 0 && v != 0.0) atomicAdd(a.kempe_out + c, v);
+  }
+}
+
 // ---------------------------------------------------------------- launch
 inline int div_up(long long a, int b) { return (int)((a + b - 1) / b); }
 
@@ -912,6 +985,11 @@ void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
   case OP_FACE_QUERY:
     if (a.nface > 0) k_face<LAT, CM, S, double, T, 1><<<div_up(a.nface, 128), 128, 0, st>>>(a);
     break;
+  case OP_KEMPE: {
+    const long long vol = (long long)a.kbox[3] * a.kbox[4] * a.kbox[5];
+    if (vol > 0) k_kempe<LAT, S, T><<<div_up(vol, 256), 256, 0, st>>>(a);
+    break;
+  }
   case OP_FACE_SEED:
     if (a.nface > 0 && a.outlet) k_face<LAT, CM, S, T, T, 2><<<div_up(a.nface, 128), 128, 0, st>>>(a);
     break;

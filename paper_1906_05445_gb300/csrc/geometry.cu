@@ -65,6 +65,12 @@ __device__ __forceinline__ long long box_node(const GeomArgs &g, long long t,
   return x + (long long)g.nx * (y + (long long)g.ny * z);
 }
 
+// whether (x, y, z) lies inside the domain across its non-periodic faces
+__device__ __forceinline__ bool in_domain(const GeomArgs &g, int x, int y, int z) {
+  return !((g.face[0] && x < 0) || (g.face[1] && x >= g.nx) || (g.face[2] && y < 0) ||
+           (g.face[3] && y >= g.ny) || (g.face[4] && z < 0) || (g.face[5] && z >= g.nz));
+}
+
 // byte-wise atomic OR on the flag array (4-byte aligned, padded)
 __device__ __forceinline__ uint8_t flag_or(uint8_t *flags, long long n, uint8_t bits) {
   unsigned int *w = (unsigned int *)(flags + (n & ~3LL));
@@ -294,8 +300,9 @@ __global__ void __launch_bounds__(128) k_geom_links(const GeomArgs g, const uint
                         (long long)g.nx * (wrap(y + ey, g.ny) + (long long)g.ny * wrap(z + ez, g.nz));
   const long long nfff = wrap(x + 2 * ex, g.nx) +
                          (long long)g.nx * (wrap(y + 2 * ey, g.ny) + (long long)g.ny * wrap(z + 2 * ez, g.nz));
-  const bool ff = sid_new[nff] == 0;
-  const bool fff = ff && sid_new[nfff] == 0;
+  // a stencil node beyond a non-periodic domain face does not exist
+  const bool ff = sid_new[nff] == 0 && in_domain(g, x + ex, y + ey, z + ez);
+  const bool fff = ff && sid_new[nfff] == 0 && in_domain(g, x + 2 * ex, y + 2 * ey, z + 2 * ez);
   T c[6];
   ibb_rule_t<T>(g.scheme, (T)q, ff, fff, c);
   // wall point relative to the centre and the wall velocity there

@@ -97,6 +97,11 @@ struct KArgs {
   void *outlet;
   int out_face;
   long long out_area;
+  // Eq. 24 for one solid over the box (x0, y0, z0, bx, by, bz) around it:
+  // sums of alpha u and alpha r x u added into kempe_out[0..5] (FP64)
+  double *kempe_out;
+  int kempe_solid;
+  int kbox[6];
 };
 
 // kernel families timed by lbm_set_timing
@@ -117,7 +122,8 @@ enum SweepOp {
   OP_FILL_EQ,      // fill dst with equilibrium deviations (g[] = u, omega = rho)
   OP_FACE_SWEEP,   // nodes next to a non-periodic domain face: pull with the face rules + collide
   OP_FACE_QUERY,   // the same nodes, fields
-  OP_FACE_SEED     // outflow face: keep the populations of a state held locally
+  OP_FACE_SEED,    // outflow face: keep the populations of a state held locally
+  OP_KEMPE         // Eq. 24: the fluid momentum inside a solid, from f*(t) and the forces
 };
 
 // Launch one operation for the given lattice/collision/precision.  grid

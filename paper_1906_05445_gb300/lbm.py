@@ -32,6 +32,7 @@ SPHERE, CYLINDER_Z = 0, 1
 TK_BULK, TK_LIST, TK_IBM, TK_GEOM = range(4)
 DELTA_PESKIN4, DELTA_ROMA3, DELTA_LINEAR2, DELTA_COSINE4 = range(4)
 FACE_PERIODIC, FACE_VELOCITY, FACE_FREE_SLIP, FACE_CONVECTIVE = range(4)
+INERTIA_FENG, INERTIA_KEMPE = range(2)
 # lbm_set_timing masks: every kind, or bit (kind + 1) per kind
 TIME_ALL = 1
 TIME_BULK, TIME_LIST, TIME_IBM, TIME_GEOM = (2 << k for k in range(4))
@@ -53,7 +54,7 @@ class lbm_solid_desc(C.Structure):
 class lbm_scheme_desc(C.Structure):
     _fields_ = [("scheme", C.c_int), ("ibm_iters", C.c_int),
                 ("ibm_retraction", C.c_double), ("ibm_marker_density", C.c_double),
-                ("ibm_kernel", C.c_int)]
+                ("ibm_kernel", C.c_int), ("ibm_inertia", C.c_int)]
 
 
 class lbm_domain_desc(C.Structure):
@@ -189,7 +190,8 @@ class Lattice:
                   p.force_all, stream=stream)
         for s in p.solids:
             lat.add_solid(s.kind, s.centre, s.radius, s.velocity, s.omega, s.fluid_inside)
-        lat.set_scheme(p.scheme, p.ibm_iters, p.retraction, p.marker_density, p.ibm_kernel)
+        lat.set_scheme(p.scheme, p.ibm_iters, p.retraction, p.marker_density, p.ibm_kernel,
+                       p.ibm_inertia)
         if p.faces is not None:
             lat.set_domain(p.faces, p.u_face)
         return lat
@@ -225,8 +227,9 @@ class Lattice:
         self._check(lbm_set_solid_motion(self.h, sid, *[None if a is None else _dp(a) for a in args]))
 
     def set_scheme(self, scheme, ibm_iters=1, retraction=0.0, marker_density=1.0,
-                   ibm_kernel=DELTA_PESKIN4):
-        s = lbm_scheme_desc(scheme, ibm_iters, retraction, marker_density, ibm_kernel)
+                   ibm_kernel=DELTA_PESKIN4, ibm_inertia=INERTIA_FENG):
+        s = lbm_scheme_desc(scheme, ibm_iters, retraction, marker_density, ibm_kernel,
+                            ibm_inertia)
         self._check(lbm_set_scheme(self.h, C.byref(s)))
 
     def init_equilibrium(self, rho=1.0, u=None):

@@ -153,3 +153,44 @@ def test_batch_of_open_boxes_matches_single():
         # FP64 atomics sum the links in another order
         assert np.abs(Fa - Fb).max() < 1e-12 * np.abs(Fa).max()
     b.close()
+
+
+@pytest.mark.parametrize("scheme,inertia", [(W.BOUZIDI_QUAD, W.FENG), (W.YU_QUAD, W.FENG),
+                                            (W.IBM, W.FENG), (W.IBM, W.KEMPE)])
+def test_free_cylinder_next_to_a_wall_fp64(scheme, inertia):
+    """A free cylinder 1.6 spacings from a resting wall (the start of the
+    settling case of Sec. 4.1): the bounce-back rules lose their stencil
+    nodes beyond the wall and fall back, IBM band nodes next to the wall run
+    in the face kernel; fields, forces and motion follow the oracle."""
+    uf = np.zeros((6, 3))
+    p = W.Problem("near_wall", W.D2Q9, 40, 64, 1, 0.6, W.MRT, W.FP64, (0, 0, 0),
+                  [W.Solid(W.SPHERE, (32.4, 40.3, 0), 5.0)], scheme, 40,
+                  faces=(V, V, V, V, P, P), u_face=tuple(map(tuple, uf)), ibm_inertia=inertia)
+    g, o = make_gpu(p), make_oracle(p)
+    f0 = random_populations(p, seed=17, amplitude=0.01)
+    for s in (g, o):
+        s.set_solid_dynamics(0, 1.03, (0, -2e-4, 0))
+        s.set_f(f0)
+    for k in (1, 19, 20):
+        g.step(k)
+        o.step(k)
+        compare(g, o, FP64_TOL, tol_F=1e-10, what=("u", "rho"))
+        assert np.allclose(g.solid_centre(0), o.solid_centre(0), rtol=0, atol=1e-11)
+        (Ug, Og), (Uo, Oo) = g.solid_velocity(0), o.solid_velocity(0)
+        assert np.allclose(Ug, Uo, rtol=0, atol=1e-13 + 1e-10 * np.abs(Uo).max())
+        assert np.allclose(Og, Oo, rtol=0, atol=1e-13 + 1e-10 * np.abs(Oo).max())
+    g.close()
+
+
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])
+def test_sphere_next_to_stress_free_faces_fp64(scheme):
+    """A sphere 1.7 spacings from a stress-free face and from a moving wall in
+    3D, driven by a body force."""
+    uf = np.zeros((6, 3))
+    uf[2] = (0.02, 0, 0)
+    p = W.Problem("near_faces", W.D3Q19, 24, 20, 22, 0.7, W.MRT, W.FP64, (2e-5, 0, 0),
+                  [W.Solid(W.SPHERE, (11.3, 6.2, 14.8), 4.5)], scheme, 30,
+                  faces=(P, P, V, V, S, S), u_face=tuple(map(tuple, uf)))
+    f0 = random_populations(p, seed=13, amplitude=0.01)
+    g, o, _ = run_both(p, f0=f0, chunks=(1, 29))
+    g.close()

@@ -442,14 +442,15 @@ def _free_problem(dim, scheme):
 
 
 @pytest.mark.parametrize("dim", [2, 3])
-@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.YU_LIN, W.IBM])
-def test_free_solid_fp64(dim, scheme):
+@pytest.mark.parametrize("scheme,inertia", [(W.BOUZIDI_QUAD, W.FENG), (W.YU_LIN, W.FENG),
+                                            (W.IBM, W.FENG), (W.IBM, W.KEMPE)])
+def test_free_solid_fp64(dim, scheme, inertia):
     """A free solid (Eq. 20 under bounce-back, Eq. 23 under IBM), heavier
     than the fluid, moved across grid lines by its weight, the body-forced
     flow, a random initial flow and its initial velocity and spin: the
     fields, the force record, the centre and the velocities follow the
     oracle."""
-    p = _free_problem(dim, scheme)
+    p = _free_problem(dim, scheme).with_(ibm_inertia=inertia)
     g, o = make_gpu(p), make_oracle(p)
     gravity = (0.0, -4e-4, 2e-4 if dim == 3 else 0.0)
     g.set_solid_dynamics(0, 1.5, gravity)

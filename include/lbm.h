@@ -235,6 +235,16 @@ lbm_status lbm_get_distributions(lbm_ctx *ctx, double *host_f, size_t n);
  * pull collide-stream sweep with interpolated bounce-back on cut links
  * (Sec. 2.2) and the momentum exchange of Eq. 17. */
 lbm_status lbm_step(lbm_ctx *ctx, int nsteps);
+/* Advance n distinct lattices nsteps steps together (asynchronous): each
+ * step runs every lattice's boundary and IBM work as lbm_step does, and the
+ * bulk sweeps of lattices with the same lattice, collision and storage as
+ * one grouped launch (up to 8 lattices per launch) on the first one's stream;
+ * lattices on other streams are joined to it with events.  Results equal
+ * those of lbm_step on each lattice.  The grouped launch's kernel time is
+ * recorded on its first lattice (lbm_get_kernel_time, LBM_TIME_BULK), with
+ * the bulk nodes of the whole group.  LBM_ERR_ARG for a NULL or repeated
+ * lattice; any lattice's error stops the call (its message is on it). */
+lbm_status lbm_step_multi(lbm_ctx *const *ctxs, int n, int nsteps);
 /* Step in blocks of check_every until the velocity residual
  * ||u^n - u^(n-K)||_2 / ||u^n||_2 over fluid nodes drops below tol or
  * max_steps is reached.  LBM_ERR_DIVERGED on a non-finite residual. */

@@ -27,6 +27,20 @@ void launch_sweep_f32(SweepOp, int, int, const KArgs &, cudaStream_t);
 void launch_sweep_bf16(SweepOp, int, int, const KArgs &, cudaStream_t);
 void launch_sweep_f16(SweepOp, int, int, const KArgs &, cudaStream_t);
 
+bool launch_bulk_group_f32(const KArgs *, int, int, int, cudaStream_t);
+bool launch_bulk_group_bf16(const KArgs *, int, int, int, cudaStream_t);
+bool launch_bulk_group_f16(const KArgs *, int, int, int, cudaStream_t);
+
+bool launch_bulk_group(const KArgs *as, int n, int lattice, int collision, int precision,
+                       cudaStream_t st) {
+  switch (precision) {
+  case LBM_FP32: return launch_bulk_group_f32(as, n, lattice, collision, st);
+  case LBM_FP32_BF16STORE: return launch_bulk_group_bf16(as, n, lattice, collision, st);
+  case LBM_FP32_FP16STORE: return launch_bulk_group_f16(as, n, lattice, collision, st);
+  default: return false;  // FP64 runs the one-node kernel
+  }
+}
+
 void launch_sweep(SweepOp op, int lattice, int collision, int precision, const KArgs &a,
                   cudaStream_t st) {
   switch (precision) {
@@ -82,6 +96,7 @@ struct lbm_ctx {
   // pre-pass run there, concurrently with the bulk sweep on `st`
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  cudaEvent_t ev_grp = nullptr;  // lbm_step_multi: this lattice's stream joins a grouped launch
   int device = 0;
   size_t ssz = 0;  // storage element size
   size_t tsz = 0;  // compute element size
@@ -1009,7 +1024,17 @@ lbm_status prepare(lbm_ctx *ctx) {
   return LBM_OK;
 }
 
-lbm_status step_once(lbm_ctx *ctx) {
+// One step is step_begin (moving geometry, refill, the auxiliary stream's
+// boundary and IBM work), the bulk sweep on the main stream, and step_end
+// (join and solid motion); lbm_step_multi runs the bulk sweeps of several
+// lattices between their begins and ends as one grouped launch.
+struct StepState {
+  KArgs a;
+  bool ibm = false, moving = false, free_ = false, prefetch = false;
+  int nxt = 0;
+};
+
+lbm_status step_begin(lbm_ctx *ctx, StepState &ss) {
   const bool moving = any_moving(ctx);
   const bool ibm = ctx->scheme.scheme == LBM_IBM_DIRECT;
   if (moving && ctx->scheme.scheme == LBM_ZHAO_YONG)
@@ -1062,10 +1087,23 @@ lbm_status step_once(lbm_ctx *ctx) {
   }
   // nodes next to non-periodic domain faces
   if (ctx->nface) sweep(ctx, OP_FACE_SWEEP, a, ctx->aux);
-  {
-    Timed tm(ctx, TK_BULK, ctx->bulk_nodes, ctx->st);
-    sweep(ctx, OP_BULK_SWEEP, a, ctx->st);
-  }
+  ss.a = a;
+  ss.ibm = ibm;
+  ss.moving = moving;
+  ss.free_ = free_;
+  ss.prefetch = prefetch;
+  ss.nxt = nxt;
+  return LBM_OK;
+}
+
+void step_bulk(lbm_ctx *ctx, const StepState &ss) {
+  Timed tm(ctx, TK_BULK, ctx->bulk_nodes, ctx->st);
+  sweep(ctx, OP_BULK_SWEEP, ss.a, ctx->st);
+}
+
+lbm_status step_end(lbm_ctx *ctx, const StepState &ss) {
+  const bool ibm = ss.ibm, moving = ss.moving, free_ = ss.free_, prefetch = ss.prefetch;
+  const int nxt = ss.nxt;
   // join
   CK(cudaEventRecord(ctx->ev_join, ctx->aux));
   CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
@@ -1088,6 +1126,55 @@ lbm_status step_once(lbm_ctx *ctx) {
   }
   ctx->records = std::min<long long>(ctx->records + 1, kHistCap);
   ctx->step++;
+  return LBM_OK;
+}
+
+lbm_status step_once(lbm_ctx *ctx) {
+  StepState ss;
+  TRY(step_begin(ctx, ss));
+  step_bulk(ctx, ss);
+  return step_end(ctx, ss);
+}
+
+// The bulk sweeps of the lattices in `idx` (same lattice, collision and
+// storage) as grouped launches of up to kMaxGroup lattices on the first
+// one's stream; a lattice whose vector shape does not fit runs alone.
+lbm_status step_bulk_group(lbm_ctx *const *ctxs, const std::vector<int> &idx,
+                           std::vector<StepState> &ss) {
+  for (size_t g0 = 0; g0 < idx.size(); g0 += kMaxGroup) {
+    const size_t g1 = std::min(idx.size(), g0 + kMaxGroup);
+    lbm_ctx *lead = ctxs[idx[g0]];
+    lbm_ctx *ctx = lead;  // errors are reported on the group's first lattice
+    if (g1 - g0 >= 2) {
+      KArgs as[kMaxGroup];
+      long long nodes = 0;
+      for (size_t k = g0; k < g1; k++) {
+        lbm_ctx *c = ctxs[idx[k]];
+        as[k - g0] = ss[idx[k]].a;
+        nodes += c->bulk_nodes;
+        if (c->st != lead->st) {
+          CK(cudaEventRecord(c->ev_grp, c->st));
+          CK(cudaStreamWaitEvent(lead->st, c->ev_grp, 0));
+        }
+      }
+      bool ok;
+      {
+        Timed tm(lead, TK_BULK, nodes, lead->st);
+        ok = launch_bulk_group(as, (int)(g1 - g0), lead->d.lattice, lead->coll_mode,
+                               lead->d.precision, lead->st);
+      }
+      if (ok) {
+        lead->launches++;
+        CK(cudaEventRecord(lead->ev_grp, lead->st));
+        for (size_t k = g0 + 1; k < g1; k++) {
+          lbm_ctx *c = ctxs[idx[k]];
+          if (c->st != lead->st) CK(cudaStreamWaitEvent(c->st, lead->ev_grp, 0));
+        }
+        continue;
+      }
+    }
+    for (size_t k = g0; k < g1; k++) step_bulk(ctxs[idx[k]], ss[idx[k]]);
+  }
   return LBM_OK;
 }
 
@@ -1229,9 +1316,13 @@ lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_st
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
     // high priority: the boundary and IBM kernels start with the bulk sweep
     // (at the default priority they start late and the join waits on them)
-    if (cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, hi) != cudaSuccess ||
+    // LBM_AUX_PRIORITY: 0 lowest, 1 default, 2 highest (the default)
+    int prio = hi;
+    if (const char *e = getenv("LBM_AUX_PRIORITY")) prio = atoi(e) == 0 ? lo : atoi(e) == 1 ? 0 : hi;
+    if (cudaStreamCreateWithPriority(&ctx->aux, cudaStreamNonBlocking, prio) != cudaSuccess ||
         cudaEventCreateWithFlags(&ctx->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
-        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+        cudaEventCreateWithFlags(&ctx->ev_join, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&ctx->ev_grp, cudaEventDisableTiming) != cudaSuccess) {
       cudaGetLastError();
       lbm_destroy(ctx);
       return LBM_ERR_CUDA;
@@ -1315,6 +1406,7 @@ void lbm_destroy(lbm_ctx *ctx) {
   if (ctx->ev_gfree) cudaEventDestroy(ctx->ev_gfree);
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
+  if (ctx->ev_grp) cudaEventDestroy(ctx->ev_grp);
   for (void *p : ctx->allocs) cudaFree(p);
   for (auto &p : ctx->pending) {
     cudaEventDestroy(p.a);
@@ -1434,6 +1526,45 @@ lbm_status lbm_step(lbm_ctx *ctx, int nsteps) {
   TRY(prepare(ctx));
   for (int k = 0; k < nsteps; k++) TRY(step_once(ctx));
   CK(cudaGetLastError());
+  return LBM_OK;
+}
+
+lbm_status lbm_step_multi(lbm_ctx *const *ctxs, int n, int nsteps) {
+  if (!ctxs || n < 1 || nsteps < 0) return LBM_ERR_ARG;
+  for (int i = 0; i < n; i++) {
+    if (!ctxs[i]) return LBM_ERR_ARG;
+    for (int j = 0; j < i; j++)
+      if (ctxs[j] == ctxs[i]) return fail(ctxs[i], LBM_ERR_ARG, "a lattice appears twice");
+  }
+  for (int i = 0; i < n; i++) TRY(prepare(ctxs[i]));
+  // lattices that can share a bulk launch: same lattice, collision and storage
+  std::vector<std::vector<int>> groups;
+  for (int i = 0; i < n; i++) {
+    bool placed = false;
+    for (auto &g : groups) {
+      const lbm_ctx *c = ctxs[g[0]];
+      if (c->d.lattice == ctxs[i]->d.lattice && c->coll_mode == ctxs[i]->coll_mode &&
+          c->d.precision == ctxs[i]->d.precision && c->device == ctxs[i]->device) {
+        g.push_back(i);
+        placed = true;
+        break;
+      }
+    }
+    if (!placed) groups.push_back({i});
+  }
+  std::vector<StepState> ss(n);
+  for (int k = 0; k < nsteps; k++) {
+    for (int i = 0; i < n; i++) TRY(step_begin(ctxs[i], ss[i]));
+    for (auto &g : groups) {
+      lbm_status st = step_bulk_group(ctxs, g, ss);
+      if (st != LBM_OK) return st;
+    }
+    for (int i = 0; i < n; i++) TRY(step_end(ctxs[i], ss[i]));
+  }
+  for (int i = 0; i < n; i++) {
+    lbm_ctx *ctx = ctxs[i];
+    CK(cudaGetLastError());
+  }
   return LBM_OK;
 }
 

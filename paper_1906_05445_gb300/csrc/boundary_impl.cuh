@@ -915,6 +915,57 @@ bool launch_bulk_vec(const KArgs &a, int want, cudaStream_t st) {
   return launch_bulk_vec_w<LAT, CM, S, 2>(a, want, packed, st);
 }
 
+template <int LAT, int CM, typename S, int W, bool PACKED>
+bool launch_group_w(const KArgs *as, int n, int want, cudaStream_t st) {
+  constexpr int V = W * VecS<S>::per_word;
+  static_assert(sizeof(GroupArgs) <= 32000, "kernel parameter space");
+  GroupArgs g;
+  g.n = n;
+  int blocks = 0;
+  for (int k = 0; k < n; k++) {
+    if (as[k].nx % V != 0 || as[k].fs % V != 0) return false;
+    g.block_start[k] = blocks;
+    blocks += div_up(as[k].N / V, want);
+    g.a[k] = as[k];
+  }
+  g.block_start[n] = blocks;
+  k_bulk_vec_group<LAT, CM, S, W, PACKED><<<blocks, want, 0, st>>>(g);
+  return true;
+}
+
+template <int LAT, int CM, typename S>
+bool launch_group_t(const KArgs *as, int n, cudaStream_t st) {
+  if constexpr (CM == CM_MRT) {
+    return false;
+  } else {
+    const KArgs &a0 = as[0];
+    for (int k = 1; k < n; k++)
+      if (as[k].bulk_mode != a0.bulk_mode || as[k].bulk_vec_words != a0.bulk_vec_words ||
+          as[k].bulk_vec_packed != a0.bulk_vec_packed || as[k].bulk_block != a0.bulk_block)
+        return false;
+    if (a0.bulk_mode != 1 || n < 1 || n > kMaxGroup) return false;
+    const int want = a0.bulk_block > 0 ? a0.bulk_block : 128;
+    const bool packed = a0.bulk_vec_packed >= 0 ? a0.bulk_vec_packed != 0 : sizeof(S) == 2;
+    if (a0.bulk_vec_words == 4)
+      return packed ? launch_group_w<LAT, CM, S, 4, true>(as, n, want, st)
+                    : launch_group_w<LAT, CM, S, 4, false>(as, n, want, st);
+    return packed ? launch_group_w<LAT, CM, S, 2, true>(as, n, want, st)
+                  : launch_group_w<LAT, CM, S, 2, false>(as, n, want, st);
+  }
+}
+
+template <typename S>
+bool launch_group_precision(const KArgs *as, int n, int lattice, int collision, cudaStream_t st) {
+  if (lattice == LBM_D2Q9) {
+    if (collision == CM_MRT_Q) return launch_group_t<0, CM_MRT_Q, S>(as, n, st);
+    if (collision == CM_BGK) return launch_group_t<0, CM_BGK, S>(as, n, st);
+  } else {
+    if (collision == CM_MRT_Q) return launch_group_t<1, CM_MRT_Q, S>(as, n, st);
+    if (collision == CM_BGK) return launch_group_t<1, CM_BGK, S>(as, n, st);
+  }
+  return false;
+}
+
 template <int LAT, int CM, typename S, typename T>
 void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
   const int want = a.bulk_block > 0 ? a.bulk_block : 128;

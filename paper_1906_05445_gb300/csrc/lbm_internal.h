@@ -126,6 +126,22 @@ enum SweepOp {
   OP_KEMPE         // Eq. 24: the fluid momentum inside a solid, from f*(t) and the forces
 };
 
+// The bulk sweeps of up to kMaxGroup lattices in one grid (the blocks of
+// lattice k start at block_start[k]): short sweeps of several lattices then
+// share one launch's ramp-up and tail instead of paying them one after the
+// other.
+constexpr int kMaxGroup = 8;
+struct GroupArgs {
+  int n;
+  int block_start[kMaxGroup + 1];
+  KArgs a[kMaxGroup];
+};
+// Launches the group when every lattice takes the same vector bulk kernel
+// (lattice, collision, storage, vector shape and block size); false, with
+// nothing launched, otherwise.
+bool launch_bulk_group(const KArgs *as, int n, int lattice, int collision, int precision,
+                       cudaStream_t st);
+
 // Launch one operation for the given lattice/collision/precision.  grid
 // sizes are chosen by the launcher; counts on the device bound list work.
 void launch_sweep(SweepOp op, int lattice, int collision, int precision,

@@ -411,4 +411,26 @@ __global__ void __launch_bounds__(256) k_bulk_vec(const KArgs a) {
                                          (unsigned)a.N / V);
 }
 
+// The same update for several lattices in one grid: block b belongs to the
+// last lattice k with block_start[k] <= b.
+// Each lattice gets its own inlined copy of the update, so that its
+// arguments stay constant-bank operands (indexing the argument array by a
+// run-time k holds them in registers: 92 instead of 80, one block per SM
+// fewer).
+// Register limits near the single-lattice kernel's: 80 for the FP32
+// node-by-node variant (6 blocks of 128 per SM), 128 for the 2-word 16-bit
+// ones; 4-word vectors are left unbounded.
+template <int LAT, int CM, typename S, int W, bool PACKED>
+__global__ void __launch_bounds__(256, W == 4 ? 1 : (sizeof(S) == 4 && !PACKED) ? 3 : 2)
+    k_bulk_vec_group(const __grid_constant__ GroupArgs g) {
+  constexpr int V = W * VecS<S>::per_word;
+  const int b = (int)blockIdx.x;
+  static_for<kMaxGroup>([&](auto kc) {
+    constexpr int k = decltype(kc)::value;
+    if (k < g.n && b >= g.block_start[k] && b < g.block_start[k + 1])
+      bulk_vec_update<LAT, CM, S, W, PACKED>(
+          g.a[k], (unsigned)(b - g.block_start[k]) * blockDim.x + threadIdx.x, (unsigned)g.a[k].N / V);
+  });
+}
+
 }  // namespace lbm

@@ -98,6 +98,7 @@ def _load():
         "lbm_copy_force_torque_async": (st, [vp, i, dp]),
         "lbm_set_solid_dynamics": (st, [vp, i, d, dp]),
         "lbm_set_domain": (st, [vp, C.POINTER(lbm_domain_desc)]),
+        "lbm_step_multi": (st, [C.POINTER(vp), i, i]),
         "lbm_get_solid_velocity": (st, [vp, i, dp, dp]),
         "lbm_get_residual": (st, [vp, dp]),
         "lbm_get_solid_centre": (st, [vp, i, dp]),
@@ -133,7 +134,7 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_get_velocity", "lbm_get_strain_rate", "lbm_get_stress",
     "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
     "lbm_copy_force_torque_async", "lbm_set_solid_dynamics", "lbm_get_solid_velocity",
-    "lbm_set_domain",
+    "lbm_set_domain", "lbm_step_multi",
     "lbm_get_residual", "lbm_get_solid_centre", "lbm_get_info",
     "lbm_device_field", "lbm_save", "lbm_load", "lbm_set_timing",
     "lbm_get_kernel_time", "lbm_get_velocity_noalloc", "lbm_sync", "lbm_last_error",
@@ -349,6 +350,16 @@ class Lattice:
 
     def sync(self):
         self._check(lbm_sync(self.h))
+
+
+def step_multi(lattices: Sequence["Lattice"], nsteps: int = 1):
+    """Advance distinct lattices together; their bulk sweeps run as grouped
+    launches (lbm_step_multi)."""
+    arr = (C.c_void_p * len(lattices))(*[lt.h.value for lt in lattices])
+    st = lbm_step_multi(arr, len(lattices), int(nsteps))
+    if st != LBM_OK:
+        msg = "; ".join(m for m in (lbm_last_error(lt.h).decode() for lt in lattices) if m)
+        raise LbmError(st, msg)
 
 
 class Batch:

@@ -1346,6 +1346,10 @@ lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_st
       if (b >= 32 && b <= 512 && b % 32 == 0) ctx->bulk_block = b;
     }
     if (const char *e = getenv("LBM_CACHE_HINTS")) ctx->cache_hints = atoi(e) & 3;
+    if (const char *e = getenv("LBM_LIST_BLOCK")) {
+      const int v = atoi(e);
+      if (v == 32 || v == 64 || v == 128 || v == 256) ctx->list_block = v;
+    }
     if (const char *e = getenv("LBM_BULK_MODE")) ctx->bulk_mode = atoi(e);
     if (const char *e = getenv("LBM_VEC_WORDS")) ctx->bulk_vec_words = atoi(e);
     if (const char *e = getenv("LBM_GEOM_PREFETCH")) ctx->geom_prefetch = atoi(e) != 0;

@@ -255,11 +255,13 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, int check_every,
  * density [nodes]; velocity [d][nodes] with the half-force correction;
  * strain rate [d(d+1)/2][nodes] from non-equilibrium moments (Sec. 3.1,
  *   Eq. 19 generalised), order xx, yy, xy (2D) / xx, yy, zz, xy, yz, xz (3D);
- * stress = -c_s^2 rho I + 2 rho0 nu S, same order. */
+ * stress = -c_s^2 rho I + 2 rho0 nu S, same order;
+ * dissipation rate epsilon = 2 nu s_ij s_ij (Sec. 3.1) [nodes]. */
 lbm_status lbm_get_density(lbm_ctx *ctx, double *host_out, size_t n);
 lbm_status lbm_get_velocity(lbm_ctx *ctx, double *host_out, size_t n);
 lbm_status lbm_get_strain_rate(lbm_ctx *ctx, double *host_out, size_t n);
 lbm_status lbm_get_stress(lbm_ctx *ctx, double *host_out, size_t n);
+lbm_status lbm_get_dissipation(lbm_ctx *ctx, double *host_out, size_t n);
 /* 1 where the node carries no distributions (solid under bounce-back). */
 lbm_status lbm_get_solid_mask(lbm_ctx *ctx, unsigned char *host_out, size_t n);
 

@@ -1302,6 +1302,24 @@ void ora_strain_rate(ora_sim *s, double *S) {
   }
 }
 
+/* Viscous dissipation rate (Sec. 3.1): epsilon = 2 nu s_ij s_ij, the strain
+ * rate from the non-equilibrium moments as above, nu = (tau - 1/2) c_s^2. */
+void ora_dissipation(ora_sim *s, double *eps) {
+  const int d = s->d, nc = d == 2 ? 3 : 6;
+  double *S = (double *)malloc(sizeof(double) * (size_t)nc * s->N);
+  ora_strain_rate(s, S);
+  const double nu = (s->tau - 0.5) * CS2;
+  for (long n = 0; n < s->N; n++) {
+    double ss = 0;
+    for (int c = 0; c < nc; c++) {
+      const double v = S[c * s->N + n];
+      ss += (c < d ? 1.0 : 2.0) * v * v;  /* off-diagonal entries appear twice */
+    }
+    eps[n] = 2 * nu * ss;
+  }
+  free(S);
+}
+
 void ora_solid_mask(ora_sim *s, unsigned char *m) {
   for (long n = 0; n < s->N; n++) m[n] = simulated(s, n) ? 0 : 1;
 }

@@ -66,6 +66,7 @@ def lib():
                 "ora_set_solid_dynamics": (None, [vp, i, d, dp]),
                 "ora_solid_velocity": (None, [vp, i, dp, dp]),
                 "ora_set_domain": (i, [vp, C.POINTER(C.c_int), dp]),
+                "ora_dissipation": (None, [vp, dp]),
                 "ora_create": (vp, [i, i, i, i, d, i, dp, dp, i]),
                 "ora_destroy": (None, [vp]),
                 "ora_add_solid": (i, [vp, i, dp, d, dp, dp, i]),
@@ -300,6 +301,11 @@ class OracleSim:
         c = np.zeros(3)
         self.L.ora_solid_centre(self.h, sid, _p(c))
         return c
+
+    def dissipation(self):
+        e = np.zeros(self.N)
+        self.L.ora_dissipation(self.h, _p(e))
+        return e.reshape(self.shape)
 
     def set_domain(self, faces, u_face=None):
         """Face types x-, x+, y-, y+, z-, z+ and the velocity of each face

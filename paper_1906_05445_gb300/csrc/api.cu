@@ -1201,12 +1201,12 @@ void run_query(lbm_ctx *ctx, KArgs a) {
   }
 }
 
-enum QueryKind { Q_RHO, Q_U, Q_S, Q_STRESS, Q_F };
+enum QueryKind { Q_RHO, Q_U, Q_S, Q_STRESS, Q_F, Q_EPS };
 
 lbm_status query(lbm_ctx *ctx, QueryKind kind, double *host, size_t n) {
   if (!ctx) return LBM_ERR_ARG;
   const int nc = ctx->D == 2 ? 3 : 6;
-  size_t comps = kind == Q_RHO ? 1 : kind == Q_U ? ctx->D : kind == Q_F ? ctx->Q : nc;
+  size_t comps = (kind == Q_RHO || kind == Q_EPS) ? 1 : kind == Q_U ? ctx->D : kind == Q_F ? ctx->Q : nc;
   const size_t need = comps * (size_t)ctx->N;
   if (!host || n < need) return fail(ctx, LBM_ERR_ARG, "output buffer too small: need " + std::to_string(need));
   TRY(prepare(ctx));
@@ -1218,6 +1218,7 @@ lbm_status query(lbm_ctx *ctx, QueryKind kind, double *host, size_t n) {
   case Q_U: a.out_u = ctx->qbuf; break;
   case Q_S: a.out_S = ctx->qbuf; break;
   case Q_STRESS: a.out_stress = ctx->qbuf; break;
+  case Q_EPS: a.out_eps = ctx->qbuf; break;
   case Q_F: a.out_f = ctx->qbuf; break;
   }
   run_query(ctx, a);
@@ -1612,6 +1613,7 @@ lbm_status lbm_get_density(lbm_ctx *ctx, double *o, size_t n) { return query(ctx
 lbm_status lbm_get_velocity(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_U, o, n); }
 lbm_status lbm_get_strain_rate(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_S, o, n); }
 lbm_status lbm_get_stress(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_STRESS, o, n); }
+lbm_status lbm_get_dissipation(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_EPS, o, n); }
 
 lbm_status lbm_get_solid_mask(lbm_ctx *ctx, unsigned char *host_out, size_t n) {
   if (!ctx || !host_out || n < (size_t)ctx->N) return LBM_ERR_ARG;

@@ -77,7 +77,7 @@ __device__ __forceinline__ void write_fields(const KArgs &a, long long n,
   if (a.out_f)
 #pragma unroll
     for (int i = 0; i < Q; i++) a.out_f[(long long)i * a.N + n] = L::w(i) + fd[i];
-  if (a.out_S || a.out_stress) {
+  if (a.out_S || a.out_stress || a.out_eps) {
     const double uu = u[0] * u[0] + u[1] * u[1] + u[2] * u[2];
     double P[3][3];
     for (int p = 0; p < 3; p++)
@@ -94,6 +94,7 @@ __device__ __forceinline__ void write_fields(const KArgs &a, long long n,
     const int nc = D == 2 ? 3 : 6;
     const int ca[6] = {0, 1, D == 2 ? 0 : 2, 0, 1, 0};
     const int cb[6] = {0, 1, D == 2 ? 1 : 2, 1, 2, 2};
+    double ss = 0;
     for (int c = 0; c < nc; c++) {
       const int p = ca[c], q = cb[c];
       const double iso = p == q ? tr / D : 0.0;
@@ -101,7 +102,9 @@ __device__ __forceinline__ void write_fields(const KArgs &a, long long n,
       if (a.out_S) a.out_S[c * a.N + n] = S;
       if (a.out_stress)
         a.out_stress[c * a.N + n] = (p == q ? -(1.0 + drho) / 3.0 : 0.0) + 2.0 * a.nu * S;
+      ss += (p == q ? 1.0 : 2.0) * S * S;
     }
+    if (a.out_eps) a.out_eps[n] = 2.0 * a.nu * ss;
   }
 }
 

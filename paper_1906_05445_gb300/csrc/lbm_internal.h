@@ -75,6 +75,7 @@ struct KArgs {
   const uint8_t *sid;
   // query outputs (FP64); unused pointers are null
   double *out_rho, *out_u, *out_S, *out_stress, *out_f;
+  double *out_eps;   // dissipation rate 2 nu s_ij s_ij
   int local_gather;  // 1: read src locally (pre-collision state), 0: pull
   int bulk_block;    // threads per block of the bulk sweep (multiple of 32)
   int cache_hints;   // bulk sweep: bit 0 evict-first loads, bit 1 evict-first stores

@@ -92,6 +92,7 @@ def _load():
         "lbm_get_velocity": (st, [vp, dp, sz]),
         "lbm_get_strain_rate": (st, [vp, dp, sz]),
         "lbm_get_stress": (st, [vp, dp, sz]),
+        "lbm_get_dissipation": (st, [vp, dp, sz]),
         "lbm_get_solid_mask": (st, [vp, C.POINTER(C.c_ubyte), sz]),
         "lbm_get_force_torque": (st, [vp, i, dp, dp]),
         "lbm_get_force_history": (st, [vp, i, dp, sz, C.POINTER(sz)]),
@@ -131,7 +132,7 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_create", "lbm_destroy", "lbm_add_solid", "lbm_set_solid_motion",
     "lbm_set_scheme", "lbm_init_equilibrium", "lbm_set_distributions",
     "lbm_get_distributions", "lbm_step", "lbm_run_to_steady", "lbm_get_density",
-    "lbm_get_velocity", "lbm_get_strain_rate", "lbm_get_stress",
+    "lbm_get_velocity", "lbm_get_strain_rate", "lbm_get_stress", "lbm_get_dissipation",
     "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
     "lbm_copy_force_torque_async", "lbm_set_solid_dynamics", "lbm_get_solid_velocity",
     "lbm_set_domain", "lbm_step_multi",
@@ -270,6 +271,9 @@ class Lattice:
 
     def stress(self):
         return self._field(lbm_get_stress, 3 if self.d == 2 else 6)
+
+    def dissipation(self):
+        return self._field(lbm_get_dissipation, 1)[0]
 
     def solid_mask(self):
         m = np.zeros(self.N, dtype=np.uint8)

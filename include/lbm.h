@@ -289,12 +289,13 @@ lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int solid_id, double density_rat
 /* The solid's current velocity and angular velocity. */
 lbm_status lbm_get_solid_velocity(lbm_ctx *ctx, int solid_id, double U[3], double Om[3]);
 /* The same record (Fx Fy Fz Tx Ty Tz) copied to host_out without waiting:
- * the copy is enqueued on the context's stream after the work already
- * there, so a caller that reads the force every step can keep the GPU busy
- * and wait once (lbm_sync, or an event on the stream) before reading the
- * values.  host_out must stay valid until then, and should be page-locked
- * (e.g. cudaHostAlloc) for the copy to be asynchronous.  CUDA errors are
- * reported by the next synchronising call. */
+ * the copy runs on a copy stream of the context, after the work already
+ * enqueued on the context's stream, and later steps do not wait for it.  A
+ * caller that reads the force every step keeps the GPU busy and waits once
+ * with lbm_sync (which also waits for the copies) before reading the values.
+ * host_out must stay valid until then, and should be page-locked (e.g.
+ * cudaHostAlloc) for the copy to be asynchronous.  CUDA errors are reported
+ * by the next synchronising call. */
 lbm_status lbm_copy_force_torque_async(lbm_ctx *ctx, int solid_id, double *host_out);
 /* The last min(max_steps, steps kept) records, oldest first, 6 doubles
  * (Fx Fy Fz Tx Ty Tz) per step; *n receives the count. */

@@ -97,6 +97,11 @@ struct lbm_ctx {
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   cudaEvent_t ev_grp = nullptr;  // lbm_step_multi: this lattice's stream joins a grouped launch
+  // lbm_copy_force_torque_async: the copies run on their own stream, after
+  // an event of the step, so that they do not hold up the next step
+  cudaStream_t cst = nullptr;
+  cudaEvent_t ev_rec = nullptr, ev_cst = nullptr;
+  long long copies = 0;
   int device = 0;
   size_t ssz = 0;  // storage element size
   size_t tsz = 0;  // compute element size
@@ -1412,6 +1417,12 @@ void lbm_destroy(lbm_ctx *ctx) {
   if (ctx->ev_fork) cudaEventDestroy(ctx->ev_fork);
   if (ctx->ev_join) cudaEventDestroy(ctx->ev_join);
   if (ctx->ev_grp) cudaEventDestroy(ctx->ev_grp);
+  if (ctx->cst) {
+    cudaStreamSynchronize(ctx->cst);
+    cudaStreamDestroy(ctx->cst);
+  }
+  if (ctx->ev_rec) cudaEventDestroy(ctx->ev_rec);
+  if (ctx->ev_cst) cudaEventDestroy(ctx->ev_cst);
   for (void *p : ctx->allocs) cudaFree(p);
   for (auto &p : ctx->pending) {
     cudaEventDestroy(p.a);
@@ -1642,8 +1653,20 @@ lbm_status lbm_get_force_torque(lbm_ctx *ctx, int id, double F[3], double T[3]) 
 lbm_status lbm_copy_force_torque_async(lbm_ctx *ctx, int id, double *host_out) {
   if (!ctx || !host_out || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
   TRY(prepare(ctx));
+  if (!ctx->cst) {
+    CK(cudaStreamCreateWithFlags(&ctx->cst, cudaStreamNonBlocking));
+    CK(cudaEventCreateWithFlags(&ctx->ev_rec, cudaEventDisableTiming));
+    CK(cudaEventCreateWithFlags(&ctx->ev_cst, cudaEventDisableTiming));
+  }
+  CK(cudaEventRecord(ctx->ev_rec, ctx->st));
+  CK(cudaStreamWaitEvent(ctx->cst, ctx->ev_rec, 0));
   CK(cudaMemcpyAsync(host_out, force_slot(ctx, ctx->slot) + 6 * id, 6 * sizeof(double),
-                     cudaMemcpyDeviceToHost, ctx->st));
+                     cudaMemcpyDeviceToHost, ctx->cst));
+  // the record ring holds kHistCap steps: keep the copies well behind it
+  if (++ctx->copies % 1024 == 0) {
+    CK(cudaEventRecord(ctx->ev_cst, ctx->cst));
+    CK(cudaStreamWaitEvent(ctx->st, ctx->ev_cst, 0));
+  }
   return LBM_OK;
 }
 
@@ -1991,6 +2014,7 @@ lbm_status lbm_get_velocity_noalloc(lbm_ctx *ctx, double *host_out, size_t n) {
 lbm_status lbm_sync(lbm_ctx *ctx) {
   if (!ctx) return LBM_ERR_ARG;
   CK(cudaStreamSynchronize(ctx->st));
+  if (ctx->cst) CK(cudaStreamSynchronize(ctx->cst));
   CK(cudaGetLastError());
   int cnt[16];
   TRY(read_counts(ctx, cnt));

@@ -367,7 +367,10 @@ const char *lbm_last_error(const lbm_ctx *ctx);
  * boundary-node block widths per lattice shape by timing the kernels into a
  * scratch buffer (the simulation state is untouched).  While in a batch the
  * contexts must be stepped only through the batch; their queries remain
- * valid.  lbm_batch_destroy gives the contexts their streams back (it does
+ * valid, and a context reconfigured between batch calls (scheme, solids,
+ * domain, populations) steps from its new configuration: every such call
+ * makes the captured graph stale, and the next batch call prepares the
+ * context and captures again.  lbm_batch_destroy gives the contexts their streams back (it does
  * not destroy them).  The batch runs on private streams but is ordered on
  * cuda_stream: lbm_batch_step and lbm_batch_run_to_steady start after the
  * work already queued there, and work queued there afterwards (an event, a

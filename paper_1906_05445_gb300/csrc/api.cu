@@ -96,6 +96,9 @@ struct lbm_ctx {
   // pre-pass run there, concurrently with the bulk sweep on `st`
   cudaStream_t aux = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+  // bumped by every call that changes what a step's launches read (their
+  // arguments, buffers or state): a batch's captured graph is then stale
+  unsigned long long gen = 0;
   cudaEvent_t ev_grp = nullptr;  // lbm_step_multi: this lattice's stream joins a grouped launch
   // lbm_copy_force_torque_async: the copies run on their own stream, after
   // an event of the step, so that they do not hold up the next step
@@ -803,6 +806,7 @@ lbm_status read_counts(lbm_ctx *ctx, int out[16]) {
 // Full rebuild over the whole lattice (solids or scheme changed): count the
 // boundary nodes and links first, size the lists exactly, then build.
 lbm_status rebuild_full(lbm_ctx *ctx) {
+  if (ctx) ctx->gen++;
   free_spare(ctx);  // capacities may change; the next moving step prefetches again
   if (!ctx->restore_geometry)
     for (auto &s : ctx->solids) memcpy(s.cg, s.c, sizeof(s.c));
@@ -1005,6 +1009,7 @@ void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStr
 
 // Collide the pre-collision state held in f[1-cur] into f[cur].
 lbm_status init_collide(lbm_ctx *ctx) {
+  if (ctx) ctx->gen++;
   TRY(ensure_geometry(ctx));
   const int prev = 1 - ctx->cur;
   ctx->slot = (ctx->slot + 1) % kHistCap;
@@ -1433,6 +1438,7 @@ void lbm_destroy(lbm_ctx *ctx) {
 }
 
 lbm_status lbm_add_solid(lbm_ctx *ctx, const lbm_solid_desc *solid, int *solid_id) {
+  if (ctx) ctx->gen++;
   if (!ctx || !solid) return LBM_ERR_ARG;
   if ((int)ctx->solids.size() >= kMaxSolids) return fail(ctx, LBM_ERR_CAPACITY, "at most 8 solids");
   if (solid->kind != LBM_SPHERE && solid->kind != LBM_CYLINDER_Z)
@@ -1455,6 +1461,7 @@ lbm_status lbm_add_solid(lbm_ctx *ctx, const lbm_solid_desc *solid, int *solid_i
 
 lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int id, const double centre[3], const double vel[3],
                                 const double omega[3]) {
+  if (ctx) ctx->gen++;
   if (!ctx || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
   SolidHost &h = ctx->solids[id];
   bool moved = false;
@@ -1476,6 +1483,7 @@ lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int id, const double centre[3], co
 }
 
 lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme) {
+  if (ctx) ctx->gen++;
   if (!ctx || !scheme) return LBM_ERR_ARG;
   if (scheme->scheme < LBM_SCHEME_NONE || scheme->scheme > LBM_ZHAO_YONG)
     return fail(ctx, LBM_ERR_ARG, "unknown scheme");
@@ -1503,6 +1511,7 @@ lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme) {
 }
 
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, double rho, const double u[3]) {
+  if (ctx) ctx->gen++;
   if (!ctx || !(rho > 0)) return LBM_ERR_ARG;
   TRY(ensure_geometry(ctx));
   KArgs a = base_args(ctx);
@@ -1517,6 +1526,7 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, double rho, const double u[3]) {
 }
 
 lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *host_f, size_t n) {
+  if (ctx) ctx->gen++;
   if (!ctx || !host_f) return LBM_ERR_ARG;
   const size_t need = (size_t)ctx->Q * ctx->N;
   if (n < need) return fail(ctx, LBM_ERR_ARG, "input must hold Q * nodes doubles");
@@ -1692,6 +1702,7 @@ lbm_status lbm_get_residual(lbm_ctx *ctx, double *r) {
 }
 
 lbm_status lbm_set_domain(lbm_ctx *ctx, const lbm_domain_desc *dom) {
+  if (ctx) ctx->gen++;
   if (!ctx) return LBM_ERR_ARG;
   lbm_domain_desc d{};
   if (dom) d = *dom;
@@ -1759,6 +1770,7 @@ lbm_status lbm_set_domain(lbm_ctx *ctx, const lbm_domain_desc *dom) {
 
 lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int id, double density_ratio,
                                   const double gravity[3]) {
+  if (ctx) ctx->gen++;
   if (!ctx || id < 0 || id >= (int)ctx->solids.size() || !(density_ratio == density_ratio))
     return LBM_ERR_ARG;
   if (density_ratio > 0 && ctx->scheme.scheme != LBM_IBM_DIRECT && !is_ibb(ctx->scheme.scheme))
@@ -1888,6 +1900,7 @@ lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size) {
 }
 
 lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size) {
+  if (ctx) ctx->gen++;
   if (!ctx || !host_buf || size < sizeof(SaveHeader)) return LBM_ERR_ARG;
   if (ctx->outlet)
     return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints do not carry the outflow face's state");
@@ -2050,6 +2063,7 @@ struct lbm_batch {
   std::vector<double> residual;
   cudaGraphExec_t exec = nullptr;
   std::vector<int> graph_cur;          // cur of each lattice when captured
+  std::vector<unsigned long long> graph_gen;  // gen of each lattice when captured
   std::vector<long long> pair_launches;  // kernels of one captured step pair
   std::vector<int> graph_slot;           // force-record slot of the pair's 2nd step
   std::vector<char> in_graph;
@@ -2136,6 +2150,7 @@ lbm_status capture(lbm_batch *b) {
   const int n = (int)b->ctx.size();
   b->in_graph.assign(n, 0);
   b->graph_cur.assign(n, 0);
+  b->graph_gen.assign(n, 0);
   b->pair_launches.assign(n, 0);
   b->graph_slot.assign(n, 0);
   struct Saved {
@@ -2155,6 +2170,7 @@ lbm_status capture(lbm_batch *b) {
     saved[i] = {c->cur, c->slot, c->prev_local, c->timing, c->step, c->launches, c->records};
     c->timing = 0;
     b->graph_cur[i] = c->cur;
+    b->graph_gen[i] = c->gen;
     cudaStreamWaitEvent(c->st, b->ev_origin, 0);
     st = step_once(c);
     if (st == LBM_OK) st = step_once(c);
@@ -2216,6 +2232,7 @@ bool graph_valid(const lbm_batch *b) {
     const bool want = b->active[i] && !any_moving(b->ctx[i]);
     if (want != (bool)b->in_graph[i]) return false;
     if (want && b->ctx[i]->cur != b->graph_cur[i]) return false;
+    if (want && b->ctx[i]->gen != b->graph_gen[i]) return false;
   }
   return true;
 }
@@ -2237,6 +2254,14 @@ lbm_status leave(lbm_batch *b) {
 
 lbm_status batch_advance(lbm_batch *b, int nsteps) {
   const int n = (int)b->ctx.size();
+  // a member changed since the last call (geometry, initial state) is brought
+  // up to date before any captured step runs; its bumped generation then
+  // makes the graph stale
+  for (int i = 0; i < n; i++)
+    if (b->active[i]) {
+      lbm_status s = prepare(b->ctx[i]);
+      if (s != LBM_OK) return bfail(b, s, lbm_last_error(b->ctx[i]));
+    }
   int done = 0;
   while (done < nsteps) {
     const bool pair = nsteps - done >= 2;

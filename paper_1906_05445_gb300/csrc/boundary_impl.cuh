@@ -947,13 +947,14 @@ bool launch_group_t(const KArgs *as, int n, cudaStream_t st) {
           as[k].bulk_vec_packed != a0.bulk_vec_packed || as[k].bulk_block != a0.bulk_block)
         return false;
     if (a0.bulk_mode != 1 || n < 1 || n > kMaxGroup) return false;
+    // only the default vector shape of the storage type is built grouped (2
+    // words; node by node for FP32, packed pairs for 16-bit storage): each
+    // grouped variant inlines the update kMaxGroup times
+    constexpr bool kPacked = sizeof(S) == 2;
+    const bool packed = a0.bulk_vec_packed >= 0 ? a0.bulk_vec_packed != 0 : kPacked;
+    if (a0.bulk_vec_words == 4 || packed != kPacked) return false;
     const int want = a0.bulk_block > 0 ? a0.bulk_block : 128;
-    const bool packed = a0.bulk_vec_packed >= 0 ? a0.bulk_vec_packed != 0 : sizeof(S) == 2;
-    if (a0.bulk_vec_words == 4)
-      return packed ? launch_group_w<LAT, CM, S, 4, true>(as, n, want, st)
-                    : launch_group_w<LAT, CM, S, 4, false>(as, n, want, st);
-    return packed ? launch_group_w<LAT, CM, S, 2, true>(as, n, want, st)
-                  : launch_group_w<LAT, CM, S, 2, false>(as, n, want, st);
+    return launch_group_w<LAT, CM, S, 2, kPacked>(as, n, want, st);
   }
 }
 

@@ -134,8 +134,11 @@ enum {
 /* inertia of the fluid inside a free solid under IBM (Sec. 4.1) */
 enum {
   LBM_INERTIA_FENG = 0, /* rigid-body inside fluid, Feng & Michaelides, Eq. 23 (default) */
-  LBM_INERTIA_KEMPE = 1 /* Kempe et al.: volume integrals over level-set cell fractions,
-                           Eqs. 24-26 */
+  LBM_INERTIA_KEMPE = 1, /* Kempe et al.: volume integrals over level-set cell fractions,
+                            Eqs. 24-26 */
+  LBM_INERTIA_UHLMANN = 2 /* Uhlmann: the inside fluid's inertia taken off the solid's,
+                             Eq. 22; needs rho_p > rho_f (LBM_ERR_ARG otherwise) and is
+                             unstable below a density ratio of about 2 in 2D */
 };
 
 /* Scheme.  For LBM_IBM_DIRECT: ibm_iters >= 1 forcing iterations (Eq. 9
@@ -277,7 +280,8 @@ lbm_status lbm_get_force_torque(lbm_ctx *ctx, int solid_id, double F[3],
  * bounce-back, under IBM the Feng & Michaelides discretisation of Eq. 23
  * or, with ibm_inertia = LBM_INERTIA_KEMPE, rho_f times the change over the
  * last step of the inside fluid's momentum and angular momentum summed with
- * the level-set cell fractions of Eqs. 24-26 (dt = 1, rho_f = 1); its
+ * the level-set cell fractions of Eqs. 24-26, or with LBM_INERTIA_UHLMANN
+ * Eq. 22 (dt = 1, rho_f = 1); its
  * centre moves by the mean of the old and new
  * velocity.  Spheres have V = 4/3 pi R^3 and I = 2/5 m R^2; cylinders
  * V = pi R^2 (times nz in 3D) and I = 1/2 m R^2 about z, turning about z

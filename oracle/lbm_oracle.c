@@ -613,7 +613,8 @@ void ora_set_scheme(ora_sim *s, int scheme, int ibm_iters, double retraction,
 }
 
 void ora_set_ibm_inertia(ora_sim *s, int inertia) {
-  s->ibm_inertia = inertia == ORA_INERTIA_KEMPE ? ORA_INERTIA_KEMPE : ORA_INERTIA_FENG;
+  s->ibm_inertia = (inertia == ORA_INERTIA_KEMPE || inertia == ORA_INERTIA_UHLMANN)
+                       ? inertia : ORA_INERTIA_FENG;
   for (int k = 0; k < s->nsol; k++) s->sol[k].have_Ip = 0;
 }
 
@@ -941,6 +942,14 @@ static void free_motion(const ora_sim *s, const solid_t *b, const double Inow[6]
   for (int a = 0; a < 3; a++) {
     double dv = b->F[a] + (b->rho_p - 1.0) * RHO0 * V * b->g[a];
     double dw = b->T[a];
+    if (ibm && s->ibm_inertia == ORA_INERTIA_UHLMANN) {
+      /* Eq. 22: the inside fluid moves rigidly with the solid and its inertia
+       * is taken off the solid's: (rho_p - rho_f) V dv = F + (rho_p - rho_f) V g,
+       * I (1 - rho_f / rho_p) dw = T */
+      Un[a] = b->U[a] + dv / ((b->rho_p - 1.0) * RHO0 * V);
+      On[a] = b->Om[a] + dw / (I * (1.0 - 1.0 / b->rho_p));
+      continue;
+    }
     if (ibm && s->ibm_inertia == ORA_INERTIA_KEMPE) {
       /* Eq. 21 with Eq. 24: rho_f times the change of the inside fluid's
        * momentum (angular momentum) over the last step */

@@ -129,10 +129,12 @@ int ora_set_domain(ora_sim *s, const int face[6], const double *u_face);
 /* epsilon = 2 nu s_ij s_ij from the strain rate of ora_strain_rate [N] */
 void ora_dissipation(ora_sim *s, double *eps);
 /* Inertia of the fluid inside a free solid under IBM (Sec. 4.1): the
- * rigid-body form of Feng & Michaelides (Eq. 23, default) or Kempe et al.'s
- * volume integrals with level-set cell fractions (Eqs. 24-26). */
+ * rigid-body form of Feng & Michaelides (Eq. 23, default), Kempe et al.'s
+ * volume integrals with level-set cell fractions (Eqs. 24-26), or Uhlmann's
+ * reduced inertia (Eq. 22). */
 #define ORA_INERTIA_FENG 0
 #define ORA_INERTIA_KEMPE 1
+#define ORA_INERTIA_UHLMANN 2 /* Eq. 22 (needs rho_p > rho_f) */
 void ora_set_ibm_inertia(ora_sim *s, int inertia);
 /* Eq. 25 at node (x, y, z) for solid id, and Eq. 24 for solid id at the
  * current time (momentum, then angular momentum about the centre). */

@@ -465,6 +465,7 @@ lbm_status kempe_integrals(lbm_ctx *ctx) {
 lbm_status advance_free(lbm_ctx *ctx, int slot) {
   const bool ibm = ctx->scheme.scheme == LBM_IBM_DIRECT;
   const bool kempe = ibm && ctx->scheme.ibm_inertia == LBM_INERTIA_KEMPE;
+  const bool uhlmann = ibm && ctx->scheme.ibm_inertia == LBM_INERTIA_UHLMANN;
   double rec[kMaxSolids * 6], In[kMaxSolids * 6];
   if (kempe) TRY(kempe_integrals(ctx));
   CK(cudaMemcpyAsync(rec, ctx->hist + (size_t)slot * kMaxSolids * 6, sizeof(rec),
@@ -495,6 +496,13 @@ lbm_status advance_free(lbm_ctx *ctx, int slot) {
       } else if (ibm) {
         dv += V * (h.d.velocity[a] - h.Up[a]);
         dw += I / h.rho_p * (h.d.omega[a] - h.Omp[a]);
+      }
+      if (uhlmann) {
+        // Eq. 22: the inside fluid moves rigidly with the solid and its
+        // inertia is taken off the solid's
+        Un[a] = h.d.velocity[a] + dv / ((h.rho_p - 1.0) * V);
+        On[a] = h.d.omega[a] + dw / (I * (1.0 - 1.0 / h.rho_p));
+        continue;
       }
       Un[a] = h.d.velocity[a] + dv / m;
       On[a] = h.d.omega[a] + dw / I;
@@ -1491,8 +1499,12 @@ lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme) {
     return fail(ctx, LBM_ERR_ARG, "negative IBM parameter");
   if (scheme->ibm_kernel < LBM_DELTA_PESKIN4 || scheme->ibm_kernel > LBM_DELTA_COSINE4)
     return fail(ctx, LBM_ERR_ARG, "unknown delta-function kernel");
-  if (scheme->ibm_inertia != LBM_INERTIA_FENG && scheme->ibm_inertia != LBM_INERTIA_KEMPE)
+  if (scheme->ibm_inertia < LBM_INERTIA_FENG || scheme->ibm_inertia > LBM_INERTIA_UHLMANN)
     return fail(ctx, LBM_ERR_ARG, "unknown inside-fluid treatment");
+  if (scheme->scheme == LBM_IBM_DIRECT && scheme->ibm_inertia == LBM_INERTIA_UHLMANN)
+    for (auto &h : ctx->solids)
+      if (h.rho_p > 0 && h.rho_p <= 1.0)
+        return fail(ctx, LBM_ERR_ARG, "Eq. 22 needs a solid denser than the fluid");
   if (scheme->scheme == LBM_ZHAO_YONG && !ctx->need_collide && !ctx->prev_local)
     return fail(ctx, LBM_ERR_STATE,
                 "select Eq. 16 before stepping, or after lbm_init_equilibrium / "
@@ -1777,6 +1789,9 @@ lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int id, double density_ratio,
     return fail(ctx, LBM_ERR_STATE, "free solids need a bounce-back or IBM scheme (set it first)");
   if (density_ratio > 0 && ctx->scheme.scheme == LBM_ZHAO_YONG)
     return fail(ctx, LBM_ERR_UNSUPPORTED, "Eq. 16 does not take translating solids");
+  if (density_ratio > 0 && density_ratio <= 1.0 && ctx->scheme.scheme == LBM_IBM_DIRECT &&
+      ctx->scheme.ibm_inertia == LBM_INERTIA_UHLMANN)
+    return fail(ctx, LBM_ERR_ARG, "Eq. 22 needs a solid denser than the fluid");
   SolidHost &h = ctx->solids[id];
   h.rho_p = density_ratio > 0 ? density_ratio : 0;
   h.have_Ip = false;

@@ -32,7 +32,7 @@ SPHERE, CYLINDER_Z = 0, 1
 TK_BULK, TK_LIST, TK_IBM, TK_GEOM = range(4)
 DELTA_PESKIN4, DELTA_ROMA3, DELTA_LINEAR2, DELTA_COSINE4 = range(4)
 FACE_PERIODIC, FACE_VELOCITY, FACE_FREE_SLIP, FACE_CONVECTIVE = range(4)
-INERTIA_FENG, INERTIA_KEMPE = range(2)
+INERTIA_FENG, INERTIA_KEMPE, INERTIA_UHLMANN = range(3)
 # lbm_set_timing masks: every kind, or bit (kind + 1) per kind
 TIME_ALL = 1
 TIME_BULK, TIME_LIST, TIME_IBM, TIME_GEOM = (2 << k for k in range(4))

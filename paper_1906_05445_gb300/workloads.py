@@ -23,7 +23,7 @@ SPHERE, CYLINDER_Z = 0, 1
 NONE, BB, BOUZIDI_LIN, BOUZIDI_QUAD, YU_LIN, YU_QUAD, IBM, ZHAO_YONG = range(8)
 PESKIN4, ROMA3, LINEAR2, COSINE4 = range(4)  # IBM delta-function kernels
 PERIODIC, VELOCITY, FREE_SLIP, CONVECTIVE = range(4)  # domain face types
-FENG, KEMPE = range(2)  # inertia of the fluid inside a free solid under IBM
+FENG, KEMPE, UHLMANN = range(3)  # inertia of the fluid inside a free solid under IBM
 SCHEME_NAMES = {NONE: "none", BB: "bounce_back", BOUZIDI_LIN: "bouzidi_linear",
                 BOUZIDI_QUAD: "bouzidi_quadratic", YU_LIN: "yu_linear",
                 YU_QUAD: "yu_quadratic", IBM: "ibm_direct_forcing", ZHAO_YONG: "zhao_yong"}

@@ -444,7 +444,8 @@ def _free_problem(dim, scheme):
 
 @pytest.mark.parametrize("dim", [2, 3])
 @pytest.mark.parametrize("scheme,inertia", [(W.BOUZIDI_QUAD, W.FENG), (W.YU_LIN, W.FENG),
-                                            (W.IBM, W.FENG), (W.IBM, W.KEMPE)])
+                                            (W.IBM, W.FENG), (W.IBM, W.KEMPE),
+                                            (W.IBM, W.UHLMANN)])
 def test_free_solid_fp64(dim, scheme, inertia):
     """A free solid (Eq. 20 under bounce-back, Eq. 23 under IBM), heavier
     than the fluid, moved across grid lines by its weight, the body-forced
@@ -454,8 +455,9 @@ def test_free_solid_fp64(dim, scheme, inertia):
     p = _free_problem(dim, scheme).with_(ibm_inertia=inertia)
     g, o = make_gpu(p), make_oracle(p)
     gravity = (0.0, -4e-4, 2e-4 if dim == 3 else 0.0)
-    g.set_solid_dynamics(0, 1.5, gravity)
-    o.set_solid_dynamics(0, 1.5, gravity)
+    rho = 2.5 if inertia == W.UHLMANN else 1.5  # Eq. 22 is unstable near neutral density
+    g.set_solid_dynamics(0, rho, gravity)
+    o.set_solid_dynamics(0, rho, gravity)
     f0 = random_populations(p, seed=31, amplitude=0.02)
     g.set_f(f0)
     o.set_f(f0)

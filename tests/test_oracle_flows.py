@@ -361,3 +361,34 @@ def test_kempe_and_feng_settle_alike_near_neutral_density(oracle):
         slips.append(u[1][fluid].mean() - U[1])
         assert abs(slips[-1] / (weight * K / (4 * np.pi * nu)) - 1) < 0.15
     assert abs(slips[1] / slips[0] - 1) < 1e-2
+
+
+def test_uhlmann_inertia_is_stable_only_well_above_neutral_density(oracle):
+    """Eq. 22 (the inside fluid's inertia taken off the solid's) reaches the
+    periodic-array slip velocity at rho_p / rho_f = 2, but at 1.03, the
+    settling case's ratio, it diverges where Feng & Michaelides' form stays
+    bounded: the paper leaves Eq. 22 out of Sec. 4.1 for that reason."""
+    L, R, tau, g0 = 32, 4.0, 1.0, 1e-4
+    nu = (tau - 0.5) / 3
+    c = np.pi * R * R / (L * L)
+    K = -0.5 * np.log(c) - 0.738 + c - 0.887 * c ** 2 + 2.039 * c ** 3
+
+    def run(rho_p, inertia, steps):
+        weight = (rho_p - 1) * np.pi * R * R * g0
+        s = oracle.OracleSim(0, L, L, 1, tau, 0, g=(0, weight / (L * L - np.pi * R * R), 0))
+        sid = s.add_solid(1, (16.3, 15.7, 0), R)
+        s.set_scheme(W.IBM, ibm_inertia=inertia)
+        s.set_solid_dynamics(sid, rho_p, (0, -g0, 0))
+        s.step(steps)
+        U, _ = s.solid_velocity(sid)
+        return s, sid, U, weight
+
+    s, sid, U, weight = run(2.0, W.UHLMANN, 12000)
+    u = s.velocity()[:, 0]
+    fluid = ~s.solid_mask()[0]
+    slip = u[1][fluid].mean() - U[1]
+    assert abs(slip / (weight * K / (4 * np.pi * nu)) - 1) < 0.15
+    _, _, Uf, _ = run(1.03, W.FENG, 3000)
+    _, _, Uu, _ = run(1.03, W.UHLMANN, 3000)
+    assert np.all(np.isfinite(Uf)) and abs(Uf[1]) < 1e-3
+    assert not (np.all(np.isfinite(Uu)) and abs(Uu[1]) < 1e-2)

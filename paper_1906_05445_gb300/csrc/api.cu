@@ -493,7 +493,7 @@ lbm_status advance_free(lbm_ctx *ctx, int slot) {
         }
         dv += In[6 * k + a] - h.Ip[a];
         dw += In[6 * k + 3 + a] - h.Ip[3 + a];
-      } else if (ibm) {
+      } else if (ibm && !uhlmann) {
         dv += V * (h.d.velocity[a] - h.Up[a]);
         dw += I / h.rho_p * (h.d.omega[a] - h.Omp[a]);
       }

@@ -385,7 +385,7 @@ def run_serve_leg(stream):
     reqs = W.request_stream(count=c["count"], seed=c["seed"], rate_hz=c["rate_hz"],
                             min_2d=c["min_2d"], max_2d=c["max_2d"], min_3d=c["min_3d"],
                             max_3d=c["max_3d"], tau_range=c["tau_range"])
-    a = serve.summarize(serve.serve_batched(reqs, c["tol"], c["check_every"], stream=stream))
+    a = serve.summarize(serve.serve_batched(reqs, c["tol"], c["check_every"]))
     s = serve.summarize(serve.serve_sequential(reqs, c["tol"], c["check_every"], stream=stream))
     return {"metric": "served solves/s", "value": a["solves_per_s"], "unit": "solves/s",
             "p50_s": a["p50_s"], "p99_s": a["p99_s"],

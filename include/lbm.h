@@ -399,6 +399,56 @@ lbm_status lbm_batch_run_to_steady(lbm_batch *batch, double tol,
 lbm_status lbm_batch_info(lbm_batch *batch, int i, int *bulk_block,
                           int *list_block, int64_t *graph_launches);
 const char *lbm_batch_last_error(const lbm_batch *batch);
+/* ---- serving: a stream of solves under continuous batching ----
+ * A server owns a worker thread on the device that was current at
+ * lbm_server_create.  lbm_server_submit queues a solve (a lattice, its
+ * solids and scheme, an initial equilibrium state); the worker admits
+ * queued solves in submission order while the device memory of the running
+ * lattices plus the next one's estimate (two distribution arrays, flags and
+ * solid ids, the IBM fields) stays within hbm_budget bytes (a solve that
+ * exceeds it alone runs by itself), steps the running lattices together as
+ * an lbm_batch in rounds of check_every steps, and retires each lattice when
+ * its velocity residual falls below tol (lbm_run_to_steady's measure), after
+ * max_steps steps, or on a non-finite residual.  Solves that arrive while
+ * others run join at the next round.  The contexts, streams and memory are
+ * the server's; the caller sees only request ids and results.
+ * lbm_server_submit: LBM_ERR_ARG for a bad request (checked as lbm_create,
+ * lbm_add_solid and lbm_set_scheme would); LBM_ERR_STATE after shutdown.
+ * lbm_server_poll: the result so far (status PENDING, RUNNING, DONE or
+ * FAILED, with the lbm_status of the failure in error); LBM_ERR_ARG for an
+ * unknown id.  lbm_server_wait: waits up to timeout_s seconds (< 0: without
+ * limit) for DONE or FAILED; LBM_ERR_TIMEOUT when the time runs out.
+ * lbm_server_velocity: the final velocity field [d][nodes] of a DONE
+ * request submitted with keep_velocity; LBM_ERR_STATE otherwise.
+ * lbm_server_destroy finishes the running round, drops queued solves and
+ * joins the worker.  Times are seconds since lbm_server_create. */
+enum { LBM_REQ_PENDING = 0, LBM_REQ_RUNNING = 1, LBM_REQ_DONE = 2, LBM_REQ_FAILED = 3 };
+typedef struct {
+  lbm_lattice_desc lattice;
+  int nsolids; /* 0..8 */
+  lbm_solid_desc solids[8];
+  lbm_scheme_desc scheme;
+  double rho0, u0[3]; /* initial equilibrium (rho0 <= 0: 1) */
+  int keep_velocity;  /* keep the final velocity field for lbm_server_velocity */
+} lbm_request;
+typedef struct {
+  int status;
+  int error;
+  int64_t steps;
+  double residual;
+  double force[3], torque[3]; /* solid 0, zero without solids */
+  double submit_s, start_s, finish_s;
+  int64_t device_bytes;       /* the lattice's device memory while it ran */
+} lbm_result;
+typedef struct lbm_server lbm_server;
+lbm_status lbm_server_create(lbm_server **out, size_t hbm_budget, double tol, int check_every,
+                             int max_steps);
+lbm_status lbm_server_submit(lbm_server *server, const lbm_request *request, int64_t *id);
+lbm_status lbm_server_poll(lbm_server *server, int64_t id, lbm_result *result);
+lbm_status lbm_server_wait(lbm_server *server, int64_t id, lbm_result *result, double timeout_s);
+lbm_status lbm_server_velocity(lbm_server *server, int64_t id, double *host_out, size_t n);
+void lbm_server_destroy(lbm_server *server);
+
 /* Library version string. */
 const char *lbm_version(void);
 

@@ -57,6 +57,22 @@ class lbm_scheme_desc(C.Structure):
                 ("ibm_kernel", C.c_int), ("ibm_inertia", C.c_int)]
 
 
+class lbm_request(C.Structure):
+    _fields_ = [("lattice", lbm_lattice_desc), ("nsolids", C.c_int),
+                ("solids", lbm_solid_desc * 8), ("scheme", lbm_scheme_desc),
+                ("rho0", C.c_double), ("u0", C.c_double * 3), ("keep_velocity", C.c_int)]
+
+
+class lbm_result(C.Structure):
+    _fields_ = [("status", C.c_int), ("error", C.c_int), ("steps", C.c_int64),
+                ("residual", C.c_double), ("force", C.c_double * 3), ("torque", C.c_double * 3),
+                ("submit_s", C.c_double), ("start_s", C.c_double), ("finish_s", C.c_double),
+                ("device_bytes", C.c_int64)]
+
+
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
+
+
 class lbm_domain_desc(C.Structure):
     _fields_ = [("type", C.c_int * 6), ("u", (C.c_double * 3) * 6)]
 
@@ -100,6 +116,12 @@ def _load():
         "lbm_set_solid_dynamics": (st, [vp, i, d, dp]),
         "lbm_set_domain": (st, [vp, C.POINTER(lbm_domain_desc)]),
         "lbm_step_multi": (st, [C.POINTER(vp), i, i]),
+        "lbm_server_create": (st, [C.POINTER(vp), sz, d, i, i]),
+        "lbm_server_submit": (st, [vp, C.POINTER(lbm_request), C.POINTER(C.c_int64)]),
+        "lbm_server_poll": (st, [vp, C.c_int64, C.POINTER(lbm_result)]),
+        "lbm_server_wait": (st, [vp, C.c_int64, C.POINTER(lbm_result), d]),
+        "lbm_server_velocity": (st, [vp, C.c_int64, dp, sz]),
+        "lbm_server_destroy": (None, [vp]),
         "lbm_get_solid_velocity": (st, [vp, i, dp, dp]),
         "lbm_get_residual": (st, [vp, dp]),
         "lbm_get_solid_centre": (st, [vp, i, dp]),
@@ -135,7 +157,8 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_get_velocity", "lbm_get_strain_rate", "lbm_get_stress", "lbm_get_dissipation",
     "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
     "lbm_copy_force_torque_async", "lbm_set_solid_dynamics", "lbm_get_solid_velocity",
-    "lbm_set_domain", "lbm_step_multi",
+    "lbm_set_domain", "lbm_step_multi", "lbm_server_create", "lbm_server_submit",
+    "lbm_server_poll", "lbm_server_wait", "lbm_server_velocity", "lbm_server_destroy",
     "lbm_get_residual", "lbm_get_solid_centre", "lbm_get_info",
     "lbm_device_field", "lbm_save", "lbm_load", "lbm_set_timing",
     "lbm_get_kernel_time", "lbm_get_velocity_noalloc", "lbm_sync", "lbm_last_error",
@@ -403,6 +426,95 @@ class Batch:
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             lbm_batch_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def request_of(p: W.Problem, u0=None, keep_velocity: bool = False) -> lbm_request:
+    """The lbm_request of a workload problem (periodic domain, started at the
+    equilibrium at rest or at u0)."""
+    r = lbm_request()
+    d = r.lattice
+    d.lattice, d.nx, d.ny, d.nz = p.lattice, p.nx, p.ny, p.nz
+    d.tau, d.collision, d.precision = p.tau, p.collision, p.precision
+    for k, v in enumerate(_v3(p.g)):
+        d.body_force[k] = v
+    d.force_region = 1 if p.force_all else 0
+    if len(p.solids) > 8:
+        raise ValueError("at most 8 solids")
+    r.nsolids = len(p.solids)
+    for k, b in enumerate(p.solids):
+        sd = r.solids[k]
+        sd.kind, sd.radius, sd.fluid_inside = b.kind, b.radius, int(b.fluid_inside)
+        for a, (c, u, o) in enumerate(zip(_v3(b.centre), _v3(b.velocity), _v3(b.omega))):
+            sd.centre[a], sd.velocity[a], sd.omega[a] = c, u, o
+    r.scheme = lbm_scheme_desc(p.scheme, p.ibm_iters, p.retraction, p.marker_density,
+                               p.ibm_kernel, p.ibm_inertia)
+    r.rho0 = 1.0
+    for k, v in enumerate(_v3(u0)):
+        r.u0[k] = v
+    r.keep_velocity = int(keep_velocity)
+    return r
+
+
+class Server:
+    """The library's serving engine (lbm_server_*): solves are admitted by
+    device-memory footprint and stepped together under continuous batching by
+    a worker thread of the library."""
+
+    def __init__(self, hbm_budget: int, tol: float, check_every: int = 200,
+                 max_steps: int = 200000):
+        self.h = C.c_void_p()
+        st = lbm_server_create(C.byref(self.h), int(hbm_budget), float(tol), int(check_every),
+                               int(max_steps))
+        if st != LBM_OK:
+            raise LbmError(st, "lbm_server_create failed")
+
+    def submit(self, p: W.Problem, u0=None, keep_velocity: bool = False) -> int:
+        i = C.c_int64()
+        st = lbm_server_submit(self.h, C.byref(request_of(p, u0, keep_velocity)), C.byref(i))
+        if st != LBM_OK:
+            raise LbmError(st, f"lbm_server_submit refused {p.name}")
+        return i.value
+
+    @staticmethod
+    def _dict(r: lbm_result) -> dict:
+        return {"status": r.status, "error": r.error, "steps": r.steps, "residual": r.residual,
+                "force": np.array(r.force[:]), "torque": np.array(r.torque[:]),
+                "submit_s": r.submit_s, "start_s": r.start_s, "finish_s": r.finish_s,
+                "device_bytes": r.device_bytes}
+
+    def poll(self, rid: int) -> dict:
+        r = lbm_result()
+        st = lbm_server_poll(self.h, rid, C.byref(r))
+        if st != LBM_OK:
+            raise LbmError(st, f"unknown request {rid}")
+        return self._dict(r)
+
+    def wait(self, rid: int, timeout: float = -1.0) -> dict:
+        r = lbm_result()
+        st = lbm_server_wait(self.h, rid, C.byref(r), float(timeout))
+        if st != LBM_OK:
+            raise LbmError(st, f"request {rid}")
+        return self._dict(r)
+
+    def velocity(self, rid: int, p: W.Problem) -> np.ndarray:
+        d = 2 if p.lattice == D2Q9 else 3
+        shape = (p.nz if p.lattice == D3Q19 else 1, p.ny, p.nx)
+        out = np.zeros((d,) + shape)
+        st = lbm_server_velocity(self.h, rid, _dp(out), out.size)
+        if st != LBM_OK:
+            raise LbmError(st, f"no velocity kept for request {rid}")
+        return out
+
+    def close(self):
+        if getattr(self, "h", None) is not None and self.h.value:
+            lbm_server_destroy(self.h)
             self.h = None
 
     def __del__(self):

@@ -1,7 +1,8 @@
 """Serving loop for a stream of lattice Boltzmann solves.
 
 Requests (a :class:`workloads.Problem` and an arrival time) are served by
-continuous batching over the CUDA library's batch engine:
+continuous batching in the CUDA library's serving engine (lbm_server_*, a
+worker thread of the library over its batch engine):
 
 * admission by HBM footprint: a request enters as soon as it has arrived and
   the device memory of the lattices on the GPU plus its own stays under the
@@ -64,59 +65,30 @@ def _finish(lt: lbm.Lattice, keep_field: bool):
 
 def serve_batched(requests: Sequence[Tuple[float, W.Problem]], tol: float,
                   check_every: int = 200, max_steps: int = 200000,
-                  hbm_budget: int = 64 << 30, keep_fields: bool = False,
-                  stream: Optional[int] = None) -> List[Result]:
+                  hbm_budget: int = 64 << 30, keep_fields: bool = False) -> List[Result]:
+    """Submit each request to the library's server (lbm_server_*) at its
+    arrival time and collect the results; admission, batching and retirement
+    run in the library's worker thread."""
     reqs = sorted(requests, key=lambda r: r[0])
-    pending = list(range(len(reqs)))
-    active: List[dict] = []
-    done: List[Result] = []
-    used = 0
-    batch = None
+    srv = lbm.Server(hbm_budget, tol, check_every, max_steps)
     t0 = time.perf_counter()
-    while pending or active:
-        now = time.perf_counter() - t0
-        changed = False
-        while pending and reqs[pending[0]][0] <= now:
-            k = pending[0]
-            need = footprint_bytes(reqs[k][1])
-            if active and used + need > hbm_budget:
-                break
-            arrival, p = reqs[k]
-            lt = lbm.Lattice.from_problem(p, stream=stream)
-            lt.init_equilibrium()
-            active.append(dict(k=k, lat=lt, need=need, start=now, steps=0))
-            used += need
-            pending.pop(0)
-            changed = True
-        if not active:
-            time.sleep(max(0.0, reqs[pending[0]][0] - (time.perf_counter() - t0)))
-            continue
-        if changed or batch is None:
-            if batch is not None:
-                batch.close()
-            batch = lbm.Batch([a["lat"] for a in active], stream=stream, autotune=False)
-        steps, res = batch.run_to_steady(tol, check_every, check_every)
-        keep = []
-        for a, s, r in zip(active, steps, res):
-            a["steps"] += int(s)
-            if r < tol or a["steps"] >= max_steps or not np.isfinite(r):
-                F, u = _finish(a["lat"], keep_fields)
-                arrival, p = reqs[a["k"]]
-                done.append(Result(p.name, arrival, a["start"], time.perf_counter() - t0,
-                                   a["steps"], float(r), F, u))
-                used -= a["need"]
-                a["retire"] = True
-            else:
-                keep.append(a)
-        if len(keep) != len(active):
-            batch.close()
-            batch = None
-            for a in active:
-                if a.get("retire"):
-                    a["lat"].close()
-            active = keep
-    if batch is not None:
-        batch.close()
+    try:
+        ids = []
+        for arrival, p in reqs:
+            now = time.perf_counter() - t0
+            if now < arrival:
+                time.sleep(arrival - now)
+            ids.append((arrival, p, srv.submit(p, keep_velocity=keep_fields)))
+        done: List[Result] = []
+        for arrival, p, rid in ids:
+            r = srv.wait(rid)
+            if r["status"] != lbm.REQ_DONE:
+                raise lbm.LbmError(r["error"], f"served solve {p.name} failed")
+            u = srv.velocity(rid, p) if keep_fields else None
+            done.append(Result(p.name, arrival, r["start_s"], r["finish_s"], int(r["steps"]),
+                               float(r["residual"]), r["force"], u))
+    finally:
+        srv.close()
     return done
 
 

@@ -121,3 +121,45 @@ def test_batch_member_changed_between_steps(lbm):
     for p, ua, ub in zip(ps, *runs):
         tol = 1e-13 if p.scheme == W.IBM else 0.0
         assert rel_l2(ub, ua) <= tol, p.name
+
+
+def test_server_admission_limits_and_errors(lbm):
+    """The library's server: with a memory budget below one lattice the
+    solves run one after another and still equal the solves alone; bad
+    requests, unknown ids, missing fields and a wait that runs out report
+    the statuses the header states; destroying a server with queued work
+    returns."""
+    ps = [W.couette_2d(32, 5.0, 14.0, (16.3, 15.8), 0.01, 0.8, W.BOUZIDI_LIN, 0, W.FP32),
+          W.fixed_sphere(20, 3.3, seed=4, tau=0.9, g=1e-6, scheme=W.IBM, precision=W.FP32)]
+    # a budget smaller than any lattice: each solve runs alone, as a solve
+    # larger than the budget does
+    srv = lbm.Server(1, 1e-5, 100, 20000)
+    ids = [srv.submit(p, keep_velocity=True) for p in ps]
+    res = [srv.wait(i) for i in ids]
+    for p, i, r in zip(ps, ids, res):
+        assert r["status"] == lbm.REQ_DONE
+        lt = lbm.Lattice.from_problem(p)
+        lt.init_equilibrium()
+        steps, resid = lt.run_to_steady(1e-5, 100, 20000)
+        assert r["steps"] == steps
+        assert rel_l2(srv.velocity(i, p), lt.velocity()) <= 1e-5
+        lt.close()
+    # one lattice at a time: the second started after the first finished
+    assert res[1]["start_s"] >= res[0]["finish_s"]
+    bad = ps[0].with_(tau=0.4)
+    with pytest.raises(lbm.LbmError, match="ARG"):
+        srv.submit(bad)
+    with pytest.raises(lbm.LbmError, match="ARG"):
+        srv.poll(10 ** 9)
+    i = srv.submit(ps[0])
+    assert srv.wait(i)["status"] == lbm.REQ_DONE
+    with pytest.raises(lbm.LbmError, match="STATE"):
+        srv.velocity(i, ps[0])  # submitted without keep_velocity
+    big = W.fixed_sphere(96, 9.0, seed=1, tau=0.6, g=1e-7, scheme=W.BOUZIDI_QUAD,
+                         precision=W.FP32)
+    j = srv.submit(big)
+    with pytest.raises(lbm.LbmError, match="TIMEOUT"):
+        srv.wait(j, timeout=0.0)
+    for _ in range(3):
+        srv.submit(big)
+    srv.close()

@@ -46,17 +46,6 @@ class Result:
         return self.finish - self.arrival
 
 
-def footprint_bytes(p: W.Problem) -> int:
-    """Device bytes of one lattice: two distribution arrays, flags, solid ids
-    and, for IBM, the two dense vector fields, rounded up by 10 %."""
-    ssz = {W.FP64: 8, W.FP32: 4, W.FP32_BF16: 2, W.FP32_FP16: 2}[p.precision]
-    tsz = 8 if p.precision == W.FP64 else 4
-    b = 2 * p.Q * p.nodes * ssz + 3 * p.nodes
-    if p.scheme == W.IBM:
-        b += 6 * p.nodes * tsz
-    return int(b * 1.1) + (1 << 20)
-
-
 def _finish(lt: lbm.Lattice, keep_field: bool):
     F, _ = lt.force_torque(0) if lt.info().num_solids else (np.zeros(3), None)
     u = lt.velocity() if keep_field else None

@@ -108,3 +108,21 @@ def test_all_cores_oracle_baseline():
     r = bench.oracle_sample_all_cores(ps, procs=2)
     assert r["cores"] == 2 and r["kind"] == "oracle" and r["value"] > 0
     assert "2 processes" in r["sample"]
+
+
+def test_request_of_carries_the_problem():
+    """The lbm_request a workload problem becomes (served solves): lattice,
+    solids, scheme and initial state field by field."""
+    from paper_1906_05445_gb300 import lbm
+    from paper_1906_05445_gb300 import workloads as W
+    p = W.fixed_sphere(40, 6.3, seed=5, tau=0.65, g=2e-6, scheme=W.IBM, precision=W.FP32,
+                       retraction=0.3).with_(ibm_kernel=W.ROMA3, ibm_inertia=W.KEMPE)
+    r = lbm.request_of(p, u0=(0.01, 0, 0), keep_velocity=True)
+    d = r.lattice
+    assert (d.lattice, d.nx, d.ny, d.nz, d.precision) == (p.lattice, 40, 40, 40, W.FP32)
+    assert d.tau == p.tau and d.body_force[0] == p.g[0]
+    assert r.nsolids == 1 and r.solids[0].radius == 6.3
+    assert tuple(r.solids[0].centre) == tuple(p.solids[0].centre)
+    assert (r.scheme.scheme, r.scheme.ibm_kernel, r.scheme.ibm_inertia) == (W.IBM, W.ROMA3, W.KEMPE)
+    assert r.scheme.ibm_retraction == 0.3
+    assert r.u0[0] == 0.01 and r.rho0 == 1.0 and r.keep_velocity == 1

@@ -476,7 +476,8 @@ def run_ours(args, rank, world, local):
         hf = torch.empty((p.Q, p.nodes), dtype=torch.float64, pin_memory=True)
         hf.numpy()[:] = wq[:, None]
         pinned_f.append(hf)
-    hu = [torch.empty((3, p.nodes), dtype=torch.float64, pin_memory=True) for p in problems]
+    hu = [torch.empty((3 if p.lattice == W.D3Q19 else 2, p.nodes), dtype=torch.float64,
+                      pin_memory=True) for p in problems]
     # every step's force and torque of every lattice, copied to page-locked
     # host memory as the steps complete (no wait per step)
     hF = torch.empty((e2e_steps, len(lats), 6), dtype=torch.float64, pin_memory=True)
@@ -491,7 +492,7 @@ def run_ours(args, rank, world, local):
             lt.step(1)
             lt.copy_force_torque_async(hFn[k, i])
     for lt, u in zip(lats, hu):
-        u.numpy()[:] = lt.velocity().reshape(3, -1)
+        lt.velocity(out=u.numpy())  # straight into page-locked memory
     for lt in lats:
         lt.sync()
     e2e_secs = reduce_max(time.perf_counter() - t0, world, device)

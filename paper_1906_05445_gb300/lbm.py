@@ -278,16 +278,21 @@ class Lattice:
                                       C.byref(done), C.byref(r)))
         return done.value, r.value
 
-    def _field(self, fn, comps):
-        out = np.zeros((comps, self.N))
+    def _field(self, fn, comps, out=None):
+        """The field into a new array, or into `out` (C-contiguous float64 of
+        comps * nodes values, e.g. page-locked memory for a faster copy)."""
+        if out is None:
+            out = np.zeros((comps, self.N))
+        elif out.dtype != np.float64 or not out.flags.c_contiguous or out.size < comps * self.N:
+            raise ValueError(f"out must be C-contiguous float64 with {comps * self.N} values")
         self._check(fn(self.h, _dp(out), out.size))
         return out.reshape((comps,) + self.shape)
 
     def density(self):
         return self._field(lbm_get_density, 1)[0]
 
-    def velocity(self):
-        return self._field(lbm_get_velocity, self.d)
+    def velocity(self, out=None):
+        return self._field(lbm_get_velocity, self.d, out)
 
     def strain_rate(self):
         return self._field(lbm_get_strain_rate, 3 if self.d == 2 else 6)

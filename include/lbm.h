@@ -48,7 +48,7 @@ typedef enum {
   LBM_ERR_CUDA = -3,        /* CUDA runtime error (message in last_error) */
   LBM_ERR_UNSUPPORTED = -4, /* valid but not implemented combination */
   LBM_ERR_STATE = -5,       /* call not valid in the current state */
-  LBM_ERR_TIMEOUT = -6,     /* reserved: no kernel waits on a device flag */
+  LBM_ERR_TIMEOUT = -6,     /* a host-side wait ran out (lbm_server_wait); no kernel waits on a device flag */
   LBM_ERR_DIVERGED = -7,    /* non-finite residual */
   LBM_ERR_CAPACITY = -8     /* a fixed-capacity device list overflowed */
 } lbm_status;

@@ -122,3 +122,31 @@ def test_invalid_domains_are_refused(oracle):
     s2 = oracle.OracleSim(W.D2Q9, 8, 8, 1, 0.7, W.BGK)
     with pytest.raises(ValueError):
         s2.set_domain([P, P, P, P, V, V])     # z faces on a 2D lattice
+
+
+def test_outflow_passes_an_advected_shear_pulse(oracle):
+    """A transverse velocity pulse carried by the stream through the outflow
+    face leaves without reflection: while it crosses the face, the field of
+    the 200-node channel matches that of a 600-node channel (whose outflow it
+    has not reached) to 1% of the pulse amplitude.  A velocity face imposing
+    the stream there instead reflects it: about 30%."""
+    U, tau, v0, x0, wd = 0.05, 0.8, 0.01, 150.0, 8.0
+    e, w = oracle.lattice(W.D2Q9)
+
+    def run(nx, out_face, steps=1000):
+        s = oracle.OracleSim(W.D2Q9, nx, 3, 1, tau, W.MRT)
+        s.set_domain([V, out_face, P, P, P, P], faces_u(x_lo=(U, 0, 0), x_hi=(U, 0, 0)))
+        x = np.arange(nx)[None, :] * np.ones((3, 1))
+        ux, uy = U * np.ones_like(x), v0 * np.exp(-((x - x0) / wd) ** 2)
+        f = np.zeros((9, 1, 3, nx))
+        for i in range(9):
+            eu = e[i, 0] * ux + e[i, 1] * uy
+            f[i, 0] = w[i] * (1 + 3 * eu + 4.5 * eu ** 2 - 1.5 * (ux ** 2 + uy ** 2))
+        s.set_f(f)
+        s.step(steps)
+        return s.velocity()[:, 0, 1, :]
+
+    ref = run(600, CV)[:, :200]
+    assert np.abs(ref[1]).max() > 0.3 * v0  # the pulse is at the face
+    assert np.abs(run(200, CV)[1] - ref[1]).max() < 0.01 * v0
+    assert np.abs(run(200, V)[1] - ref[1]).max() > 0.2 * v0

@@ -417,12 +417,21 @@ const char *lbm_batch_last_error(const lbm_batch *batch);
  * lbm_server_poll: the result so far (status PENDING, RUNNING, DONE or
  * FAILED, with the lbm_status of the failure in error); LBM_ERR_ARG for an
  * unknown id.  lbm_server_wait: waits up to timeout_s seconds (< 0: without
- * limit) for DONE or FAILED; LBM_ERR_TIMEOUT when the time runs out.
+ * limit) for DONE, FAILED or CANCELLED; LBM_ERR_TIMEOUT when the time runs
+ * out.
  * lbm_server_velocity: the final velocity field [d][nodes] of a DONE
- * request submitted with keep_velocity; LBM_ERR_STATE otherwise.
+ * request submitted with keep_velocity; LBM_ERR_STATE otherwise.  A request
+ * with a deadline that is still queued or running when it passes fails with
+ * error LBM_ERR_TIMEOUT (checked at admission and at each round's end).
  * lbm_server_destroy finishes the running round, drops queued solves and
  * joins the worker.  Times are seconds since lbm_server_create. */
-enum { LBM_REQ_PENDING = 0, LBM_REQ_RUNNING = 1, LBM_REQ_DONE = 2, LBM_REQ_FAILED = 3 };
+enum {
+  LBM_REQ_PENDING = 0,
+  LBM_REQ_RUNNING = 1,
+  LBM_REQ_DONE = 2,
+  LBM_REQ_FAILED = 3,   /* error: the lbm_status (LBM_ERR_TIMEOUT past the deadline) */
+  LBM_REQ_CANCELLED = 4
+};
 typedef struct {
   lbm_lattice_desc lattice;
   int nsolids; /* 0..8 */
@@ -430,6 +439,7 @@ typedef struct {
   lbm_scheme_desc scheme;
   double rho0, u0[3]; /* initial equilibrium (rho0 <= 0: 1) */
   int keep_velocity;  /* keep the final velocity field for lbm_server_velocity */
+  double deadline_s;  /* > 0: seconds after submission by which the solve must be done */
 } lbm_request;
 typedef struct {
   int status;
@@ -447,7 +457,17 @@ lbm_status lbm_server_submit(lbm_server *server, const lbm_request *request, int
 lbm_status lbm_server_poll(lbm_server *server, int64_t id, lbm_result *result);
 lbm_status lbm_server_wait(lbm_server *server, int64_t id, lbm_result *result, double timeout_s);
 lbm_status lbm_server_velocity(lbm_server *server, int64_t id, double *host_out, size_t n);
+/* Cancels a request: a queued one at once, a running one at the end of the
+ * current round (its lattice is freed then).  LBM_ERR_ARG for an unknown id;
+ * LBM_ERR_STATE if it has already finished. */
+lbm_status lbm_server_cancel(lbm_server *server, int64_t id);
 void lbm_server_destroy(lbm_server *server);
+
+/* Fault injection for tests: after n more device allocations (any context,
+ * any thread) every allocation fails with LBM_ERR_OOM until the hook is reset
+ * with n < 0.  The failing call leaves its context usable or destroyed as
+ * its own error contract states; no device memory is touched. */
+void lbm_debug_fail_allocations_after(long long n);
 
 /* Library version string. */
 const char *lbm_version(void);

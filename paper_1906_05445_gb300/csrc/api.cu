@@ -14,6 +14,7 @@
 #include <string.h>
 
 #include <algorithm>
+#include <atomic>
 #include <mutex>
 #include <string>
 #include <vector>
@@ -223,9 +224,18 @@ lbm_status cuda_check(lbm_ctx *c, cudaError_t e, const char *what) {
     if (_s != LBM_OK) return _s;                              \
   } while (0)
 
+// allocation fault injection (lbm_debug_fail_allocations_after): the
+// number of device allocations still allowed, or -1 for no limit
+std::atomic<long long> g_alloc_budget{-1};
+
 lbm_status dalloc(lbm_ctx *ctx, void **p, size_t bytes) {
   *p = nullptr;
   if (bytes == 0) return LBM_OK;
+  if (g_alloc_budget.load() >= 0 && g_alloc_budget.fetch_sub(1) <= 0) {
+    g_alloc_budget.store(0);
+    return fail(ctx, LBM_ERR_OOM, "cudaMalloc of " + std::to_string(bytes) +
+                                      " bytes refused by the allocation fault hook");
+  }
   cudaError_t e = cudaMalloc(p, bytes);
   if (e != cudaSuccess) {
     *p = nullptr;
@@ -559,6 +569,9 @@ lbm_status ensure_list_capacity(lbm_ctx *ctx, int list_cap, int link_cap, int re
     ctx->list_cst = nullptr;
     ctx->refill_node = nullptr;
     ctx->refill_sid = nullptr;
+    // no capacity until every array exists (a failed allocation leaves the
+    // kernels nothing to index)
+    ctx->list_cap = ctx->refill_cap = 0;
     const int lc = std::max(list_cap, 1), rc = std::max(refill_cap, 1);
     TRY(dalloc(ctx, (void **)&ctx->list_node, sizeof(int) * lc));
     TRY(dalloc(ctx, (void **)&ctx->list_mask, sizeof(uint32_t) * lc));
@@ -576,6 +589,7 @@ lbm_status ensure_list_capacity(lbm_ctx *ctx, int list_cap, int link_cap, int re
     ctx->link_mem = nullptr;
     ctx->link_list = nullptr;
     ctx->link_dir = nullptr;
+    ctx->link_cap = 0;
     const size_t lk = std::max(link_cap, 1);
     TRY(dalloc(ctx, (void **)&ctx->link_list, sizeof(int) * lk));
     TRY(dalloc(ctx, (void **)&ctx->link_dir, lk));
@@ -795,8 +809,10 @@ lbm_status build_markers(lbm_ctx *ctx) {
   ctx->nmark = n;
   if (!ctx->u_band) {
     TRY(dalloc(ctx, &ctx->u_band, 3 * ctx->tsz * ctx->N));
-    TRY(dalloc(ctx, &ctx->f_ibm, 3 * ctx->tsz * ctx->N));
     CK(cudaMemsetAsync(ctx->u_band, 0, 3 * ctx->tsz * ctx->N, ctx->st));
+  }
+  if (!ctx->f_ibm) {
+    TRY(dalloc(ctx, &ctx->f_ibm, 3 * ctx->tsz * ctx->N));
     CK(cudaMemsetAsync(ctx->f_ibm, 0, 3 * ctx->tsz * ctx->N, ctx->st));
   }
   return LBM_OK;
@@ -1200,6 +1216,7 @@ lbm_status qbuf_ensure(lbm_ctx *ctx, size_t elems) {
   if (elems <= ctx->qbuf_elems) return LBM_OK;
   dfree(ctx, ctx->qbuf);
   ctx->qbuf = nullptr;
+  ctx->qbuf_elems = 0;
   TRY(dalloc(ctx, (void **)&ctx->qbuf, elems * sizeof(double)));
   ctx->qbuf_elems = elems;
   return LBM_OK;
@@ -1301,6 +1318,8 @@ void set_collision_constants(lbm_ctx *ctx) {
 
 // ===================================================================== ABI
 extern "C" {
+
+void lbm_debug_fail_allocations_after(long long n) { g_alloc_budget.store(n < 0 ? -1 : n); }
 
 const char *lbm_version(void) { return "lbm-gb300 0.1 (sm_103a)"; }
 
@@ -1610,10 +1629,9 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, int check_every, int max_
                              int *steps_done, double *residual) {
   if (!ctx || check_every < 1 || max_steps < 0) return LBM_ERR_ARG;
   TRY(prepare(ctx));
-  if (!ctx->u_now) {
-    TRY(dalloc(ctx, (void **)&ctx->u_now, sizeof(double) * ctx->D * ctx->N));
-    TRY(dalloc(ctx, (void **)&ctx->u_snap, sizeof(double) * ctx->D * ctx->N));
-  }
+  // each buffer on its own: a failed allocation leaves no half-made pair
+  if (!ctx->u_now) TRY(dalloc(ctx, (void **)&ctx->u_now, sizeof(double) * ctx->D * ctx->N));
+  if (!ctx->u_snap) TRY(dalloc(ctx, (void **)&ctx->u_snap, sizeof(double) * ctx->D * ctx->N));
   TRY(velocity_to(ctx, ctx->u_snap));
   int done = 0;
   double r = INFINITY;
@@ -1761,6 +1779,9 @@ lbm_status lbm_set_domain(lbm_ctx *ctx, const lbm_domain_desc *dom) {
   ctx->nface = 0;
   ctx->out_face = -1;
   ctx->out_area = 0;
+  // periodic until the new faces' arrays exist
+  ctx->dom = lbm_domain_desc{};
+  ctx->geom_dirty = true;
   if (!nodes.empty()) {
     TRY(dalloc(ctx, (void **)&ctx->face_node, nodes.size() * sizeof(int)));
     CK(cudaMemcpy(ctx->face_node, nodes.data(), nodes.size() * sizeof(int), cudaMemcpyHostToDevice));
@@ -2447,10 +2468,10 @@ lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int check_every, in
   const int n = (int)b->ctx.size();
   for (int i = 0; i < n; i++) {
     lbm_ctx *c = b->ctx[i];
-    if (!c->u_now) {
+    {
       lbm_ctx *ctx = c;
-      TRY(dalloc(ctx, (void **)&c->u_now, sizeof(double) * c->D * c->N));
-      TRY(dalloc(ctx, (void **)&c->u_snap, sizeof(double) * c->D * c->N));
+      if (!c->u_now) TRY(dalloc(ctx, (void **)&c->u_now, sizeof(double) * c->D * c->N));
+      if (!c->u_snap) TRY(dalloc(ctx, (void **)&c->u_snap, sizeof(double) * c->D * c->N));
     }
     b->active[i] = 1;
     b->steps_done[i] = 0;

@@ -32,6 +32,7 @@ struct lbm_server {
     lbm_request r;
     lbm_result res;
     std::vector<double> vel;
+    bool cancel = false;
   };
   std::unordered_map<int64_t, Req> reqs;
   std::deque<int64_t> queue;
@@ -173,6 +174,15 @@ void run(lbm_server *s) {
         if (s->queue.empty()) break;
         id = s->queue.front();
         r = s->reqs[id].r;
+        if (r.deadline_s > 0 && now_s(s) > s->reqs[id].res.submit_s + r.deadline_s) {
+          // expired while queued
+          s->queue.pop_front();
+          s->reqs[id].res.status = LBM_REQ_FAILED;
+          s->reqs[id].res.error = LBM_ERR_TIMEOUT;
+          s->reqs[id].res.finish_s = now_s(s);
+          s->cv_done.notify_all();
+          continue;
+        }
         if (!act.empty() && used + estimate_bytes(r) > s->budget) break;
         s->queue.pop_front();
         s->reqs[id].res.status = LBM_REQ_RUNNING;
@@ -221,12 +231,27 @@ void run(lbm_server *s) {
       continue;
     }
     bool any = false;
+    std::vector<int> why(act.size(), LBM_REQ_DONE);
+    std::vector<int> err(act.size(), LBM_OK);
     for (size_t i = 0; i < act.size(); i++) {
       Active &a = act[i];
       a.steps += steps[i];
       if (res[i] < s->tol || a.steps >= s->max_steps || !std::isfinite(res[i])) {
         a.retire = true;
         any = true;
+      }
+      std::lock_guard<std::mutex> lk(s->mu);
+      const lbm_server::Req &q = s->reqs[a.id];
+      if (q.cancel) {
+        a.retire = true;
+        any = true;
+        why[i] = LBM_REQ_CANCELLED;
+      } else if (!(res[i] < s->tol) && q.r.deadline_s > 0 &&
+                 now_s(s) > q.res.submit_s + q.r.deadline_s) {
+        a.retire = true;
+        any = true;
+        why[i] = LBM_REQ_FAILED;
+        err[i] = LBM_ERR_TIMEOUT;
       }
     }
     if (any) {
@@ -237,7 +262,7 @@ void run(lbm_server *s) {
       for (size_t i = 0; i < act.size(); i++) {
         if (act[i].retire) {
           used -= act[i].bytes;
-          finish(s, act[i], res[i], LBM_REQ_DONE, LBM_OK);
+          finish(s, act[i], res[i], why[i], err[i]);
         } else {
           keep.push_back(act[i]);
         }
@@ -321,7 +346,7 @@ lbm_status lbm_server_wait(lbm_server *s, int64_t id, lbm_result *result, double
   if (it == s->reqs.end()) return LBM_ERR_ARG;
   auto done = [&] {
     const int st = s->reqs[id].res.status;
-    return st == LBM_REQ_DONE || st == LBM_REQ_FAILED;
+    return st == LBM_REQ_DONE || st == LBM_REQ_FAILED || st == LBM_REQ_CANCELLED;
   };
   if (timeout_s < 0) {
     s->cv_done.wait(lk, done);
@@ -342,6 +367,28 @@ lbm_status lbm_server_velocity(lbm_server *s, int64_t id, double *host_out, size
   if (q.res.status != LBM_REQ_DONE || q.vel.empty()) return LBM_ERR_STATE;
   if (n < q.vel.size()) return LBM_ERR_ARG;
   memcpy(host_out, q.vel.data(), q.vel.size() * sizeof(double));
+  return LBM_OK;
+}
+
+lbm_status lbm_server_cancel(lbm_server *s, int64_t id) {
+  if (!s) return LBM_ERR_ARG;
+  std::lock_guard<std::mutex> lk(s->mu);
+  auto it = s->reqs.find(id);
+  if (it == s->reqs.end()) return LBM_ERR_ARG;
+  lbm_server::Req &q = it->second;
+  if (q.res.status == LBM_REQ_PENDING) {
+    for (auto qi = s->queue.begin(); qi != s->queue.end(); ++qi)
+      if (*qi == id) {
+        s->queue.erase(qi);
+        break;
+      }
+    q.res.status = LBM_REQ_CANCELLED;
+    q.res.finish_s = now_s(s);
+    s->cv_done.notify_all();
+    return LBM_OK;
+  }
+  if (q.res.status != LBM_REQ_RUNNING) return LBM_ERR_STATE;
+  q.cancel = true;  // retired at the end of the round
   return LBM_OK;
 }
 

@@ -60,7 +60,8 @@ class lbm_scheme_desc(C.Structure):
 class lbm_request(C.Structure):
     _fields_ = [("lattice", lbm_lattice_desc), ("nsolids", C.c_int),
                 ("solids", lbm_solid_desc * 8), ("scheme", lbm_scheme_desc),
-                ("rho0", C.c_double), ("u0", C.c_double * 3), ("keep_velocity", C.c_int)]
+                ("rho0", C.c_double), ("u0", C.c_double * 3), ("keep_velocity", C.c_int),
+                ("deadline_s", C.c_double)]
 
 
 class lbm_result(C.Structure):
@@ -70,7 +71,7 @@ class lbm_result(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
-REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED = range(4)
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
 
 
 class lbm_domain_desc(C.Structure):
@@ -122,6 +123,8 @@ def _load():
         "lbm_server_wait": (st, [vp, C.c_int64, C.POINTER(lbm_result), d]),
         "lbm_server_velocity": (st, [vp, C.c_int64, dp, sz]),
         "lbm_server_destroy": (None, [vp]),
+        "lbm_server_cancel": (st, [vp, C.c_int64]),
+        "lbm_debug_fail_allocations_after": (None, [C.c_longlong]),
         "lbm_get_solid_velocity": (st, [vp, i, dp, dp]),
         "lbm_get_residual": (st, [vp, dp]),
         "lbm_get_solid_centre": (st, [vp, i, dp]),
@@ -159,6 +162,7 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_copy_force_torque_async", "lbm_set_solid_dynamics", "lbm_get_solid_velocity",
     "lbm_set_domain", "lbm_step_multi", "lbm_server_create", "lbm_server_submit",
     "lbm_server_poll", "lbm_server_wait", "lbm_server_velocity", "lbm_server_destroy",
+    "lbm_server_cancel", "lbm_debug_fail_allocations_after",
     "lbm_get_residual", "lbm_get_solid_centre", "lbm_get_info",
     "lbm_device_field", "lbm_save", "lbm_load", "lbm_set_timing",
     "lbm_get_kernel_time", "lbm_get_velocity_noalloc", "lbm_sync", "lbm_last_error",
@@ -440,7 +444,8 @@ class Batch:
             pass
 
 
-def request_of(p: W.Problem, u0=None, keep_velocity: bool = False) -> lbm_request:
+def request_of(p: W.Problem, u0=None, keep_velocity: bool = False,
+               deadline: float = 0.0) -> lbm_request:
     """The lbm_request of a workload problem (periodic domain, started at the
     equilibrium at rest or at u0)."""
     r = lbm_request()
@@ -464,6 +469,7 @@ def request_of(p: W.Problem, u0=None, keep_velocity: bool = False) -> lbm_reques
     for k, v in enumerate(_v3(u0)):
         r.u0[k] = v
     r.keep_velocity = int(keep_velocity)
+    r.deadline_s = float(deadline)
     return r
 
 
@@ -480,9 +486,11 @@ class Server:
         if st != LBM_OK:
             raise LbmError(st, "lbm_server_create failed")
 
-    def submit(self, p: W.Problem, u0=None, keep_velocity: bool = False) -> int:
+    def submit(self, p: W.Problem, u0=None, keep_velocity: bool = False,
+               deadline: float = 0.0) -> int:
         i = C.c_int64()
-        st = lbm_server_submit(self.h, C.byref(request_of(p, u0, keep_velocity)), C.byref(i))
+        st = lbm_server_submit(self.h, C.byref(request_of(p, u0, keep_velocity, deadline)),
+                               C.byref(i))
         if st != LBM_OK:
             raise LbmError(st, f"lbm_server_submit refused {p.name}")
         return i.value
@@ -517,6 +525,11 @@ class Server:
             raise LbmError(st, f"no velocity kept for request {rid}")
         return out
 
+    def cancel(self, rid: int):
+        st = lbm_server_cancel(self.h, rid)
+        if st != LBM_OK:
+            raise LbmError(st, f"request {rid} cannot be cancelled")
+
     def close(self):
         if getattr(self, "h", None) is not None and self.h.value:
             lbm_server_destroy(self.h)
@@ -527,3 +540,9 @@ class Server:
             self.close()
         except Exception:
             pass
+
+
+def debug_fail_allocations_after(n: int):
+    """Fault injection: the next n device allocations succeed, later ones fail
+    with LBM_ERR_OOM; n < 0 turns the hook off."""
+    lbm_debug_fail_allocations_after(int(n))

@@ -1491,9 +1491,7 @@ lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int id, const double centre[3], co
   if (ctx) ctx->gen++;
   if (!ctx || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
   SolidHost &h = ctx->solids[id];
-  bool moved = false;
   for (int a = 0; a < 3; a++) {
-    if (centre && centre[a] != h.c[a]) moved = true;
     if (centre) h.c[a] = h.d.centre[a] = centre[a];
     if (vel) h.d.velocity[a] = vel[a];
     if (omega) h.d.omega[a] = omega[a];

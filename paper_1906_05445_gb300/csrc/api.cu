@@ -1502,7 +1502,6 @@ lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int id, const double centre[3], co
     h.d.omega[0] = h.d.omega[1] = 0;
   }
   // wall velocities are stored with the links: rebuild
-  (void)moved;
   ctx->geom_dirty = true;
   return LBM_OK;
 }

@@ -47,9 +47,12 @@ def test_library_exports_every_declared_symbol(lbm):
 def test_struct_layout_matches_header(lbm, tmp_path):
     prog = tmp_path / "sizes.c"
     prog.write_text('#include <stdio.h>\n#include <stddef.h>\n#include "lbm.h"\n'
-                    'int main(void){printf("%zu %zu %zu %zu %zu %zu\\n", sizeof(lbm_lattice_desc),'
+                    'int main(void){printf("%zu %zu %zu %zu %zu %zu %zu %zu %zu %zu %zu\\n",'
+                    ' sizeof(lbm_lattice_desc),'
                     ' sizeof(lbm_solid_desc), sizeof(lbm_scheme_desc), sizeof(lbm_info),'
-                    ' offsetof(lbm_lattice_desc, body_force), offsetof(lbm_solid_desc, fluid_inside));'
+                    ' offsetof(lbm_lattice_desc, body_force), offsetof(lbm_solid_desc, fluid_inside),'
+                    ' sizeof(lbm_domain_desc), sizeof(lbm_request), sizeof(lbm_result),'
+                    ' offsetof(lbm_request, deadline_s), offsetof(lbm_result, device_bytes));'
                     'return 0;}\n')
     exe = tmp_path / "sizes"
     subprocess.run(["gcc", "-I", os.path.join(ROOT, "include"), str(prog), "-o", str(exe)], check=True)
@@ -57,7 +60,9 @@ def test_struct_layout_matches_header(lbm, tmp_path):
                                        check=True).stdout.split()))
     want = [C.sizeof(lbm.lbm_lattice_desc), C.sizeof(lbm.lbm_solid_desc),
             C.sizeof(lbm.lbm_scheme_desc), C.sizeof(lbm.lbm_info),
-            lbm.lbm_lattice_desc.body_force.offset, lbm.lbm_solid_desc.fluid_inside.offset]
+            lbm.lbm_lattice_desc.body_force.offset, lbm.lbm_solid_desc.fluid_inside.offset,
+            C.sizeof(lbm.lbm_domain_desc), C.sizeof(lbm.lbm_request), C.sizeof(lbm.lbm_result),
+            lbm.lbm_request.deadline_s.offset, lbm.lbm_result.device_bytes.offset]
     assert got == want
 
 
@@ -89,3 +94,25 @@ def test_invalid_descriptors_rejected_before_device_work(lbm):
     assert lbm.lbm_create(C.byref(h), C.byref(d), None) == -1
     d.lattice, d.nx = 1, 0
     assert lbm.lbm_create(C.byref(h), C.byref(d), None) == -1
+
+
+def test_header_is_plain_c(tmp_path):
+    """include/lbm.h compiles as strict C99 (no C++ or compiler extensions in
+    the ABI), so a C caller can use it as it is."""
+    import shutil
+    import subprocess
+    gcc = shutil.which("gcc")
+    if gcc is None:
+        pytest.skip("no C compiler")
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    src = tmp_path / "use.c"
+    src.write_text('#include "include/lbm.h"\n'
+                   "int main(void) {\n"
+                   "  lbm_lattice_desc d; lbm_request r; lbm_result s; lbm_domain_desc f;\n"
+                   "  (void)d; (void)r; (void)s; (void)f;\n"
+                   "  return 0;\n"
+                   "}\n")
+    r = subprocess.run([gcc, "-std=c99", "-Wall", "-Wextra", "-pedantic", "-Werror",
+                        "-I", root, "-c", str(src), "-o", str(tmp_path / "use.o")],
+                       capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr

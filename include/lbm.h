@@ -318,7 +318,12 @@ lbm_status lbm_device_field(lbm_ctx *ctx, int which, void **dptr,
                             size_t *bytes, size_t *dir_stride);
 
 /* Checkpoint: the full state (distributions, flags of the current geometry,
- * solids, step count).  With host_buf == NULL *size receives the size. */
+ * solids with their motion and free-body state, scheme, step count) into a
+ * caller-owned host buffer.  With host_buf == NULL *size receives the size.
+ * The lattice description and the domain faces are not in it: lbm_load
+ * takes a context created with the same lattice (LBM_ERR_ARG otherwise) and
+ * keeps that context's faces.  LBM_ERR_UNSUPPORTED under LBM_ZHAO_YONG or
+ * with an outflow face (their kept boundary state is not saved). */
 lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size);
 lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size);
 

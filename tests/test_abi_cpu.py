@@ -94,6 +94,13 @@ def test_invalid_descriptors_rejected_before_device_work(lbm):
     assert lbm.lbm_create(C.byref(h), C.byref(d), None) == -1
     d.lattice, d.nx = 1, 0
     assert lbm.lbm_create(C.byref(h), C.byref(d), None) == -1
+    # more nodes than a 32-bit node index holds: refused before any device call
+    d.nx, d.ny, d.nz = 2048, 2048, 1024
+    assert lbm.lbm_create(C.byref(h), C.byref(d), None) == -4   # LBM_ERR_UNSUPPORTED
+    d.nx, d.ny, d.nz, d.precision = 8, 8, 8, 9                # unknown precision
+    assert lbm.lbm_create(C.byref(h), C.byref(d), None) == -1
+    d.precision, d.collision = 1, 5                            # unknown collision
+    assert lbm.lbm_create(C.byref(h), C.byref(d), None) == -1
 
 
 def test_header_is_plain_c(tmp_path):

@@ -1329,6 +1329,27 @@ void ora_dissipation(ora_sim *s, double *eps) {
   free(S);
 }
 
+/* Stress (Sec. 3.1): sigma = -c_s^2 rho I + 2 rho0 nu S, the pressure of
+ * the lattice equation of state p = c_s^2 rho plus the Newtonian viscous
+ * stress of the strain rate above, nu = (tau - 1/2) c_s^2.  Same component
+ * order as ora_strain_rate; 0 at nodes that are not simulated. */
+void ora_stress(ora_sim *s, double *sig) {
+  const int d = s->d, nc = d == 2 ? 3 : 6;
+  double *S = (double *)malloc(sizeof(double) * (size_t)nc * s->N);
+  double *rho = (double *)malloc(sizeof(double) * (size_t)s->N);
+  ora_strain_rate(s, S);
+  ora_density(s, rho);
+  const double nu = (s->tau - 0.5) * CS2;
+  for (long n = 0; n < s->N; n++)
+    for (int c = 0; c < nc; c++) {
+      double v = 0;
+      if (simulated(s, n)) v = (c < d ? -CS2 * rho[n] : 0.0) + 2 * RHO0 * nu * S[c * s->N + n];
+      sig[c * s->N + n] = v;
+    }
+  free(S);
+  free(rho);
+}
+
 void ora_solid_mask(ora_sim *s, unsigned char *m) {
   for (long n = 0; n < s->N; n++) m[n] = simulated(s, n) ? 0 : 1;
 }

@@ -128,6 +128,8 @@ void ora_set_solid_dynamics(ora_sim *s, int id, double rho_ratio, const double g
 int ora_set_domain(ora_sim *s, const int face[6], const double *u_face);
 /* epsilon = 2 nu s_ij s_ij from the strain rate of ora_strain_rate [N] */
 void ora_dissipation(ora_sim *s, double *eps);
+/* sigma = -c_s^2 rho I + 2 rho0 nu S (Sec. 3.1), order of ora_strain_rate */
+void ora_stress(ora_sim *s, double *sig /*[d(d+1)/2][N]*/);
 /* Inertia of the fluid inside a free solid under IBM (Sec. 4.1): the
  * rigid-body form of Feng & Michaelides (Eq. 23, default), Kempe et al.'s
  * volume integrals with level-set cell fractions (Eqs. 24-26), or Uhlmann's

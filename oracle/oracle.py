@@ -67,6 +67,7 @@ def lib():
                 "ora_solid_velocity": (None, [vp, i, dp, dp]),
                 "ora_set_domain": (i, [vp, C.POINTER(C.c_int), dp]),
                 "ora_dissipation": (None, [vp, dp]),
+                "ora_stress": (None, [vp, dp]),
                 "ora_create": (vp, [i, i, i, i, d, i, dp, dp, i]),
                 "ora_destroy": (None, [vp]),
                 "ora_add_solid": (i, [vp, i, dp, d, dp, dp, i]),
@@ -272,6 +273,12 @@ class OracleSim:
         nc = 3 if self.d == 2 else 6
         S = np.zeros((nc, self.N))
         self.L.ora_strain_rate(self.h, _p(S))
+        return S.reshape((nc,) + self.shape)
+
+    def stress(self):
+        nc = 3 if self.d == 2 else 6
+        S = np.zeros((nc, self.N))
+        self.L.ora_stress(self.h, _p(S))
         return S.reshape((nc,) + self.shape)
 
     def solid_mask(self):

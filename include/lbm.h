@@ -64,6 +64,20 @@ enum {
   LBM_FP32_BF16STORE = 2, /* BF16 storage of f - w_i, FP32 arithmetic */
   LBM_FP32_FP16STORE = 3  /* FP16 storage of scaled f - w_i, FP32 arithmetic */
 };
+/* Accuracy of the 16-bit storage paths.  A storage precision is accepted
+ * for a flow only where its drag error against the FP64 result stays below
+ * 10% of the discretisation error at that resolution (Richardson estimate
+ * from twice the resolution).  Measured:
+ *  - fixed sphere, R = 3.75 in a 40^3 periodic box, tau = 0.6, g = 3.4e-8
+ *    (flow speed ~1e-4), 2000 steps: FP16 meets it under IBM (0.05-0.8%) but
+ *    not under quadratic Bouzidi (24%); BF16 meets it under neither (IBM
+ *    3-19% from run to run, Bouzidi 366%);
+ *  - sphere translating at U = 0.01 (R = 8, 20000 steps): FP16 meets it
+ *    under both schemes (4.8% / 0.46%); BF16 under IBM only (9.7%), not
+ *    under Bouzidi with refilling (216%).
+ * BF16 storage with any bounce-back scheme therefore does not meet the rule
+ * in any flow measured; use FP32 or FP16 storage there.  The library does
+ * not refuse the combination: it is a fast, less accurate option. */
 /* where the external body force acts */
 enum { LBM_FORCE_FLUID_ONLY = 0, LBM_FORCE_ALL = 1 };
 /* solid shapes */
@@ -131,7 +145,7 @@ enum {
   LBM_DELTA_COSINE4 = 3  /* 4-point cosine kernel (Appendix B) */
 };
 
-/* inertia of the fluid inside a free solid under IBM (Sec. 4.1) */
+/* inertia of the fluid inside a free solid under IBM (Sec. 3.2) */
 enum {
   LBM_INERTIA_FENG = 0, /* rigid-body inside fluid, Feng & Michaelides, Eq. 23 (default) */
   LBM_INERTIA_KEMPE = 1, /* Kempe et al.: volume integrals over level-set cell fractions,
@@ -188,7 +202,7 @@ lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int solid_id,
                                 const double omega[3]);
 lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme);
 
-/* Domain faces (Sec. 6, the uniform flow past a sphere in an open box).
+/* Domain faces (Sec. 3.4, the uniform flow past a sphere in an open box).
  * type[k] for the faces x-, x+, y-, y+, z-, z+; u[k] the velocity of a
  * LBM_FACE_VELOCITY face.  A non-periodic face lies half a spacing outside
  * the outermost nodes:

@@ -966,7 +966,7 @@ static void free_motion(const ora_sim *s, const solid_t *b, const double Inow[6]
   if (s->d == 2 || b->kind == ORA_CYLINDER_Z) On[0] = On[1] = 0;
 }
 
-/* ---- domain faces (Sec. 6: uniform flow past a sphere) ----
+/* ---- domain faces (Sec. 3.4: uniform flow past a sphere) ----
  * A non-periodic face lies half a spacing outside the outermost nodes.  A
  * pull from (x, y, z) along e_i that leaves the domain crosses one face, or
  * two at an edge; bit 2a marks the low face of axis a, bit 2a + 1 the high

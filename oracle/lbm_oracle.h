@@ -116,7 +116,7 @@ void ora_link_stats(const ora_sim *s, long counts[8]);
  * motion) and gravity; the solid's velocities then follow Eq. 20
  * (bounce-back) or Eq. 23 (IBM) every step */
 void ora_set_solid_dynamics(ora_sim *s, int id, double rho_ratio, const double g[3]);
-/* Domain faces x-, x+, y-, y+, z-, z+ (Sec. 6): periodic pairs, plane walls
+/* Domain faces x-, x+, y-, y+, z-, z+ (Sec. 3.4): periodic pairs, plane walls
  * moving with u_face[3k..3k+2] (velocity inlet or no-slip wall), stress-free
  * (specular) faces, and at most one convective outflow face.  Returns 0, or
  * -1 for an unpaired periodic face, a z face on a 2D lattice or a second
@@ -130,7 +130,7 @@ int ora_set_domain(ora_sim *s, const int face[6], const double *u_face);
 void ora_dissipation(ora_sim *s, double *eps);
 /* sigma = -c_s^2 rho I + 2 rho0 nu S (Sec. 3.1), order of ora_strain_rate */
 void ora_stress(ora_sim *s, double *sig /*[d(d+1)/2][N]*/);
-/* Inertia of the fluid inside a free solid under IBM (Sec. 4.1): the
+/* Inertia of the fluid inside a free solid under IBM (Sec. 3.2): the
  * rigid-body form of Feng & Michaelides (Eq. 23, default), Kempe et al.'s
  * volume integrals with level-set cell fractions (Eqs. 24-26), or Uhlmann's
  * reduced inertia (Eq. 22). */

@@ -651,7 +651,7 @@ __global__ void __launch_bounds__(128) k_zy_seed(const KArgs a) {
 }
 
 // ---------------------------------------------------------------- domain
-// faces (the open box of the uniform flow past a sphere, Sec. 6).  A
+// faces (the open box of the uniform flow past a sphere, Sec. 3.4).  A
 // non-periodic face lies half a spacing outside the outermost nodes; the
 // nodes next to one (flag FL_FACE) run in k_face, a thread per node, which
 // pulls like the bulk sweep except on links that leave the domain:

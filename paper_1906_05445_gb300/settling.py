@@ -1,4 +1,4 @@
-"""A cylinder settling in a closed vertical channel (Sec. 4.1), run on the GPU
+"""A cylinder settling in a closed vertical channel (Sec. 3.2), run on the GPU
 for each no-slip treatment and grid resolution:
 
 * physical parameters of the paper: D = 0.1 cm, channel width H = 0.4 cm,

@@ -1,4 +1,4 @@
-"""Drag of a fixed sphere in a uniform stream (Sec. 6) against the grid
+"""Drag of a fixed sphere in a uniform stream (Sec. 3.4) against the grid
 resolution, run on the GPU for each no-slip treatment:
 
 * the open box of the paper: 24D x 12D x 12D, the sphere at (6D, 6D, 6D)

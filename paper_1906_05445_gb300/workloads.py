@@ -157,7 +157,7 @@ def open_sphere(D: float = 8.0, re: float = 20.0, nu: float = 0.02, seed: int = 
                 scheme: int = BOUZIDI_QUAD, precision: int = FP64, collision: int = MRT,
                 steps: int = 4000, length=(24, 12, 12), centre=(6, 6, 6),
                 ibm_iters: int = 1, retraction: float = 0.0) -> Problem:
-    """Uniform flow past a fixed sphere in an open box (Sec. 6): a box of
+    """Uniform flow past a fixed sphere in an open box (Sec. 3.4): a box of
     length x (24D, 12D, 12D), the sphere of diameter D at (6D, 6D, 6D) plus a
     sub-node offset drawn from the seed, a velocity inlet U = Re nu / D at
     x = 0, stress-free sides and a convective outflow at x = Lx (the caller

@@ -70,3 +70,22 @@ def compare(gpu, ora, tol_u, tol_F=None, sids=(0,), what=("u",), F_abs=1e-13,
             out[f"T{sid}"] = np.linalg.norm(Tg - To) / tscale
             assert np.linalg.norm(Fg - Fo) <= tol_F * scale + F_abs, out
     return out
+
+
+def run_series(sim, steps: int, every: int):
+    """Step `sim` (a GPU lattice or an oracle simulation: the same method
+    names) for `steps` steps, recording the force on solid 0 every `every`
+    steps; returns (final velocity, [steps // every][3] forces)."""
+    F = []
+    for _ in range(steps // every):
+        sim.step(every)
+        F.append(np.array(sim.force_torque(0)[0]))
+    return sim.velocity(), np.array(F)
+
+
+def oracle_series(p: W.Problem, every: int):
+    """The oracle's run_series of problem p from rest (a picklable entry
+    point for a process pool started with 'spawn')."""
+    o = make_oracle(p)
+    u, F = run_series(o, p.steps, every)
+    return u, F, o.solid_mask()

@@ -1,5 +1,5 @@
 """GPU parity of the domain faces (velocity walls and inlets, stress-free
-faces, the convective outflow of the open-box sphere flow of Sec. 6) against
+faces, the convective outflow of the open-box sphere flow of Sec. 3.4) against
 the FP64 oracle, and the limits the header states."""
 import numpy as np
 import pytest
@@ -159,7 +159,7 @@ def test_batch_of_open_boxes_matches_single():
                                             (W.IBM, W.FENG), (W.IBM, W.KEMPE)])
 def test_free_cylinder_next_to_a_wall_fp64(scheme, inertia):
     """A free cylinder 1.6 spacings from a resting wall (the start of the
-    settling case of Sec. 4.1): the bounce-back rules lose their stencil
+    settling case of Sec. 3.2): the bounce-back rules lose their stencil
     nodes beyond the wall and fall back, IBM band nodes next to the wall run
     in the face kernel; fields, forces and motion follow the oracle."""
     uf = np.zeros((6, 3))

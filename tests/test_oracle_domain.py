@@ -1,5 +1,5 @@
 """Pins of the oracle's domain faces (the open box of the uniform flow past a
-sphere, Sec. 6): velocity faces (a plane wall moving with a given velocity,
+sphere, Sec. 3.4): velocity faces (a plane wall moving with a given velocity,
 as inlet or no-slip wall), stress-free faces (specular reflection) and the
 convective outflow face.  Each pin is a closed form or a symmetry that a
 plausible slip in the rules (a wrong sign of the moving-wall term, a

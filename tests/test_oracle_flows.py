@@ -341,7 +341,7 @@ def test_kempe_angular_momentum_of_rigid_rotation(oracle):
 
 def test_kempe_and_feng_settle_alike_near_neutral_density(oracle):
     """At rho_p / rho_f = 1.03 (the density ratio of the settling cylinder of
-    Sec. 4.1) both treatments of the inside fluid stay stable, reach the
+    Sec. 3.2) both treatments of the inside fluid stay stable, reach the
     periodic-array slip velocity within 15% and agree within 1%."""
     L, R, tau, rho_p, g0 = 32, 4.0, 1.0, 1.03, 1e-4
     nu = (tau - 0.5) / 3
@@ -367,7 +367,7 @@ def test_uhlmann_inertia_is_stable_only_well_above_neutral_density(oracle):
     """Eq. 22 (the inside fluid's inertia taken off the solid's) reaches the
     periodic-array slip velocity at rho_p / rho_f = 2, but at 1.03, the
     settling case's ratio, it diverges where Feng & Michaelides' form stays
-    bounded: the paper leaves Eq. 22 out of Sec. 4.1 for that reason."""
+    bounded: the paper leaves Eq. 22 out of Sec. 3.2 for that reason."""
     L, R, tau, g0 = 32, 4.0, 1.0, 1e-4
     nu = (tau - 0.5) / 3
     c = np.pi * R * R / (L * L)

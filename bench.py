@@ -171,6 +171,29 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def pinned_bandwidth(device, nbytes=1 << 29):
+    """Copy bandwidth between page-locked host memory and the device (GB/s),
+    best of 3 CUDA-event-timed copies of `nbytes` each way."""
+    import torch
+    h = torch.empty(nbytes // 8, dtype=torch.float64, pin_memory=True)
+    d = torch.empty(nbytes // 8, dtype=torch.float64, device=device)
+    out = {}
+    for name, fn in (("h2d", lambda: d.copy_(h, non_blocking=True)),
+                     ("d2h", lambda: h.copy_(d, non_blocking=True))):
+        best = float("inf")
+        for _ in range(3):
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record()
+            fn()
+            b.record()
+            torch.cuda.synchronize(device)
+            best = min(best, a.elapsed_time(b) / 1e3)
+        out[name] = nbytes / best / 1e9
+    del h, d
+    return out
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -265,7 +288,7 @@ def oracle_sample_all_cores(problems, procs=None):
 
 
 REFERENCE_BUDGET_S = 150.0
-TIMING_EVERY = 10
+ROOFLINE_STEPS = 200
 PRECISIONS = {"fp32": W.FP32, "bf16": W.FP32_BF16, "fp16": W.FP32_FP16, "fp64": W.FP64}
 
 
@@ -414,12 +437,10 @@ def run_ours(args, rank, world, local):
     for _ in range(args.warmup):
         for lt in lats:
             lt.step(1)
-    # the timed region times the bulk sweeps (the roofline's kernel) with
-    # CUDA events on their stream, on every TIMING_EVERY-th step (each pair of
-    # event records costs the step a few microseconds); the other kinds get
-    # their own short pass
-    for lt in lats:
-        lt.set_timing(lbm.TIME_BULK, every=TIMING_EVERY)
+    # the timed region carries no kernel timing; the roofline's kernel (the
+    # bulk sweep) is timed with CUDA events on its stream in a pass of its
+    # own below, every launch (each pair of event records costs the step a
+    # few microseconds, not the kernel)
     launches0 = sum(lt.info().kernel_launches for lt in lats)
     sampler = ClockSampler(local)
     sampler.start()
@@ -442,7 +463,14 @@ def run_ours(args, rank, world, local):
     units = sum(p.nodes for p in problems) * args.steps
     value = aggregate(units, max_secs, world)
 
-    # dominant kernel: the bulk sweep of the bounce-back lattice
+    # dominant kernel: the bulk sweep of the bounce-back lattice, every
+    # launch of a pass of ROOFLINE_STEPS steps of the same two-lattice loop
+    for lt in lats:
+        lt.set_timing(lbm.TIME_BULK, every=1)
+    for _ in range(ROOFLINE_STEPS):
+        for lt in lats:
+            lt.step(1)
+    torch.cuda.synchronize(device)
     ms, nl, nodes = lats[0].kernel_time(lbm.TK_BULK)
     bpn = BYTES_PER_NODE[precision]
     per_launch_bytes = nodes / max(nl, 1) * bpn
@@ -450,7 +478,7 @@ def run_ours(args, rank, world, local):
     peaks, peak_kind = measured_peaks()
     peak = float(peaks["hbm_gbs"])
     # per-kind breakdown over a shorter pass with every kind timed
-    kt_steps = max(min(args.steps // 5, 500), 1)
+    kt_steps = ROOFLINE_STEPS
     for lt in lats:
         lt.set_timing(lbm.TIME_ALL)
     for _ in range(kt_steps):
@@ -466,45 +494,66 @@ def run_ours(args, rank, world, local):
     traffic = recorded_traffic() if precision == W.FP32 and args.workload == "fixed" else None
 
     # end to end through the C ABI with host buffers: upload the initial
-    # populations of both lattices from pinned memory, step, read the force
-    # and torque of every step, read the velocity field at the end
-    e2e_steps = max(args.steps // 2, 10)
-    # initial populations: the rest state f = w_i, written on the host
+    # populations of both lattices from pinned memory, step, copy every
+    # step's force and torque to pinned memory, read the velocity field at
+    # the end.  One untimed pass first (the velocity query's staging buffer
+    # is allocated on its first use), then the timed pass.
+    e2e_steps = args.steps
     wq = np.array([1 / 3] + [1 / 18] * 6 + [1 / 36] * 12)
     pinned_f = []
     for p in problems:
         hf = torch.empty((p.Q, p.nodes), dtype=torch.float64, pin_memory=True)
-        hf.numpy()[:] = wq[:, None]
+        hf.numpy()[:] = wq[:, None]      # the rest state f = w_i, written on the host
         pinned_f.append(hf)
     hu = [torch.empty((3 if p.lattice == W.D3Q19 else 2, p.nodes), dtype=torch.float64,
                       pin_memory=True) for p in problems]
-    # every step's force and torque of every lattice, copied to page-locked
-    # host memory as the steps complete (no wait per step)
     hF = torch.empty((e2e_steps, len(lats), 6), dtype=torch.float64, pin_memory=True)
     hFn = hF.numpy()
+    evs = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+
+    def e2e_pass():
+        evs[0].record(stream)
+        for lt, hf in zip(lats, pinned_f):
+            lt.set_f_async(hf.numpy())
+        evs[1].record(stream)
+        for k in range(e2e_steps):
+            for i, lt in enumerate(lats):
+                lt.step(1)
+                lt.copy_force_torque_async(hFn[k, i])
+        evs[2].record(stream)
+        for lt, u in zip(lats, hu):
+            lt.velocity(out=u.numpy())  # straight into page-locked memory
+        evs[3].record(stream)
+        for lt in lats:
+            lt.sync()
+
+    e2e_pass()
     torch.cuda.synchronize(device)
     barrier(world)
     t0 = time.perf_counter()
-    for lt, hf in zip(lats, pinned_f):
-        lt.set_f(hf.numpy())
-    for k in range(e2e_steps):
-        for i, lt in enumerate(lats):
-            lt.step(1)
-            lt.copy_force_torque_async(hFn[k, i])
-    for lt, u in zip(lats, hu):
-        lt.velocity(out=u.numpy())  # straight into page-locked memory
-    for lt in lats:
-        lt.sync()
-    e2e_secs = reduce_max(time.perf_counter() - t0, world, device)
+    e2e_pass()
+    e2e_wall = time.perf_counter() - t0
+    e2e_secs = reduce_max(e2e_wall, world, device)
     e2e_units = sum(p.nodes for p in problems) * e2e_steps
-    h2d = sum(hf.numel() * 8 for hf in pinned_f) / e2e_steps
-    d2h = (48 * len(lats) * e2e_steps + sum(u.numel() * 8 for u in hu)) / e2e_steps
+    up_bytes = sum(hf.numel() * 8 for hf in pinned_f)
+    rd_bytes = sum(u.numel() * 8 for u in hu)
+    h2d = up_bytes / e2e_steps
+    d2h = (48 * len(lats) * e2e_steps + rd_bytes) / e2e_steps
+    up_ms, st_ms, rd_ms = (evs[0].elapsed_time(evs[1]), evs[1].elapsed_time(evs[2]),
+                           evs[2].elapsed_time(evs[3]))
+    bw = pinned_bandwidth(device)
     e2e = {"value": aggregate(e2e_units, e2e_secs, world), "unit": UNIT,
            "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
            "steps": e2e_steps,
-           "path": "lbm_set_distributions (pinned FP64 host) + lbm_step(1) and "
-                   "lbm_copy_force_torque_async (pinned host) per step per lattice + "
-                   "lbm_get_velocity at the end"}
+           "breakdown_ms": {"upload": round(up_ms, 4), "steps": round(st_ms, 4),
+                            "readback": round(rd_ms, 4), "wall": round(e2e_wall * 1e3, 4)},
+           "upload_gbs": up_bytes / (up_ms / 1e3) / 1e9,
+           "readback_gbs": rd_bytes / (rd_ms / 1e3) / 1e9,
+           "pinned_copy_gbs": bw,
+           "path": "lbm_set_distributions_async (pinned FP64 host, chunked through the "
+                   "library's staging ring) + lbm_step(1) and lbm_copy_force_torque_async "
+                   "(pinned host) per step per lattice + lbm_get_velocity into pinned host "
+                   "memory; one untimed pass before the timed one"}
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -533,7 +582,9 @@ def run_ours(args, rank, world, local):
                              "kernel": "k_bulk_vec<D3Q19,MRT-q,storage,2 words>",
                              "bytes_per_node": bpn, "nodes_per_launch": nodes / max(nl, 1),
                              "launch_ms": ms / max(nl, 1), "timed_launches": int(nl),
-                             "timed_sample": f"bulk sweep of every {TIMING_EVERY}th timed step",
+                             "timed_sample": f"every bulk sweep of the bounce-back lattice in a "
+                                             f"{ROOFLINE_STEPS}-step pass of the same loop after "
+                                             f"the timed region",
                              "peak_kind": peak_kind + " hbm_gbs"},
                 "kernel_ms_per_step": kt,
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,

@@ -243,8 +243,18 @@ lbm_status lbm_set_domain(lbm_ctx *ctx, const lbm_domain_desc *domain);
 lbm_status lbm_init_equilibrium(lbm_ctx *ctx, double rho, const double u[3]);
 /* Set / read the pre-collision distributions f(x, t) (full f, not f - w):
  * host array of n = Q * nodes doubles, [Q][z][y][x].  Values at solid nodes
- * are ignored on input and returned as 0. */
+ * are ignored on input and returned as 0.  The upload needs no device
+ * allocation: it is copied in chunks of up to 2^20 doubles through staging
+ * space inside the distribution array that the next step overwrites, and
+ * converted on the device to the storage type while the next chunk is
+ * copied.  lbm_set_distributions returns when the upload is complete. */
 lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *host_f, size_t n);
+/* The same upload without waiting: it is ordered on the context's stream
+ * (later steps and queries see it).  host_f must stay valid and unchanged
+ * until a synchronising call (lbm_sync, a query) returns; page-locked memory
+ * (e.g. cudaHostAlloc) makes the copies asynchronous.  CUDA errors are
+ * reported by the next synchronising call. */
+lbm_status lbm_set_distributions_async(lbm_ctx *ctx, const double *host_f, size_t n);
 lbm_status lbm_get_distributions(lbm_ctx *ctx, double *host_f, size_t n);
 
 /* Advance nsteps time steps (asynchronous).  One step: geometry of moving
@@ -361,8 +371,10 @@ lbm_status lbm_get_kernel_time(lbm_ctx *ctx, int kernel, double *total_ms,
  * its own pool allocator, or a time-critical loop where a cudaMalloc would
  * synchronise the device.  lbm_get_velocity allocates its FP64 staging
  * buffer the first time it is called; this variant stages the field through
- * a fixed array compiled into the library instead: 2^20 doubles (8 MiB),
- * held on every GPU that loads the library until the process exits.
+ * a fixed array compiled into the library instead: 2^20 doubles (8 MiB).
+ * The array is committed on a GPU by the first lbm_create on it (which also
+ * looks up its device address, with that device current) and is held until
+ * the process exits; the query itself then needs no set-up.
  *  - Output: as lbm_get_velocity, [d][z][y][x] FP64 into host_out (n >= d *
  *    nodes); 0 at solid nodes.
  *  - d * nodes above 2^20 is rejected with LBM_ERR_CAPACITY.
@@ -370,8 +382,6 @@ lbm_status lbm_get_kernel_time(lbm_ctx *ctx, int kernel, double *total_ms,
  *    would allocate): call lbm_step or lbm_sync after add_solid / set_scheme
  *    / set_solid_motion, otherwise LBM_ERR_STATE.  The context's device must
  *    be current (LBM_ERR_STATE otherwise).
- *  - The first call on a device looks up the array's device address once
- *    (cudaGetSymbolAddress); make that first call before any stream capture.
  *  - All calls, from every context, share the one array and it keeps the
  *    previous call's contents (the call clears the part it uses).  Calls
  *    whose work overlaps on the GPU (contexts on different streams, or
@@ -424,22 +434,28 @@ const char *lbm_batch_last_error(const lbm_batch *batch);
  * solids and scheme, an initial equilibrium state); the worker admits
  * queued solves in submission order while the device memory of the running
  * lattices plus the next one's estimate (two distribution arrays, flags and
- * solid ids, the IBM fields) stays within hbm_budget bytes (a solve that
- * exceeds it alone runs by itself), steps the running lattices together as
- * an lbm_batch in rounds of check_every steps, and retires each lattice when
- * its velocity residual falls below tol (lbm_run_to_steady's measure), after
- * max_steps steps, or on a non-finite residual.  Solves that arrive while
- * others run join at the next round.  The contexts, streams and memory are
- * the server's; the caller sees only request ids and results.
+ * solid ids, the IBM fields, the two FP64 velocity snapshots of the residual
+ * and, with keep_velocity, the FP64 staging of the final velocity query)
+ * stays within hbm_budget bytes (a solve that exceeds it alone runs by
+ * itself).  A running lattice is counted at its memory after creation plus
+ * the buffers it allocates later (the snapshots and the staging).  The
+ * worker steps the running lattices together as an lbm_batch in rounds of
+ * check_every steps and retires each lattice when its velocity residual
+ * falls below tol (lbm_run_to_steady's measure: DONE), after max_steps steps
+ * without that (UNCONVERGED, with the results at max_steps), or on a
+ * non-finite residual (FAILED with LBM_ERR_DIVERGED; the other lattices of
+ * the round go on unaffected).  Solves that arrive while others run join at
+ * the next round.  The contexts, streams and memory are the server's; the
+ * caller sees only request ids and results.
  * lbm_server_submit: LBM_ERR_ARG for a bad request (checked as lbm_create,
  * lbm_add_solid and lbm_set_scheme would); LBM_ERR_STATE after shutdown.
- * lbm_server_poll: the result so far (status PENDING, RUNNING, DONE or
- * FAILED, with the lbm_status of the failure in error); LBM_ERR_ARG for an
- * unknown id.  lbm_server_wait: waits up to timeout_s seconds (< 0: without
- * limit) for DONE, FAILED or CANCELLED; LBM_ERR_TIMEOUT when the time runs
- * out.
- * lbm_server_velocity: the final velocity field [d][nodes] of a DONE
- * request submitted with keep_velocity; LBM_ERR_STATE otherwise.  A request
+ * lbm_server_poll: the result so far (status PENDING, RUNNING, DONE,
+ * UNCONVERGED or FAILED, with the lbm_status of the failure in error);
+ * LBM_ERR_ARG for an unknown id.  lbm_server_wait: waits up to timeout_s
+ * seconds (< 0: without limit) for DONE, UNCONVERGED, FAILED or CANCELLED;
+ * LBM_ERR_TIMEOUT when the time runs out.
+ * lbm_server_velocity: the final velocity field [d][nodes] of a DONE or
+ * UNCONVERGED request submitted with keep_velocity; LBM_ERR_STATE otherwise.  A request
  * with a deadline that is still queued or running when it passes fails with
  * error LBM_ERR_TIMEOUT (checked at admission and at each round's end).
  * lbm_server_destroy finishes the running round, drops queued solves and
@@ -448,8 +464,10 @@ enum {
   LBM_REQ_PENDING = 0,
   LBM_REQ_RUNNING = 1,
   LBM_REQ_DONE = 2,
-  LBM_REQ_FAILED = 3,   /* error: the lbm_status (LBM_ERR_TIMEOUT past the deadline) */
-  LBM_REQ_CANCELLED = 4
+  LBM_REQ_FAILED = 3,   /* error: the lbm_status (LBM_ERR_TIMEOUT past the deadline,
+                           LBM_ERR_DIVERGED on a non-finite residual) */
+  LBM_REQ_CANCELLED = 4,
+  LBM_REQ_UNCONVERGED = 5 /* max_steps reached with the residual still >= tol */
 };
 typedef struct {
   lbm_lattice_desc lattice;
@@ -467,7 +485,8 @@ typedef struct {
   double residual;
   double force[3], torque[3]; /* solid 0, zero without solids */
   double submit_s, start_s, finish_s;
-  int64_t device_bytes;       /* the lattice's device memory while it ran */
+  int64_t device_bytes;       /* device memory counted for the lattice while it ran (or,
+                                 if larger, what it held at the end) */
 } lbm_result;
 typedef struct lbm_server lbm_server;
 lbm_status lbm_server_create(lbm_server **out, size_t hbm_budget, double tol, int check_every,

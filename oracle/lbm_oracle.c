@@ -1378,6 +1378,7 @@ double ora_residual(ora_sim *s) {
       den += u[a * s->N + n] * u[a * s->N + n];
     }
   free(u);
+  if (!isfinite(num) || !isfinite(den)) return NAN; /* a diverged field has no residual */
   return den > 0 ? sqrt(num / den) : 0;
 }
 

@@ -106,6 +106,10 @@ struct lbm_ctx {
   cudaStream_t cst = nullptr;
   cudaEvent_t ev_rec = nullptr, ev_cst = nullptr;
   long long copies = 0;
+  // uploads (lbm_set_distributions): copies of staging slot k on `cst`,
+  // conversions on `st`, each slot reused only after its last conversion
+  cudaEvent_t ev_up_start = nullptr, ev_up_copy[2] = {nullptr, nullptr},
+              ev_up_conv[2] = {nullptr, nullptr};
   int device = 0;
   size_t ssz = 0;  // storage element size
   size_t tsz = 0;  // compute element size
@@ -1212,6 +1216,26 @@ lbm_status step_bulk_group(lbm_ctx *const *ctxs, const std::vector<int> &idx,
   return LBM_OK;
 }
 
+// ||u - u_snap||_2 / ||u||_2 from the two reduced sums; NaN when either sum
+// is not finite (a diverged field must not read as converged), 0 for a
+// field at rest.
+double residual_of(const double h[2]) {
+  if (!std::isfinite(h[0]) || !std::isfinite(h[1])) return NAN;
+  return h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+}
+
+// The copy stream and its events (asynchronous force copies, uploads).
+lbm_status ensure_copy_stream(lbm_ctx *ctx) {
+  if (ctx->cst) return LBM_OK;
+  cudaStream_t s = nullptr;
+  CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+  ctx->cst = s;
+  for (cudaEvent_t *e : {&ctx->ev_rec, &ctx->ev_cst, &ctx->ev_up_start, &ctx->ev_up_copy[0],
+                         &ctx->ev_up_copy[1], &ctx->ev_up_conv[0], &ctx->ev_up_conv[1]})
+    CK(cudaEventCreateWithFlags(e, cudaEventDisableTiming));
+  return LBM_OK;
+}
+
 lbm_status qbuf_ensure(lbm_ctx *ctx, size_t elems) {
   if (elems <= ctx->qbuf_elems) return LBM_OK;
   dfree(ctx, ctx->qbuf);
@@ -1325,6 +1349,30 @@ const char *lbm_version(void) { return "lbm-gb300 0.1 (sm_103a)"; }
 
 const char *lbm_last_error(const lbm_ctx *ctx) { return ctx ? ctx->err.c_str() : "null context"; }
 
+// ---- staging array of lbm_get_velocity_noalloc
+//
+// 2^20 doubles (8 MiB) compiled into the library, shared by all contexts and
+// all calls on a device.  Host code may not take the address of a __device__
+// variable directly: lbm_create looks it up once per device, with that
+// device current, and caches it.  The lookup also loads this file's module
+// (CUDA loads modules lazily), so the 8 MiB is committed on the device by
+// its first lbm_create, not by a later query.
+static constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
+static constexpr int kNoAllocMaxDevices = 64;
+static double *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
+static std::mutex g_noalloc_mu;
+
+static cudaError_t noalloc_lookup(int dev) {
+  if (dev < 0 || dev >= kNoAllocMaxDevices) return cudaSuccess;  // the query refuses it
+  std::lock_guard<std::mutex> lock(g_noalloc_mu);
+  if (g_noalloc_addr[dev]) return cudaSuccess;
+  void *p = nullptr;
+  const cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (e == cudaSuccess) g_noalloc_addr[dev] = (double *)p;
+  return e;
+}
+
 lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_stream) {
   if (!out || !desc) return LBM_ERR_ARG;
   *out = nullptr;
@@ -1349,6 +1397,11 @@ lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_st
   ctx->N = N;
   ctx->st = (cudaStream_t)cuda_stream;
   cudaGetDevice(&ctx->device);
+  if (noalloc_lookup(ctx->device) != cudaSuccess) {
+    cudaGetLastError();
+    delete ctx;
+    return LBM_ERR_CUDA;
+  }
   {
     int lo = 0, hi = 0;
     cudaDeviceGetStreamPriorityRange(&lo, &hi);
@@ -1455,6 +1508,9 @@ void lbm_destroy(lbm_ctx *ctx) {
   }
   if (ctx->ev_rec) cudaEventDestroy(ctx->ev_rec);
   if (ctx->ev_cst) cudaEventDestroy(ctx->ev_cst);
+  for (cudaEvent_t e : {ctx->ev_up_start, ctx->ev_up_copy[0], ctx->ev_up_copy[1],
+                        ctx->ev_up_conv[0], ctx->ev_up_conv[1]})
+    if (e) cudaEventDestroy(e);
   for (void *p : ctx->allocs) cudaFree(p);
   for (auto &p : ctx->pending) {
     cudaEventDestroy(p.a);
@@ -1553,22 +1609,73 @@ lbm_status lbm_init_equilibrium(lbm_ctx *ctx, double rho, const double u[3]) {
   return LBM_OK;
 }
 
+namespace {
+
+// Upload of full FP64 populations [Q][nodes] into the pre-collision slot
+// f[1-cur].  The other array, f[cur], holds nothing that is read again
+// before the initial collision rewrites it, so two staging slots of up to
+// 2^20 doubles are carved out of it: no device allocation.  Slot k % 2
+// takes chunk k (one direction, a run of nodes) on the copy stream; the
+// conversion to stored deviations runs on the context's stream after that
+// copy, and the copy of chunk k + 2 waits for the conversion of chunk k.
+lbm_status upload_f(lbm_ctx *ctx, const double *host_f) {
+  TRY(ensure_geometry(ctx));
+  TRY(ensure_copy_stream(ctx));
+  const long long N = ctx->N;
+  const size_t fbytes = (size_t)ctx->Q * ctx->fs * ctx->ssz;
+  const long long C = std::max<long long>(
+      1, std::min<long long>(1LL << 20, (long long)(fbytes / (2 * sizeof(double)))));
+  double *stage[2] = {(double *)ctx->f[ctx->cur], (double *)ctx->f[ctx->cur] + C};
+  void *dst = ctx->f[1 - ctx->cur];
+  // the staging array is free once the work already on the stream is done
+  CK(cudaEventRecord(ctx->ev_up_start, ctx->st));
+  CK(cudaStreamWaitEvent(ctx->cst, ctx->ev_up_start, 0));
+  long long k = 0;
+  for (int i = 0; i < ctx->Q; i++) {
+    const double w = ctx->D == 2 ? Lat<0>::w(i) : Lat<1>::w(i);
+    for (long long n0 = 0; n0 < N; n0 += C, k++) {
+      const int sl = (int)(k & 1);
+      const long long len = std::min(C, N - n0);
+      if (k >= 2) CK(cudaStreamWaitEvent(ctx->cst, ctx->ev_up_conv[sl], 0));
+      CK(cudaMemcpyAsync(stage[sl], host_f + (size_t)i * N + n0, (size_t)len * sizeof(double),
+                         cudaMemcpyHostToDevice, ctx->cst));
+      CK(cudaEventRecord(ctx->ev_up_copy[sl], ctx->cst));
+      CK(cudaStreamWaitEvent(ctx->st, ctx->ev_up_copy[sl], 0));
+      UploadArgs u;
+      u.src = stage[sl];
+      u.dst = (char *)dst + (size_t)i * ctx->fs * ctx->ssz;
+      u.flags = ctx->flags;
+      u.n0 = n0;
+      u.len = len;
+      u.w = w;
+      u.inv_scale = ctx->inv_scale;
+      launch_upload_chunk(u, ctx->d.precision, ctx->st);
+      ctx->launches++;
+      CK(cudaEventRecord(ctx->ev_up_conv[sl], ctx->st));
+    }
+  }
+  CK(cudaGetLastError());
+  ctx->need_collide = true;
+  ctx->prev_local = true;
+  return LBM_OK;
+}
+
+}  // namespace
+
 lbm_status lbm_set_distributions(lbm_ctx *ctx, const double *host_f, size_t n) {
   if (ctx) ctx->gen++;
   if (!ctx || !host_f) return LBM_ERR_ARG;
-  const size_t need = (size_t)ctx->Q * ctx->N;
-  if (n < need) return fail(ctx, LBM_ERR_ARG, "input must hold Q * nodes doubles");
-  TRY(ensure_geometry(ctx));
-  TRY(qbuf_ensure(ctx, need));
-  CK(cudaMemcpyAsync(ctx->qbuf, host_f, need * sizeof(double), cudaMemcpyHostToDevice, ctx->st));
-  KArgs a = base_args(ctx);
-  a.dst = ctx->f[1 - ctx->cur];
-  a.out_f = ctx->qbuf;
-  sweep(ctx, OP_FROM_DOUBLE, a);
-  ctx->need_collide = true;
-  ctx->prev_local = true;
+  if (n < (size_t)ctx->Q * ctx->N) return fail(ctx, LBM_ERR_ARG, "input must hold Q * nodes doubles");
+  TRY(upload_f(ctx, host_f));
   CK(cudaStreamSynchronize(ctx->st));
   return LBM_OK;
+}
+
+lbm_status lbm_set_distributions_async(lbm_ctx *ctx, const double *host_f, size_t n) {
+  if (ctx) ctx->gen++;
+  if (!ctx || !host_f) return LBM_ERR_ARG;
+  if (n < (size_t)ctx->Q * ctx->N) return fail(ctx, LBM_ERR_ARG, "input must hold Q * nodes doubles");
+  return upload_f(ctx, host_f);
 }
 
 lbm_status lbm_get_distributions(lbm_ctx *ctx, double *host_f, size_t n) {
@@ -1643,7 +1750,7 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, int check_every, int max_
     double h[2];
     CK(cudaMemcpyAsync(h, ctx->red2, sizeof(h), cudaMemcpyDeviceToHost, ctx->st));
     CK(cudaStreamSynchronize(ctx->st));
-    r = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
+    r = residual_of(h);
     ctx->last_residual = r;
     if (!std::isfinite(r)) {
       st = fail(ctx, LBM_ERR_DIVERGED, "non-finite residual");
@@ -1690,11 +1797,7 @@ lbm_status lbm_get_force_torque(lbm_ctx *ctx, int id, double F[3], double T[3]) 
 lbm_status lbm_copy_force_torque_async(lbm_ctx *ctx, int id, double *host_out) {
   if (!ctx || !host_out || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
   TRY(prepare(ctx));
-  if (!ctx->cst) {
-    CK(cudaStreamCreateWithFlags(&ctx->cst, cudaStreamNonBlocking));
-    CK(cudaEventCreateWithFlags(&ctx->ev_rec, cudaEventDisableTiming));
-    CK(cudaEventCreateWithFlags(&ctx->ev_cst, cudaEventDisableTiming));
-  }
+  TRY(ensure_copy_stream(ctx));
   CK(cudaEventRecord(ctx->ev_rec, ctx->st));
   CK(cudaStreamWaitEvent(ctx->cst, ctx->ev_rec, 0));
   CK(cudaMemcpyAsync(host_out, force_slot(ctx, ctx->slot) + 6 * id, 6 * sizeof(double),
@@ -1999,18 +2102,8 @@ lbm_status lbm_get_kernel_time(lbm_ctx *ctx, int kernel, double *ms, int64_t *la
   return LBM_OK;
 }
 
-// ---- velocity query without device allocation
-//
-// Staging buffer compiled into the library: 2^20 doubles (8 MiB) on every
-// device that loads it, shared by all contexts and all calls.
-static constexpr size_t kNoAllocScratchDoubles = size_t(1) << 20;
-static __device__ __align__(256) double g_noalloc_scratch[kNoAllocScratchDoubles];
-
-// Device address of the staging buffer, looked up once per device (host code
-// may not take the address of a __device__ variable directly).
-static constexpr int kNoAllocMaxDevices = 64;
-static double *g_noalloc_addr[kNoAllocMaxDevices] = {nullptr};
-static std::mutex g_noalloc_mu;
+// ---- velocity query without device allocation (staging array and its
+// per-device address: see the definitions before lbm_create)
 
 lbm_status lbm_get_velocity_noalloc(lbm_ctx *ctx, double *host_out, size_t n) {
   if (!ctx || !host_out) return LBM_ERR_ARG;
@@ -2033,18 +2126,11 @@ lbm_status lbm_get_velocity_noalloc(lbm_ctx *ctx, double *host_out, size_t n) {
   if (dev < 0 || dev >= kNoAllocMaxDevices) return fail(ctx, LBM_ERR_UNSUPPORTED, "device index too large");
   double *scratch = nullptr;
   {
+    // cached by lbm_create on this device (the context was created there)
     std::lock_guard<std::mutex> lock(g_noalloc_mu);
-    if (!g_noalloc_addr[dev]) {
-      void *p = nullptr;
-      cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
-      if (e != cudaSuccess) {
-        cudaGetLastError();
-        return fail(ctx, LBM_ERR_CUDA, std::string("cudaGetSymbolAddress: ") + cudaGetErrorString(e));
-      }
-      g_noalloc_addr[dev] = (double *)p;
-    }
     scratch = g_noalloc_addr[dev];
   }
+  if (!scratch) return fail(ctx, LBM_ERR_STATE, "staging array address not set up on this device");
   if (ctx->need_collide) TRY(init_collide(ctx));  // kernels only, no allocation
   // the array keeps the previous call's values: solid nodes must read 0
   CK(cudaMemsetAsync(scratch, 0, need * sizeof(double), ctx->st));
@@ -2459,6 +2545,60 @@ lbm_status lbm_batch_step(lbm_batch *b, int nsteps) {
   return LBM_OK;
 }
 
+namespace {
+
+// The stepping loop of lbm_batch_run_to_steady, between enter and leave.
+// A lattice whose residual is not finite leaves the loop (LBM_ERR_DIVERGED
+// at the end); the others run on to their own residual or max_steps.
+lbm_status run_batch_to_steady(lbm_batch *b, double tol, int check_every, int max_steps) {
+  const int n = (int)b->ctx.size();
+  for (int i = 0; i < n; i++) {
+    lbm_ctx *ctx = b->ctx[i];
+    TRY(velocity_to(ctx, ctx->u_snap));
+  }
+  int left = n;
+  lbm_status result = LBM_OK;
+  while (left > 0) {
+    int k = check_every;
+    long long most = 0;
+    for (int i = 0; i < n; i++)
+      if (b->active[i]) most = std::max(most, b->steps_done[i]);
+    if (most + k > max_steps) k = (int)(max_steps - most);
+    if (k <= 0) break;
+    TRY(batch_advance(b, k));
+    for (int i = 0; i < n; i++) {
+      if (!b->active[i]) continue;
+      lbm_ctx *c = b->ctx[i];
+      TRY(velocity_to(c, c->u_now));
+      launch_residual(c->u_now, c->u_snap, 0, c->flags, c->N, c->D, c->red2, c->st);
+      c->launches++;
+    }
+    for (int i = 0; i < n; i++) {
+      if (!b->active[i]) continue;
+      lbm_ctx *c = b->ctx[i];
+      double h[2];
+      BCK(cudaMemcpyAsync(h, c->red2, sizeof(h), cudaMemcpyDeviceToHost, c->st));
+      BCK(cudaStreamSynchronize(c->st));
+      const double r = residual_of(h);
+      b->residual[i] = r;
+      c->last_residual = r;
+      if (!std::isfinite(r)) {
+        b->active[i] = 0;
+        left--;
+        result = bfail(b, LBM_ERR_DIVERGED, "lattice " + std::to_string(i) + " diverged");
+      } else if (r < tol) {
+        b->active[i] = 0;
+        left--;
+      } else {
+        std::swap(c->u_now, c->u_snap);
+      }
+    }
+  }
+  return result;
+}
+
+}  // namespace
+
 lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int check_every, int max_steps,
                                    int64_t *steps_done, double *residual) {
   if (!b || check_every < 1 || max_steps < 0) return LBM_ERR_ARG;
@@ -2478,49 +2618,9 @@ lbm_status lbm_batch_run_to_steady(lbm_batch *b, double tol, int check_every, in
     const lbm_status s = enter(b);
     if (s != LBM_OK) return s;
   }
-  for (int i = 0; i < n; i++) {
-    lbm_ctx *ctx = b->ctx[i];
-    TRY(velocity_to(ctx, ctx->u_snap));
-  }
-  int left = n;
-  lbm_status result = LBM_OK;
-  while (left > 0) {
-    int k = check_every;
-    long long most = 0;
-    for (int i = 0; i < n; i++)
-      if (b->active[i]) most = std::max(most, b->steps_done[i]);
-    if (most + k > max_steps) k = (int)(max_steps - most);
-    if (k <= 0) break;
-    lbm_status s = batch_advance(b, k);
-    if (s != LBM_OK) return s;
-    for (int i = 0; i < n; i++) {
-      if (!b->active[i]) continue;
-      lbm_ctx *c = b->ctx[i];
-      TRY(velocity_to(c, c->u_now));
-      launch_residual(c->u_now, c->u_snap, 0, c->flags, c->N, c->D, c->red2, c->st);
-      c->launches++;
-    }
-    for (int i = 0; i < n; i++) {
-      if (!b->active[i]) continue;
-      lbm_ctx *c = b->ctx[i];
-      double h[2];
-      BCK(cudaMemcpyAsync(h, c->red2, sizeof(h), cudaMemcpyDeviceToHost, c->st));
-      BCK(cudaStreamSynchronize(c->st));
-      const double r = h[1] > 0 ? sqrt(h[0] / h[1]) : 0.0;
-      b->residual[i] = r;
-      c->last_residual = r;
-      if (!std::isfinite(r)) {
-        b->active[i] = 0;
-        left--;
-        result = bfail(b, LBM_ERR_DIVERGED, "lattice " + std::to_string(i) + " diverged");
-      } else if (r < tol) {
-        b->active[i] = 0;
-        left--;
-      } else {
-        std::swap(c->u_now, c->u_snap);
-      }
-    }
-  }
+  // every exit from here on passes through leave(): work queued on the
+  // caller's stream afterwards stays ordered after the batch's work
+  const lbm_status result = run_batch_to_steady(b, tol, check_every, max_steps);
   for (int i = 0; i < n; i++) {
     if (steps_done) steps_done[i] = b->steps_done[i];
     if (residual) residual[i] = b->residual[i];

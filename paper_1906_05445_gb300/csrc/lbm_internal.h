@@ -206,6 +206,17 @@ void launch_ibm_interp(const IbmArgs &a, int precision, cudaStream_t st);
 void launch_ibm_spread(const IbmArgs &a, int precision, cudaStream_t st);
 void launch_zero_band(const KArgs &a, int precision, cudaStream_t st);
 
+// chunked upload of FP64 populations (transfer.cu)
+struct UploadArgs {
+  const double *src;     // staged full populations f_i of nodes n0 .. n0 + len - 1
+  void *dst;             // storage array of direction i (element 0 = node 0)
+  const uint8_t *flags;  // node flags (solid nodes store 0)
+  long long n0, len;
+  double w;              // lattice weight w_i
+  double inv_scale;      // storage scale^-1 (1 except FP16 storage)
+};
+void launch_upload_chunk(const UploadArgs &a, int precision, cudaStream_t st);
+
 // reductions (reduce.cu)
 void launch_residual(const double *u, const double *usnap, long long n,
                      const uint8_t *flags, long long N, int d, double *out2,

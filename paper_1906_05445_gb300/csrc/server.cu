@@ -46,17 +46,30 @@ double now_s(const lbm_server *s) {
   return std::chrono::duration<double>(std::chrono::steady_clock::now() - s->t0).count();
 }
 
+size_t nodes_of(const lbm_lattice_desc &d) {
+  return (size_t)d.nx * d.ny * (d.lattice == LBM_D2Q9 ? 1 : d.nz);
+}
+
+// device bytes a running request allocates after its creation: the two FP64
+// velocity snapshots of the residual (allocated by the first batch round)
+// and, with keep_velocity, the FP64 staging of the final velocity query
+size_t run_bytes(const lbm_request &r) {
+  const size_t dn = nodes_of(r.lattice) * (r.lattice.lattice == LBM_D2Q9 ? 2 : 3);
+  return (2 + (r.keep_velocity ? 1 : 0)) * dn * sizeof(double);
+}
+
 // device bytes of a request before it is created: two distribution arrays,
-// flags and solid ids, the IBM fields, plus 10% and 1 MiB for the rest
+// flags and solid ids, the IBM fields, plus 10% and 1 MiB for the rest, and
+// what it allocates while it runs
 size_t estimate_bytes(const lbm_request &r) {
   const lbm_lattice_desc &d = r.lattice;
-  const size_t n = (size_t)d.nx * d.ny * (d.lattice == LBM_D2Q9 ? 1 : d.nz);
+  const size_t n = nodes_of(d);
   const size_t q = d.lattice == LBM_D2Q9 ? 9 : 19;
   const size_t ssz = d.precision == LBM_FP64 ? 8 : d.precision == LBM_FP32 ? 4 : 2;
   const size_t tsz = d.precision == LBM_FP64 ? 8 : 4;
   size_t b = 2 * q * n * ssz + 3 * n;
   if (r.scheme.scheme == LBM_IBM_DIRECT) b += 6 * n * tsz;
-  return b + b / 10 + (1u << 20);
+  return b + b / 10 + (1u << 20) + run_bytes(r);
 }
 
 bool request_ok(const lbm_request &r) {
@@ -110,7 +123,8 @@ void finish(lbm_server *s, Active &a, double residual, int status, int error) {
     keep = r.keep_velocity != 0;
     nsolids = r.nsolids;
   }
-  if (a.ctx && status == LBM_REQ_DONE) {
+  const bool has_result = status == LBM_REQ_DONE || status == LBM_REQ_UNCONVERGED;
+  if (a.ctx && has_result) {
     if (nsolids > 0) lbm_get_force_torque(a.ctx, 0, res.force, res.torque);
     if (keep) {
       lbm_info info;
@@ -125,10 +139,18 @@ void finish(lbm_server *s, Active &a, double residual, int status, int error) {
       if (lbm_get_velocity(a.ctx, vel.data(), n) != LBM_OK) vel.clear();
     }
   }
-  if (a.ctx) lbm_destroy(a.ctx);
+  // what the lattice held at the end, if that is above what admission
+  // counted for it (it should not be)
+  int64_t held = (int64_t)a.bytes;
+  if (a.ctx) {
+    lbm_info info;
+    if (lbm_get_info(a.ctx, &info) == LBM_OK && info.device_bytes > held) held = info.device_bytes;
+    lbm_destroy(a.ctx);
+  }
   a.ctx = nullptr;
   std::lock_guard<std::mutex> lk(s->mu);
   lbm_server::Req &q = s->reqs[a.id];
+  q.res.device_bytes = held;
   q.res.status = status;
   q.res.error = error;
   q.res.steps = a.steps;
@@ -196,11 +218,13 @@ void run(lbm_server *s) {
       }
       lbm_info info;
       lbm_get_info(c, &info);
-      act.push_back({id, c, (size_t)info.device_bytes, 0, false});
-      used += (size_t)info.device_bytes;
+      // its memory now plus what the batch rounds and the final query add
+      const size_t bytes = (size_t)info.device_bytes + run_bytes(r);
+      act.push_back({id, c, bytes, 0, false});
+      used += bytes;
       {
         std::lock_guard<std::mutex> lk(s->mu);
-        s->reqs[id].res.device_bytes = info.device_bytes;
+        s->reqs[id].res.device_bytes = (int64_t)bytes;
       }
       changed = true;
     }
@@ -220,12 +244,15 @@ void run(lbm_server *s) {
     if (bs == LBM_OK)
       bs = lbm_batch_run_to_steady(batch, s->tol, s->check_every, s->check_every, steps.data(),
                                    res.data());
-    if (bs != LBM_OK) {
+    // a member whose residual is not finite makes the round return
+    // LBM_ERR_DIVERGED after the others have run their steps: only that
+    // member fails, below.  Any other error fails the whole round.
+    if (bs != LBM_OK && bs != LBM_ERR_DIVERGED) {
       if (batch) lbm_batch_destroy(batch);
       batch = nullptr;
       for (auto &a : act) {
-        finish(s, a, NAN, LBM_REQ_FAILED, bs);
         used -= a.bytes;
+        finish(s, a, NAN, LBM_REQ_FAILED, bs);
       }
       act.clear();
       continue;
@@ -236,9 +263,20 @@ void run(lbm_server *s) {
     for (size_t i = 0; i < act.size(); i++) {
       Active &a = act[i];
       a.steps += steps[i];
-      if (res[i] < s->tol || a.steps >= s->max_steps || !std::isfinite(res[i])) {
+      if (!std::isfinite(res[i])) {
         a.retire = true;
         any = true;
+        why[i] = LBM_REQ_FAILED;
+        err[i] = LBM_ERR_DIVERGED;
+        continue;
+      }
+      if (res[i] < s->tol) {
+        a.retire = true;
+        any = true;
+      } else if (a.steps >= s->max_steps) {
+        a.retire = true;
+        any = true;
+        why[i] = LBM_REQ_UNCONVERGED;
       }
       std::lock_guard<std::mutex> lk(s->mu);
       const lbm_server::Req &q = s->reqs[a.id];
@@ -346,7 +384,8 @@ lbm_status lbm_server_wait(lbm_server *s, int64_t id, lbm_result *result, double
   if (it == s->reqs.end()) return LBM_ERR_ARG;
   auto done = [&] {
     const int st = s->reqs[id].res.status;
-    return st == LBM_REQ_DONE || st == LBM_REQ_FAILED || st == LBM_REQ_CANCELLED;
+    return st == LBM_REQ_DONE || st == LBM_REQ_FAILED || st == LBM_REQ_CANCELLED ||
+           st == LBM_REQ_UNCONVERGED;
   };
   if (timeout_s < 0) {
     s->cv_done.wait(lk, done);
@@ -364,7 +403,8 @@ lbm_status lbm_server_velocity(lbm_server *s, int64_t id, double *host_out, size
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return LBM_ERR_ARG;
   const lbm_server::Req &q = it->second;
-  if (q.res.status != LBM_REQ_DONE || q.vel.empty()) return LBM_ERR_STATE;
+  if ((q.res.status != LBM_REQ_DONE && q.res.status != LBM_REQ_UNCONVERGED) || q.vel.empty())
+    return LBM_ERR_STATE;
   if (n < q.vel.size()) return LBM_ERR_ARG;
   memcpy(host_out, q.vel.data(), q.vel.size() * sizeof(double));
   return LBM_OK;

@@ -71,7 +71,7 @@ class lbm_result(C.Structure):
                 ("device_bytes", C.c_int64)]
 
 
-REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED = range(5)
+REQ_PENDING, REQ_RUNNING, REQ_DONE, REQ_FAILED, REQ_CANCELLED, REQ_UNCONVERGED = range(6)
 
 
 class lbm_domain_desc(C.Structure):
@@ -102,6 +102,7 @@ def _load():
         "lbm_set_scheme": (st, [vp, C.POINTER(lbm_scheme_desc)]),
         "lbm_init_equilibrium": (st, [vp, d, dp]),
         "lbm_set_distributions": (st, [vp, dp, sz]),
+        "lbm_set_distributions_async": (st, [vp, dp, sz]),
         "lbm_get_distributions": (st, [vp, dp, sz]),
         "lbm_step": (st, [vp, i]),
         "lbm_run_to_steady": (st, [vp, d, i, i, C.POINTER(i), dp]),
@@ -156,6 +157,7 @@ lib = _load()
 globals().update({name: getattr(lib, name) for name in (
     "lbm_create", "lbm_destroy", "lbm_add_solid", "lbm_set_solid_motion",
     "lbm_set_scheme", "lbm_init_equilibrium", "lbm_set_distributions",
+    "lbm_set_distributions_async",
     "lbm_get_distributions", "lbm_step", "lbm_run_to_steady", "lbm_get_density",
     "lbm_get_velocity", "lbm_get_strain_rate", "lbm_get_stress", "lbm_get_dissipation",
     "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
@@ -267,6 +269,13 @@ class Lattice:
     def set_f(self, f):
         f = np.ascontiguousarray(f, dtype=np.float64)
         self._check(lbm_set_distributions(self.h, _dp(f), f.size))
+
+    def set_f_async(self, f):
+        """Upload without waiting.  `f` (C-contiguous float64, best
+        page-locked) must stay alive and unchanged until sync() or a query."""
+        if f.dtype != np.float64 or not f.flags.c_contiguous:
+            raise ValueError("f must be C-contiguous float64")
+        self._check(lbm_set_distributions_async(self.h, _dp(f), f.size))
 
     def get_f(self):
         out = np.zeros((self.Q, self.N))

@@ -188,3 +188,16 @@ def test_residual_on_hand_built_fields(oracle):
     assert abs(np.sqrt(num / (u_old[:, fl] ** 2).sum()) / want - 1) > 0.01
     assert abs(np.sqrt(((u_new - u_old)[0, fl] ** 2).sum() / (u_new[0, fl] ** 2).sum())
                / want - 1) > 0.01
+
+
+def test_residual_of_a_diverged_field_is_not_finite(oracle):
+    """A field with a non-finite value has no residual: NaN, never a small
+    number that would read as converged."""
+    s = oracle.OracleSim(0, 6, 5, 1, 0.8, 0)
+    e, w = oracle.lattice(0)
+    f = np.tile(w[:, None, None, None], (1, 1, 5, 6))
+    s.set_f(f)
+    s.snapshot_velocity()
+    f[1, 0, 2, 3] = np.nan
+    s.set_f(f)
+    assert np.isnan(s.residual())

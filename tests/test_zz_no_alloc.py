@@ -39,21 +39,39 @@ def noalloc_velocity(L, lat):
 
 @pytest.mark.parametrize("precision", [W.FP64, W.FP32])
 def test_noalloc_velocity_matches_lbm_get_velocity(lbm, precision):
+    """Two calls in a row, a few steps apart, on a lattice that has never
+    run the allocating query: the free device memory is the same before and
+    after them, and each result equals lbm_get_velocity at the same state."""
+    import torch
     # a fixed sphere with interpolated bounce-back: bulk and boundary-node
     # query kernels both write into the staging array
     p = W.fixed_sphere(40, 7.3, seed=31, tau=0.7, g=2e-4, scheme=W.BOUZIDI_QUAD,
                        precision=precision, collision=W.MRT)
+    # the reference state after 5 steps comes from an identical twin.  Its
+    # query also loads the query kernels: CUDA loads kernel code lazily, on
+    # a kernel's first launch, and that code occupies device memory
+    twin = lbm.Lattice.from_problem(p)
+    twin.step(5)
+    ref_a = twin.velocity()
     lat = lbm.Lattice.from_problem(p)
     lat.step(5)
-    for _ in range(2):                       # two calls in a row
-        ref = lat.velocity()
-        st, got = noalloc_velocity(lbm, lat)
-        assert st == 0, lbm.lbm_last_error(lat.h)
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    st, u_a = noalloc_velocity(lbm, lat)
+    assert st == 0, lbm.lbm_last_error(lat.h)
+    lat.step(3)
+    st, u_b = noalloc_velocity(lbm, lat)
+    assert st == 0, lbm.lbm_last_error(lat.h)
+    torch.cuda.synchronize()
+    assert torch.cuda.mem_get_info()[0] == free0
+    ref_b = lat.velocity()
+    for got, ref in ((u_a, ref_a), (u_b, ref_b)):
         assert not np.isnan(got).any()
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= TOL, err
-        lat.step(3)
+    assert np.linalg.norm(ref_b - ref_a) > 1e-3 * np.linalg.norm(ref_a)  # the state moved
     lat.close()
+    twin.close()
 
 
 def test_noalloc_velocity_limits(lbm):

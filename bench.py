@@ -417,6 +417,49 @@ def run_serve_leg(stream):
             "config": {k: v for k, v in c.items()}}
 
 
+def storage_roofline(lbm, stream, device, precision, steps=ROOFLINE_STEPS):
+    """The two-lattice step with 16-bit storage: MLUPS over `steps` steps and
+    the roofline of the bounce-back lattice's bulk sweep (76 B per node),
+    every launch timed with CUDA events on its stream."""
+    import torch
+    problems = workload(precision)
+    lats = [lbm.Lattice.from_problem(p, stream=stream.cuda_stream) for p in problems]
+    for lt in lats:
+        lt.init_equilibrium()
+    for _ in range(5):
+        for lt in lats:
+            lt.step(1)
+    torch.cuda.synchronize(device)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        for lt in lats:
+            lt.step(1)
+    e1.record(stream)
+    torch.cuda.synchronize(device)
+    secs = e0.elapsed_time(e1) / 1e3
+    for lt in lats:
+        lt.set_timing(lbm.TIME_BULK, every=1)
+    for _ in range(steps):
+        for lt in lats:
+            lt.step(1)
+    torch.cuda.synchronize(device)
+    ms, nl, nodes = lats[0].kernel_time(lbm.TK_BULK)
+    for lt in lats:
+        lt.close()
+    bpn = BYTES_PER_NODE[precision]
+    achieved = nodes / nl * bpn / (ms / nl / 1e3) / 1e9
+    peaks, kind = measured_peaks()
+    peak = float(peaks["hbm_gbs"])
+    return {"value": sum(p.nodes for p in problems) * steps / secs / 1e6, "unit": UNIT,
+            "steps": steps, "bound": "hbm", "achieved": achieved, "peak": peak,
+            "unit_roofline": "GB/s", "frac": achieved / peak, "bytes_per_node": bpn,
+            "launch_ms": ms / nl, "timed_launches": int(nl),
+            "kernel": "k_bulk_vec<D3Q19,MRT-q,%s,2 words,packed>" % (
+                "bf16" if precision == W.FP32_BF16 else "fp16 x 2^10"),
+            "peak_kind": kind + " hbm_gbs", "traffic": None}
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args, rank, world, local):
     import torch
@@ -563,6 +606,11 @@ def run_ours(args, rank, world, local):
             cpu["single_thread"] = single
         except (OSError, RuntimeError) as e:  # no room for the processes
             cpu = dict(single, all_cores_error=str(e))
+    lowp = {}
+    if rank == 0 and world == 1 and not args.no_lowp and args.workload == "fixed" and \
+            precision == W.FP32:
+        for name, prec in (("bf16", W.FP32_BF16), ("fp16", W.FP32_FP16)):
+            lowp[name] = storage_roofline(lbm, stream, device, prec)
     batch = serve_leg = None
     if rank == 0 and world == 1 and not args.no_batch and args.workload == "fixed":
         batch = run_batch_leg(lbm, stream.cuda_stream,
@@ -587,6 +635,7 @@ def run_ours(args, rank, world, local):
                                              f"the timed region",
                              "peak_kind": peak_kind + " hbm_gbs"},
                 "kernel_ms_per_step": kt,
+                "roofline_bf16": lowp.get("bf16"), "roofline_fp16": lowp.get("fp16"),
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": int(launches) * world,
                 "batch": batch, "serve": serve_leg}
@@ -613,6 +662,8 @@ def main(argv=None):
                     help="batch leg: 8 lattices R 3..8 (default) or 32 lattices R 4..12")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-solve and served-stream legs")
+    ap.add_argument("--no-lowp", action="store_true",
+                    help="skip the BF16 / FP16 storage roofline passes")
     args = ap.parse_args(argv)
     args.warmup = max(args.warmup, 3)
     rank, world, local = dist_env()

@@ -161,6 +161,17 @@ struct lbm_ctx {
   int out_face = -1;
   long long out_area = 0;
   double pf_c[kMaxSolids][3] = {};
+  // free solids: the solids' state lives in device memory (sol_d[0] the
+  // current state, sol_d[1] the centres of the current geometry, free_d the
+  // dynamics) and a step moves them there.  The host copy in `solids` is
+  // brought up to date on demand (motion_pull) and sent back after a change
+  // (motion_push).
+  SolidsDev *sol_d = nullptr;
+  FreeDev *free_d = nullptr;
+  bool host_stale = false, push_needed = true;
+  // the force-record slot the next IBM step's motion reads instead of the
+  // current one (-1: none); set for the first step of a captured step pair
+  int motion_slot = -1;
   cudaStream_t gst = nullptr;
   cudaEvent_t ev_geom = nullptr, ev_gfree = nullptr;
   // IBM
@@ -310,6 +321,9 @@ void resolve_timing(lbm_ctx *ctx) {
   ctx->pending.clear();
 }
 
+bool any_free(const lbm_ctx *ctx);
+bool dev_motion(const lbm_ctx *ctx);
+
 // ---- kernel argument assembly
 SolidsDev solids_dev(const lbm_ctx *ctx, bool geometry_centres) {
   SolidsDev s{};
@@ -391,6 +405,7 @@ KArgs base_args(lbm_ctx *ctx) {
   a.refill_sid = ctx->refill_sid;
   a.refill_cap = ctx->refill_cap;
   a.solids = solids_dev(ctx, true);
+  a.solids_d = dev_motion(ctx) ? ctx->sol_d + 1 : nullptr;
   a.sid = ctx->sid;
   return a;
 }
@@ -434,6 +449,75 @@ bool any_moving(const lbm_ctx *ctx) {
   return false;
 }
 
+// Whether the solids move on the device (a free solid is present).
+bool dev_motion(const lbm_ctx *ctx) { return any_free(ctx); }
+
+// Host copy of the solids' state <- device (waits for the stream).
+lbm_status motion_pull(lbm_ctx *ctx) {
+  if (!ctx->host_stale || !ctx->sol_d) return LBM_OK;
+  SolidsDev sd[2];
+  FreeDev fd[kMaxSolids];
+  CK(cudaMemcpyAsync(sd, ctx->sol_d, sizeof(sd), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaMemcpyAsync(fd, ctx->free_d, sizeof(fd), cudaMemcpyDeviceToHost, ctx->st));
+  CK(cudaStreamSynchronize(ctx->st));
+  for (size_t k = 0; k < ctx->solids.size(); k++) {
+    SolidHost &h = ctx->solids[k];
+    for (int a = 0; a < 3; a++) {
+      h.c[a] = sd[0].s[k].c[a];
+      h.cg[a] = sd[1].s[k].c[a];
+      h.d.velocity[a] = sd[0].s[k].U[a];
+      h.d.omega[a] = sd[0].s[k].Om[a];
+      h.Up[a] = fd[k].Up[a];
+      h.Omp[a] = fd[k].Omp[a];
+    }
+    for (int c = 0; c < 6; c++) h.Ip[c] = fd[k].Ip[c];
+    h.have_Ip = fd[k].have_Ip != 0;
+  }
+  ctx->host_stale = false;
+  return LBM_OK;
+}
+
+// Device copy of the solids' state <- host (the current state, the
+// geometry's centres and the dynamics), ordered on the stream.
+lbm_status motion_push(lbm_ctx *ctx) {
+  if (!dev_motion(ctx)) {
+    ctx->push_needed = false;
+    return LBM_OK;
+  }
+  if (!ctx->sol_d) TRY(dalloc(ctx, (void **)&ctx->sol_d, 2 * sizeof(SolidsDev)));
+  if (!ctx->free_d) TRY(dalloc(ctx, (void **)&ctx->free_d, kMaxSolids * sizeof(FreeDev)));
+  if (!ctx->kempe) TRY(dalloc(ctx, (void **)&ctx->kempe, sizeof(double) * kMaxSolids * 6));
+  SolidsDev sd[2] = {solids_dev(ctx, false), solids_dev(ctx, true)};
+  FreeDev fd[kMaxSolids];
+  memset(fd, 0, sizeof(fd));
+  for (size_t k = 0; k < ctx->solids.size(); k++) {
+    const SolidHost &h = ctx->solids[k];
+    fd[k].rho_p = h.rho_p;
+    for (int a = 0; a < 3; a++) {
+      fd[k].g[a] = h.g[a];
+      fd[k].Up[a] = h.Up[a];
+      fd[k].Omp[a] = h.Omp[a];
+    }
+    for (int c = 0; c < 6; c++) fd[k].Ip[c] = h.Ip[c];
+    fd[k].have_Ip = h.have_Ip ? 1 : 0;
+  }
+  CK(cudaMemcpyAsync(ctx->sol_d, sd, sizeof(sd), cudaMemcpyHostToDevice, ctx->st));
+  CK(cudaMemcpyAsync(ctx->free_d, fd, sizeof(fd), cudaMemcpyHostToDevice, ctx->st));
+  // the copies read host locals: let them finish before those go
+  CK(cudaStreamSynchronize(ctx->st));
+  ctx->push_needed = false;
+  ctx->host_stale = false;
+  return LBM_OK;
+}
+
+// Before the host reads or changes the solids: bring its copy up to date,
+// and have the device copy sent again before the next kernel reads it.
+lbm_status solids_to_host(lbm_ctx *ctx, bool will_change) {
+  TRY(motion_pull(ctx));
+  if (will_change) ctx->push_needed = true;
+  return LBM_OK;
+}
+
 // Eq. 24 for every free solid from the current state f*(t) and the forces
 // of its collision, into ctx->kempe (FP64, zeroed first).
 lbm_status kempe_integrals(lbm_ctx *ctx) {
@@ -446,95 +530,56 @@ lbm_status kempe_integrals(lbm_ctx *ctx) {
     KArgs a = base_args(ctx);
     a.src = ctx->f[ctx->cur];
     a.solids = solids_dev(ctx, false);
+    a.solids_d = ctx->sol_d;  // the current state (free solids move on the device)
+    a.kbox_dev = 1;
     a.kempe_out = ctx->kempe + 6 * k;
     a.kempe_solid = (int)k;
     for (int c = 0; c < 3; c++) {
-      // every node with a cell corner inside lies within R + 1 of the centre
+      // every node with a cell corner inside lies within R + 1 of the
+      // centre: a box of ceil(2R + 2) + 2 nodes from floor(c - R - 1)
       const bool whole = c >= ctx->D || (c == 2 && h.d.kind == LBM_CYLINDER_Z);
-      const int lo = (int)floor(h.c[c] - h.d.radius - 1.0);
-      const int hi = (int)ceil(h.c[c] + h.d.radius + 1.0);
-      const int ext = hi - lo + 1;
-      if (whole || ext >= len[c]) {
-        a.kbox[c] = 0;
-        a.kbox[3 + c] = len[c];
-      } else {
-        a.kbox[c] = lo;
-        a.kbox[3 + c] = ext;
-      }
+      const int ext = (int)ceil(2.0 * h.d.radius + 2.0) + 2;
+      a.kbox[c] = 0;
+      a.kbox[3 + c] = (whole || ext >= len[c]) ? len[c] : ext;
     }
     sweep(ctx, OP_KEMPE, a);
   }
   return LBM_OK;
 }
 
-// Free solids (Sec. 3.2): new velocities from the force record `slot` (this
-// step's momentum exchange under bounce-back, the current IBM force under
-// IBM) and gravity, dt = 1, rho_f = rho0 = 1:
-//  - bounce-back, Eq. 20: rho_p V dv = F + (rho_p - rho_f) V g, I dw = T;
-//  - IBM, Eq. 23: rho_p V dv = rho_f V (v - v_prev) + F + (rho_p - rho_f) V g,
-//    I dw = I (rho_f / rho_p)(w - w_prev) + T.
-// The centre moves by the mean of the old and new velocity.  V and I are
-// those of a sphere (4/3 pi R^3, 2/5 m R^2) or a cylinder (pi R^2 times its
-// length: 1 in 2D, nz in 3D; 1/2 m R^2 about z).
-lbm_status advance_free(lbm_ctx *ctx, int slot) {
+double *force_slot(lbm_ctx *ctx, int slot);
+
+// One step of the solids' motion on the device (motion.cu): free solids by
+// Newton-Euler from the force record `slot` (this step's momentum exchange
+// under bounce-back, the current IBM force under IBM), the others by their
+// prescribed velocity.  Nothing is read back.
+lbm_status motion_step(lbm_ctx *ctx, int slot) {
   const bool ibm = ctx->scheme.scheme == LBM_IBM_DIRECT;
   const bool kempe = ibm && ctx->scheme.ibm_inertia == LBM_INERTIA_KEMPE;
-  const bool uhlmann = ibm && ctx->scheme.ibm_inertia == LBM_INERTIA_UHLMANN;
-  double rec[kMaxSolids * 6], In[kMaxSolids * 6];
+  if (ctx->push_needed) TRY(motion_push(ctx));
   if (kempe) TRY(kempe_integrals(ctx));
-  CK(cudaMemcpyAsync(rec, ctx->hist + (size_t)slot * kMaxSolids * 6, sizeof(rec),
-                     cudaMemcpyDeviceToHost, ctx->st));
-  if (kempe) CK(cudaMemcpyAsync(In, ctx->kempe, sizeof(In), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
-  for (size_t k = 0; k < ctx->solids.size(); k++) {
-    SolidHost &h = ctx->solids[k];
-    if (!(h.rho_p > 0)) continue;
-    const double R = h.d.radius;
-    const bool cyl = ctx->D == 2 || h.d.kind == LBM_CYLINDER_Z;
-    const double V = cyl ? PI * R * R * (ctx->D == 2 ? 1.0 : (double)ctx->d.nz)
-                         : 4.0 / 3.0 * PI * R * R * R;
-    const double m = h.rho_p * V, I = m * (cyl ? 0.5 : 0.4) * R * R;
-    double Un[3], On[3];
-    for (int a = 0; a < 3; a++) {
-      double dv = rec[6 * k + a] + (h.rho_p - 1.0) * V * h.g[a];
-      double dw = rec[6 * k + 3 + a];
-      if (kempe) {
-        // Eq. 21 with Eq. 24: the change of the inside fluid's momentum
-        // (angular momentum) over the last step
-        if (!h.have_Ip) {
-          h.Ip[a] = In[6 * k + a];
-          h.Ip[3 + a] = In[6 * k + 3 + a];
-        }
-        dv += In[6 * k + a] - h.Ip[a];
-        dw += In[6 * k + 3 + a] - h.Ip[3 + a];
-      } else if (ibm && !uhlmann) {
-        dv += V * (h.d.velocity[a] - h.Up[a]);
-        dw += I / h.rho_p * (h.d.omega[a] - h.Omp[a]);
-      }
-      if (uhlmann) {
-        // Eq. 22: the inside fluid moves rigidly with the solid and its
-        // inertia is taken off the solid's
-        Un[a] = h.d.velocity[a] + dv / ((h.rho_p - 1.0) * V);
-        On[a] = h.d.omega[a] + dw / (I * (1.0 - 1.0 / h.rho_p));
-        continue;
-      }
-      Un[a] = h.d.velocity[a] + dv / m;
-      On[a] = h.d.omega[a] + dw / I;
-    }
-    if (ctx->D == 2) Un[2] = 0;
-    if (cyl) On[0] = On[1] = 0;
-    if (kempe) {
-      for (int c = 0; c < 6; c++) h.Ip[c] = In[6 * k + c];
-      h.have_Ip = true;
-    }
-    for (int a = 0; a < 3; a++) {
-      h.c[a] += 0.5 * (h.d.velocity[a] + Un[a]);
-      h.Up[a] = h.d.velocity[a];
-      h.Omp[a] = h.d.omega[a];
-      h.d.velocity[a] = Un[a];
-      h.d.omega[a] = On[a];
-    }
-  }
+  MotionArgs m;
+  memset(&m, 0, sizeof(m));
+  m.now = ctx->sol_d;
+  m.fr = ctx->free_d;
+  m.rec = force_slot(ctx, slot);
+  m.kempe = kempe ? ctx->kempe : nullptr;
+  m.n = (int)ctx->solids.size();
+  m.mode = !ibm ? MM_BOUNCE_BACK
+                : kempe ? MM_IBM_KEMPE
+                        : ctx->scheme.ibm_inertia == LBM_INERTIA_UHLMANN ? MM_IBM_UHLMANN
+                                                                         : MM_IBM_FENG;
+  m.dim = ctx->D;
+  m.nz = ctx->D == 2 ? 1 : ctx->d.nz;
+  for (int k = 0; k < 6; k++) m.face[k] = ctx->dom.type[k];
+  m.len[0] = ctx->d.nx;
+  m.len[1] = ctx->d.ny;
+  m.len[2] = m.nz;
+  m.err = ctx->counts + 4;
+  launch_motion(m, ctx->st);
+  ctx->launches++;
+  ctx->host_stale = true;
+  CK(cudaGetLastError());
   return LBM_OK;
 }
 
@@ -679,6 +724,7 @@ GeomArgs geom_args(lbm_ctx *ctx) {
   g.scheme = ctx->scheme.scheme;
   g.force_all = ctx->d.force_region == LBM_FORCE_ALL;
   g.solids = solids_dev(ctx, true);
+  g.solids_d = dev_motion(ctx) ? ctx->sol_d + 1 : nullptr;
   g.flags = ctx->flags;
   g.sid = ctx->sid;
   g.counts = ctx->counts;
@@ -729,9 +775,29 @@ lbm_status check_clearance(lbm_ctx *ctx) {
 }
 
 void set_boxes(lbm_ctx *ctx, GeomArgs &g, bool full) {
+  g.box_dev = 0;
   if (full || ctx->solids.empty()) {
     g.nbox = 1;
     g.box[0] = {0, 0, 0, g.nx, g.ny, g.nz};
+  } else if (dev_motion(ctx)) {
+    // the centres are in device memory: boxes of a fixed width that covers
+    // any position, anchored there by the geometry kernels
+    g.nbox = (int)ctx->solids.size();
+    g.box_dev = 1;
+    const int n[3] = {g.nx, g.ny, g.nz};
+    for (int k = 0; k < g.nbox; k++) {
+      const SolidHost &h = ctx->solids[k];
+      const double ext = h.d.radius + kGeomMargin + fabs(ctx->scheme.ibm_retraction);
+      g.box_ext[k] = ext;
+      int w[3];
+      for (int a = 0; a < 3; a++) {
+        const bool whole =
+            h.d.fluid_inside || (a == 2 && (ctx->D == 2 || h.d.kind == LBM_CYLINDER_Z));
+        const int wa = (int)ceil(2.0 * ext) + 2;
+        w[a] = (whole || wa >= n[a]) ? n[a] : wa;
+      }
+      g.box[k] = {0, 0, 0, w[0], w[1], w[2]};
+    }
   } else {
     g.nbox = (int)ctx->solids.size();
     for (int k = 0; k < g.nbox; k++) solid_box(ctx, ctx->solids[k], g.box[k]);
@@ -836,9 +902,11 @@ lbm_status read_counts(lbm_ctx *ctx, int out[16]) {
 lbm_status rebuild_full(lbm_ctx *ctx) {
   if (ctx) ctx->gen++;
   free_spare(ctx);  // capacities may change; the next moving step prefetches again
+  TRY(motion_pull(ctx));
   if (!ctx->restore_geometry)
     for (auto &s : ctx->solids) memcpy(s.cg, s.c, sizeof(s.c));
   ctx->restore_geometry = false;
+  TRY(motion_push(ctx));
   TRY(build_markers(ctx));
   GeomArgs g = geom_args(ctx);
   set_boxes(ctx, g, true);
@@ -889,7 +957,14 @@ lbm_status rebuild_full(lbm_ctx *ctx) {
 
 // Per-step rebuild over the boxes of the solids (moving geometry).
 lbm_status rebuild_boxes(lbm_ctx *ctx) {
-  for (auto &s : ctx->solids) memcpy(s.cg, s.c, sizeof(s.c));
+  if (dev_motion(ctx)) {
+    // the geometry's centres <- the current ones, on the device
+    if (ctx->push_needed) TRY(motion_push(ctx));
+    CK(cudaMemcpyAsync(ctx->sol_d + 1, ctx->sol_d, sizeof(SolidsDev), cudaMemcpyDeviceToDevice,
+                       ctx->st));
+  } else {
+    for (auto &s : ctx->solids) memcpy(s.cg, s.c, sizeof(s.c));
+  }
   GeomArgs g = geom_args(ctx);
   set_boxes(ctx, g, false);
   g.track_new = is_ibb(ctx->scheme.scheme) ? 1 : 0;
@@ -953,8 +1028,10 @@ bool take_prefetched(lbm_ctx *ctx) {
 }
 
 lbm_status ensure_geometry(lbm_ctx *ctx) {
-  if (ctx->nface) TRY(check_clearance(ctx));
+  // solids moving on the device are checked there, after each move
+  if (ctx->nface && !ctx->host_stale) TRY(check_clearance(ctx));
   if (ctx->geom_dirty) return rebuild_full(ctx);
+  if (ctx->push_needed) TRY(motion_push(ctx));
   return LBM_OK;
 }
 
@@ -977,6 +1054,7 @@ IbmArgs ibm_args(lbm_ctx *ctx, double *acc) {
   ib.Fm = ctx->mk_F;
   ib.kernel = ctx->scheme.ibm_kernel;
   ib.solids = solids_dev(ctx, true);
+  ib.solids_d = dev_motion(ctx) ? ctx->sol_d + 1 : nullptr;
   ib.u_band = ctx->u_band;
   ib.f_ibm = ctx->f_ibm;
   ib.force_acc = acc;
@@ -1080,15 +1158,19 @@ lbm_status step_begin(lbm_ctx *ctx, StepState &ss) {
                 "Eq. 16 keeps pre-collision values per boundary node: solids must not translate");
   const bool free_ = any_free(ctx);
   // IBM: the force of the previous step's pre-pass moves the free solids;
-  // the others move with their prescribed velocity
-  if (ibm && free_) TRY(advance_free(ctx, ctx->slot));
-  if (ibm && moving)
+  // the others move with their prescribed velocity.  With a free solid all
+  // of them move on the device (and are checked against the faces there).
+  if (ibm && free_) {
+    const int ms = ctx->motion_slot >= 0 ? ctx->motion_slot : ctx->slot;
+    ctx->motion_slot = -1;
+    TRY(motion_step(ctx, ms));
+  }
+  if (ibm && moving && !free_)
     for (auto &s : ctx->solids)
-      if (!(s.rho_p > 0))
-        for (int a = 0; a < 3; a++) s.c[a] += s.d.velocity[a];
+      for (int a = 0; a < 3; a++) s.c[a] += s.d.velocity[a];
   // free solids' next velocities are not known ahead: no prefetch
   const bool prefetch = moving && ctx->geom_prefetch && !free_;
-  if (moving && ctx->nface) TRY(check_clearance(ctx));
+  if (moving && ctx->nface && !free_) TRY(check_clearance(ctx));
   if (prefetch && ctx->gst) CK(cudaEventRecord(ctx->ev_gfree, ctx->st));
   if (moving && !take_prefetched(ctx)) TRY(rebuild_boxes(ctx));
   if (prefetch && !ctx->gst) {
@@ -1147,12 +1229,12 @@ lbm_status step_end(lbm_ctx *ctx, const StepState &ss) {
   CK(cudaStreamWaitEvent(ctx->st, ctx->ev_join, 0));
   ctx->cur = nxt;
   ctx->prev_local = false;
-  if (!ibm && moving)
+  if (!ibm && moving && !free_)
     for (auto &s : ctx->solids)
-      if (!(s.rho_p > 0))
-        for (int k = 0; k < 3; k++) s.c[k] += s.d.velocity[k];
-  // bounce-back: this step's momentum exchange moves the free solids
-  if (!ibm && free_) TRY(advance_free(ctx, ctx->slot));
+      for (int k = 0; k < 3; k++) s.c[k] += s.d.velocity[k];
+  // bounce-back: this step's momentum exchange moves the free solids (and
+  // the others with them, on the device)
+  if (!ibm && free_) TRY(motion_step(ctx, ctx->slot));
   if (prefetch) {
     // the next step's geometry: bounce-back uses the centres just reached,
     // IBM moves first and uses them plus one step
@@ -1523,6 +1605,7 @@ void lbm_destroy(lbm_ctx *ctx) {
 lbm_status lbm_add_solid(lbm_ctx *ctx, const lbm_solid_desc *solid, int *solid_id) {
   if (ctx) ctx->gen++;
   if (!ctx || !solid) return LBM_ERR_ARG;
+  TRY(solids_to_host(ctx, true));
   if ((int)ctx->solids.size() >= kMaxSolids) return fail(ctx, LBM_ERR_CAPACITY, "at most 8 solids");
   if (solid->kind != LBM_SPHERE && solid->kind != LBM_CYLINDER_Z)
     return fail(ctx, LBM_ERR_ARG, "unknown solid kind");
@@ -1546,6 +1629,7 @@ lbm_status lbm_set_solid_motion(lbm_ctx *ctx, int id, const double centre[3], co
                                 const double omega[3]) {
   if (ctx) ctx->gen++;
   if (!ctx || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
+  TRY(solids_to_host(ctx, true));
   SolidHost &h = ctx->solids[id];
   for (int a = 0; a < 3; a++) {
     if (centre) h.c[a] = h.d.centre[a] = centre[a];
@@ -1581,6 +1665,7 @@ lbm_status lbm_set_scheme(lbm_ctx *ctx, const lbm_scheme_desc *scheme) {
     return fail(ctx, LBM_ERR_STATE,
                 "select Eq. 16 before stepping, or after lbm_init_equilibrium / "
                 "lbm_set_distributions (its boundary state starts from a pre-collision state)");
+  TRY(solids_to_host(ctx, true));
   if (scheme->scheme == LBM_ZHAO_YONG && !ctx->zy_pre) {
     TRY(dalloc(ctx, &ctx->zy_pre, (size_t)ctx->Q * ctx->fs * ctx->tsz));
     CK(cudaMemsetAsync(ctx->zy_pre, 0, (size_t)ctx->Q * ctx->fs * ctx->tsz, ctx->st));
@@ -1834,6 +1919,7 @@ lbm_status lbm_get_residual(lbm_ctx *ctx, double *r) {
 lbm_status lbm_set_domain(lbm_ctx *ctx, const lbm_domain_desc *dom) {
   if (ctx) ctx->gen++;
   if (!ctx) return LBM_ERR_ARG;
+  TRY(solids_to_host(ctx, false));
   lbm_domain_desc d{};
   if (dom) d = *dom;
   const int len[3] = {ctx->d.nx, ctx->d.ny, ctx->D == 2 ? 1 : ctx->d.nz};
@@ -1913,6 +1999,7 @@ lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int id, double density_ratio,
   if (density_ratio > 0 && density_ratio <= 1.0 && ctx->scheme.scheme == LBM_IBM_DIRECT &&
       ctx->scheme.ibm_inertia == LBM_INERTIA_UHLMANN)
     return fail(ctx, LBM_ERR_ARG, "Eq. 22 needs a solid denser than the fluid");
+  TRY(solids_to_host(ctx, true));
   SolidHost &h = ctx->solids[id];
   h.rho_p = density_ratio > 0 ? density_ratio : 0;
   h.have_Ip = false;
@@ -1928,6 +2015,7 @@ lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int id, double density_ratio,
 
 lbm_status lbm_get_solid_velocity(lbm_ctx *ctx, int id, double U[3], double Om[3]) {
   if (!ctx || id < 0 || id >= (int)ctx->solids.size()) return LBM_ERR_ARG;
+  TRY(solids_to_host(ctx, false));
   for (int a = 0; a < 3; a++) {
     if (U) U[a] = ctx->solids[id].d.velocity[a];
     if (Om) Om[a] = ctx->solids[id].d.omega[a];
@@ -1937,6 +2025,7 @@ lbm_status lbm_get_solid_velocity(lbm_ctx *ctx, int id, double U[3], double Om[3
 
 lbm_status lbm_get_solid_centre(lbm_ctx *ctx, int id, double c[3]) {
   if (!ctx || id < 0 || id >= (int)ctx->solids.size() || !c) return LBM_ERR_ARG;
+  TRY(solids_to_host(ctx, false));
   memcpy(c, ctx->solids[id].c, 3 * sizeof(double));
   return LBM_OK;
 }
@@ -1997,6 +2086,7 @@ lbm_status lbm_save(lbm_ctx *ctx, void *host_buf, size_t *size) {
     return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints do not carry the Eq. 16 boundary state");
   if (ctx->outlet)
     return fail(ctx, LBM_ERR_UNSUPPORTED, "checkpoints do not carry the outflow face's state");
+  TRY(solids_to_host(ctx, false));
   const size_t fb = (size_t)ctx->Q * ctx->fs * ctx->ssz;
   const size_t total = sizeof(SaveHeader) + sizeof(SolidHost) * ctx->solids.size() + 2 * fb + ctx->N;
   if (!host_buf) {
@@ -2052,6 +2142,8 @@ lbm_status lbm_load(lbm_ctx *ctx, const void *host_buf, size_t size) {
   if (size < total) return fail(ctx, LBM_ERR_ARG, "checkpoint truncated");
   const char *p = (const char *)host_buf + sizeof(h);
   ctx->solids.assign((const SolidHost *)p, (const SolidHost *)p + h.nsolids);
+  ctx->host_stale = false;  // the saved state replaces the device copy
+  ctx->push_needed = true;
   p += sizeof(SolidHost) * h.nsolids;
   ctx->scheme = h.sch;
   ctx->cur = 0;
@@ -2151,6 +2243,10 @@ lbm_status lbm_sync(lbm_ctx *ctx) {
   int cnt[16];
   TRY(read_counts(ctx, cnt));
   if (cnt[3]) return fail(ctx, LBM_ERR_CAPACITY, "a boundary or refill list overflowed its capacity");
+  if (cnt[4])
+    return fail(ctx, LBM_ERR_UNSUPPORTED,
+                "a moving solid came too close to a non-periodic face (1.5 nodes from a wall or "
+                "stress-free face, R + 5 from an outflow face)");
   return LBM_OK;
 }
 
@@ -2263,7 +2359,14 @@ void drop_graph(lbm_batch *b) {
   b->exec = nullptr;
 }
 
-// Capture two steps of every active lattice with static geometry.
+// Whether a lattice's steps can be captured in the batch's graph: static
+// solids, or solids that move on the device (a free solid present).  Solids
+// with a prescribed motion move on the host, which prefetches their next
+// geometry: those lattices step directly.
+bool graphable(const lbm_ctx *c) { return !any_moving(c) || dev_motion(c); }
+
+// Capture two steps of every active lattice with static geometry or solids
+// moving on the device.
 lbm_status capture(lbm_batch *b) {
   drop_graph(b);
   const int n = (int)b->ctx.size();
@@ -2279,17 +2382,32 @@ lbm_status capture(lbm_batch *b) {
     long long step, launches, records;
   };
   std::vector<Saved> saved(n);
+  // the device copy of moving solids is sent before the capture (a push
+  // waits for its stream)
+  for (int i = 0; i < n; i++) {
+    lbm_ctx *c = b->ctx[i];
+    if (b->active[i] && graphable(c) && c->push_needed) {
+      const lbm_status s = motion_push(c);
+      if (s != LBM_OK) return bfail(b, s, lbm_last_error(c));
+    }
+  }
   BCK(cudaStreamBeginCapture(b->origin, cudaStreamCaptureModeThreadLocal));
   BCK(cudaEventRecord(b->ev_origin, b->origin));
   lbm_status st = LBM_OK;
   int members = 0;
   for (int i = 0; i < n && st == LBM_OK; i++) {
     lbm_ctx *c = b->ctx[i];
-    if (!b->active[i] || any_moving(c)) continue;
+    if (!b->active[i] || !graphable(c)) continue;
     saved[i] = {c->cur, c->slot, c->prev_local, c->timing, c->step, c->launches, c->records};
     c->timing = 0;
     b->graph_cur[i] = c->cur;
     b->graph_gen[i] = c->gen;
+    // a free solid under IBM moves by the record of the step before: in
+    // every replay after the first, that is the pair's second record, so
+    // the first step reads it there (the current record is copied there
+    // before the first replay, below)
+    if (c->scheme.scheme == LBM_IBM_DIRECT && dev_motion(c))
+      c->motion_slot = (c->slot + 2) % kHistCap;
     cudaStreamWaitEvent(c->st, b->ev_origin, 0);
     st = step_once(c);
     if (st == LBM_OK) st = step_once(c);
@@ -2304,6 +2422,10 @@ lbm_status capture(lbm_batch *b) {
   for (int i = 0; i < n; i++) {
     if (!b->in_graph[i]) continue;
     lbm_ctx *c = b->ctx[i];
+    c->motion_slot = -1;
+    if (c->scheme.scheme == LBM_IBM_DIRECT && dev_motion(c))
+      cudaMemcpyAsync(force_slot(c, (saved[i].slot + 2) % kHistCap), force_slot(c, saved[i].slot),
+                      sizeof(double) * kMaxSolids * 6, cudaMemcpyDeviceToDevice, c->st);
     b->pair_launches[i] = c->launches - saved[i].launches;
     b->graph_slot[i] = c->slot;  // after two captured steps
     c->cur = saved[i].cur;
@@ -2338,6 +2460,7 @@ void after_replay(lbm_batch *b) {
     lbm_ctx *c = b->ctx[i];
     c->slot = b->graph_slot[i];
     c->step += 2;
+    if (dev_motion(c)) c->host_stale = true;  // the replay moved the solids
     c->prev_local = false;
     c->records = std::min<long long>(c->records + 2, kHistCap);
     c->launches += b->pair_launches[i];
@@ -2348,7 +2471,7 @@ void after_replay(lbm_batch *b) {
 bool graph_valid(const lbm_batch *b) {
   if (!b->exec) return false;
   for (size_t i = 0; i < b->ctx.size(); i++) {
-    const bool want = b->active[i] && !any_moving(b->ctx[i]);
+    const bool want = b->active[i] && graphable(b->ctx[i]);
     if (want != (bool)b->in_graph[i]) return false;
     if (want && b->ctx[i]->cur != b->graph_cur[i]) return false;
     if (want && b->ctx[i]->gen != b->graph_gen[i]) return false;
@@ -2385,7 +2508,7 @@ lbm_status batch_advance(lbm_batch *b, int nsteps) {
   while (done < nsteps) {
     const bool pair = nsteps - done >= 2;
     bool any_static = false;
-    for (int i = 0; i < n; i++) any_static |= b->active[i] && !any_moving(b->ctx[i]);
+    for (int i = 0; i < n; i++) any_static |= b->active[i] && graphable(b->ctx[i]);
     if (pair && any_static) {
       if (!graph_valid(b)) {
         // the per-slot bookkeeping in after_replay assumes the capture-time
@@ -2408,7 +2531,7 @@ lbm_status batch_advance(lbm_batch *b, int nsteps) {
         b->graph_launches++;
         after_replay(b);
       }
-      // lattices outside the graph (moving solids) step directly
+      // lattices outside the graph (solids with a prescribed motion) step directly
       for (int i = 0; i < n; i++) {
         if (!b->active[i] || b->in_graph[i]) continue;
         for (int k = 0; k < 2; k++) {

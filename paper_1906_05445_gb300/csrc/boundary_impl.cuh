@@ -454,7 +454,7 @@ __device__ __forceinline__ void refill_node_warp(const KArgs &a, int t, int lane
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) cn += __shfl_xor_sync(0xffffffffu, cn, o);
   const double rho = cn ? rs / cn : 1.0;
-  const SolidDev &b = a.solids.s[sidx];
+  const SolidDev b = solid_of(a, sidx);
   double r[3] = {x - b.c[0], y - b.c[1], z - b.c[2]};
   r[0] -= a.nx * round(r[0] / a.nx);
   r[1] -= a.ny * round(r[1] / a.ny);
@@ -542,7 +542,7 @@ __global__ void __launch_bounds__(128) k_refill(const KArgs a) {
     cntn++;
   }
   const double rho = cntn ? rs / cntn : 1.0;
-  const SolidDev &b = a.solids.s[sidx];
+  const SolidDev b = solid_of(a, sidx);
   double r[3] = {x - b.c[0], y - b.c[1], z - b.c[2]};
   r[0] -= a.nx * round(r[0] / a.nx);
   r[1] -= a.ny * round(r[1] / a.ny);
@@ -845,10 +845,17 @@ __global__ void __launch_bounds__(256) k_kempe(const KArgs a) {
   const int bx = a.kbox[3], by = a.kbox[4], bz = a.kbox[5];
   double acc[6] = {0, 0, 0, 0, 0, 0};
   if (t < (long long)bx * by * bz) {
-    const int x = wrap(a.kbox[0] + (int)(t % bx), a.nx);
-    const int y = wrap(a.kbox[1] + (int)((t / bx) % by), a.ny);
-    const int z = wrap(a.kbox[2] + (int)(t / ((long long)bx * by)), a.nz);
-    const SolidDev &b = a.solids.s[a.kempe_solid];
+    const SolidDev b = solid_of(a, a.kempe_solid);
+    int o[3] = {a.kbox[0], a.kbox[1], a.kbox[2]};
+    if (a.kbox_dev) {
+      // every node with a cell corner inside lies within R + 1 of the centre
+      const int len[3] = {a.nx, a.ny, a.nz};
+      for (int c = 0; c < 3; c++)
+        if (a.kbox[3 + c] < len[c]) o[c] = (int)floor(b.c[c] - b.R - 1.0);
+    }
+    const int x = wrap(o[0] + (int)(t % bx), a.nx);
+    const int y = wrap(o[1] + (int)((t / bx) % by), a.ny);
+    const int z = wrap(o[2] + (int)(t / ((long long)bx * by)), a.nz);
     const bool flat = L::D == 2 || b.kind == LBM_CYLINDER_Z;
     double num = 0, den = 0;
     for (int c = 0; c < (L::D == 2 ? 4 : 8); c++) {

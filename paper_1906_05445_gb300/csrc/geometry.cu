@@ -59,9 +59,18 @@ __device__ __forceinline__ long long box_node(const GeomArgs &g, long long t,
   const int i = (int)(l % B.bx);
   const int j = (int)((l / B.bx) % B.by);
   const int k = (int)(l / ((long long)B.bx * B.by));
-  x = wrap(B.x0 + i, g.nx);
-  y = wrap(B.y0 + j, g.ny);
-  z = wrap(B.z0 + k, g.nz);
+  int x0 = B.x0, y0 = B.y0, z0 = B.z0;
+  if (g.box_dev) {
+    // anchored on the solid's centre in device memory
+    const SolidDev s = solid_of(g, b);
+    const double e = g.box_ext[b];
+    if (B.bx < g.nx) x0 = (int)floor(s.c[0] - e);
+    if (B.by < g.ny) y0 = (int)floor(s.c[1] - e);
+    if (B.bz < g.nz) z0 = (int)floor(s.c[2] - e);
+  }
+  x = wrap(x0 + i, g.nx);
+  y = wrap(y0 + j, g.ny);
+  z = wrap(z0 + k, g.nz);
   return x + (long long)g.nx * (y + (long long)g.ny * z);
 }
 
@@ -87,7 +96,7 @@ __global__ void k_geom_flags(const GeomArgs g, uint8_t *sid_new) {
   int s_in = 0;
   if (g.scheme != LBM_SCHEME_NONE)
     for (int s = 0; s < g.solids.n; s++)
-      if (inside(g, g.solids.s[s], x, y, z)) {
+      if (inside(g, solid_of(g, s), x, y, z)) {
         s_in = s + 1;
         break;
       }
@@ -104,8 +113,9 @@ __global__ void k_geom_flags(const GeomArgs g, uint8_t *sid_new) {
     for (int s = 0; s < g.solids.n; s++) {
       // | |r| - R_L | <= band_w, without the square root
       double r[3];
-      rel(g, g.solids.s[s], x, y, z, r);
-      const double r2 = norm2(r), RL = g.solids.s[s].RL;
+      const SolidDev b = solid_of(g, s);
+      rel(g, b, x, y, z, r);
+      const double r2 = norm2(r), RL = b.RL;
       const double lo = RL - g.band_w, hi = RL + g.band_w;
       if (r2 <= hi * hi && (lo <= 0 || r2 >= lo * lo)) fl |= FL_BAND;
     }
@@ -279,7 +289,7 @@ __global__ void __launch_bounds__(128) k_geom_links(const GeomArgs g, const uint
   const long long src = wrap(x - ex, g.nx) +
                         (long long)g.nx * (wrap(y - ey, g.ny) + (long long)g.ny * wrap(z - ez, g.nz));
   const int s = sid_new[src] - 1;
-  const SolidDev &b = g.solids.s[s];
+  const SolidDev b = solid_of(g, s);
   double r[3];
   rel(g, b, x, y, z, r);
   const bool flat = g.lattice == LBM_D2Q9 || b.kind == LBM_CYLINDER_Z;

@@ -48,7 +48,7 @@ struct Marker {
 __device__ __forceinline__ Marker marker(const IbmArgs &a, int m) {
   Marker k;
   k.s = a.msid[m];
-  const SolidDev &b = a.solids.s[k.s];
+  const SolidDev b = solid_of(a, k.s);
   const double dx = a.dir[m], dy = a.dir[a.nmark + m], dz = a.dir[2 * a.nmark + m];
   k.X[0] = b.c[0] + b.RL * dx;
   k.X[1] = b.c[1] + b.RL * dy;
@@ -148,7 +148,7 @@ __device__ __forceinline__ void interp_marker(const IbmArgs &a, int m, int lane,
 // desired velocity U + Omega x (X - c) of marker m minus the interpolated one
 __device__ __forceinline__ void direct_force(const IbmArgs &a, const Marker &k, const double U[3],
                                              double F[3]) {
-  const SolidDev &b = a.solids.s[k.s];
+  const SolidDev b = solid_of(a, k.s);
   const double Ud[3] = {b.U[0] + b.Om[1] * k.r[2] - b.Om[2] * k.r[1],
                         b.U[1] + b.Om[2] * k.r[0] - b.Om[0] * k.r[2],
                         b.U[2] + b.Om[0] * k.r[1] - b.Om[1] * k.r[0]};

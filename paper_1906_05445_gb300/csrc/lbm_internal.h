@@ -72,6 +72,9 @@ struct KArgs {
   const uint8_t *refill_sid;
   int refill_cap;
   SolidsDev solids;
+  // device copy of the solids, read instead of `solids` when it is set (free
+  // solids: their motion is integrated on the device)
+  const SolidsDev *solids_d;
   const uint8_t *sid;
   // query outputs (FP64); unused pointers are null
   double *out_rho, *out_u, *out_S, *out_stress, *out_f;
@@ -103,7 +106,17 @@ struct KArgs {
   double *kempe_out;
   int kempe_solid;
   int kbox[6];
+  int kbox_dev;  // the box origin is floor(c - R - 1) of the device copy's centre
 };
+
+#ifdef __CUDACC__
+// Solid s of a kernel's arguments: the device copy when there is one.
+template <typename A>
+__device__ __forceinline__ SolidDev solid_of(const A &a, int s) {
+  if (a.solids_d) return a.solids_d->s[s];
+  return a.solids.s[s];
+}
+#endif
 
 // kernel families timed by lbm_set_timing
 enum TimedKernel { TK_BULK = 0, TK_LIST = 1, TK_IBM = 2, TK_GEOM = 3, TK_COUNT = 4 };
@@ -176,6 +189,12 @@ struct GeomArgs {
   GeomBox box[kMaxSolids];
   int nbox;
   long long box_offset[kMaxSolids + 1];
+  // device copy of the solids (see KArgs) and, when box_dev is set, box k is
+  // anchored on solid k's centre there: origin floor(c - box_ext[k]) on the
+  // axes where its width is below the lattice's
+  const SolidsDev *solids_d;
+  int box_dev;
+  double box_ext[kMaxSolids];
 };
 void launch_geometry(const GeomArgs &g, int precision, cudaStream_t st);
 
@@ -197,6 +216,7 @@ struct IbmArgs {
   int4 *mk_base;      // [nmark] first stencil node (unwrapped x, y, z) and solid
   void *mk_wts;       // T [nmark][4^dim] delta weights of the stencil points
   int kernel;         // delta-function kernel (LBM_DELTA_*)
+  const SolidsDev *solids_d;  // device copy of the solids (see KArgs)
 };
 // stencil bases and weights of every marker (after each geometry change)
 void launch_ibm_prepare(const IbmArgs &a, int precision, cudaStream_t st);
@@ -216,6 +236,29 @@ struct UploadArgs {
   double inv_scale;      // storage scale^-1 (1 except FP16 storage)
 };
 void launch_upload_chunk(const UploadArgs &a, int precision, cudaStream_t st);
+
+// solid motion on the device (motion.cu).  Per solid: the density ratio
+// rho_p / rho_f (0: prescribed motion), gravity, the velocities of the
+// previous step (Eq. 23) and the inside fluid's momentum and angular
+// momentum of the previous step (Eq. 24).
+struct FreeDev {
+  double rho_p, g[3], Up[3], Omp[3], Ip[6];
+  int have_Ip;
+};
+enum MotionMode { MM_BOUNCE_BACK = 0, MM_IBM_FENG = 1, MM_IBM_KEMPE = 2, MM_IBM_UHLMANN = 3 };
+struct MotionArgs {
+  SolidsDev *now;       // the solids' current state, advanced in place
+  FreeDev *fr;          // [kMaxSolids]
+  const double *rec;    // force record of the step: [kMaxSolids][F, T]
+  const double *kempe;  // [kMaxSolids][6] inside-fluid integrals (MM_IBM_KEMPE)
+  int n, mode, dim, nz;
+  int face[6];          // domain face types (clearance of free solids)
+  int len[3];
+  int *err;             // set to 1 when a free solid comes too close to a non-periodic face
+};
+// One step of motion: free solids by Newton-Euler (Eq. 20 / 23 / 22 / 24),
+// the others by their prescribed velocity.
+void launch_motion(const MotionArgs &m, cudaStream_t st);
 
 // reductions (reduce.cu)
 void launch_residual(const double *u, const double *usnap, long long n,

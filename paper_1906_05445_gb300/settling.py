@@ -10,7 +10,9 @@ for each no-slip treatment and grid resolution:
   (bounce-back) or Eq. 23 / Eqs. 24-26 (IBM, Feng & Michaelides or Kempe);
 * the trajectory, velocities and angular velocity are sampled every 0.01 s
   in physical units; the summary gives the vertical velocity and the
-  lateral position at the end, relative to the finest resolution run.
+  lateral position at the end, relative to the finest resolution run;
+* the cylinder's motion is integrated on the device, so the steps between
+  samples replay as CUDA graphs (a one-lattice batch).
 
     python -m paper_1906_05445_gb300.settling [--diameters 10 15 20 30] [--time 1.0]
         [--schemes bouzidi_quad ibm ibm_rd0.4 ibm_rd0.4_kempe] [--out FILE]
@@ -56,15 +58,19 @@ def run_case(name: str, N: int, t_end: float, tau: float = 0.6, sample: float = 
     rows = []
     t0 = time.time()
     done = 0
+    # the solid moves on the device, so its steps replay as CUDA graphs of
+    # a one-lattice batch (two steps per launch); the samples read it back
+    b = lbm.Batch([g], autotune=False)
     while done < steps:
         k = min(every, steps - done)
-        g.step(k)
+        b.step(k)
         done += k
         c = g.solid_centre(sid)
         U, Om = g.solid_velocity(sid)
         rows.append([done * dt, (c[0] + 0.5) * dx, (c[1] + 0.5) * dx, U[0] * vel, U[1] * vel,
                      Om[2] * rot])
     secs = time.time() - t0
+    b.close()
     g.close()
     tr = np.array(rows)
     return {"scheme": name, "N": N, "nx": nx, "ny": ny, "dt": dt, "steps": steps,

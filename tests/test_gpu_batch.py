@@ -163,3 +163,62 @@ def test_server_admission_limits_and_errors(lbm):
     for _ in range(3):
         srv.submit(big)
     srv.close()
+
+
+def _free(p, rho, gravity, inertia=None):
+    return (p if inertia is None else p.with_(ibm_inertia=inertia)), rho, gravity
+
+
+def free_problems():
+    """Lattices whose solids move freely (their motion integrated on the
+    device, so they join the batch's graph) beside a static one."""
+    sphere = W.Problem("free_sphere", W.D3Q19, 30, 26, 24, 0.7, W.MRT, W.FP64, (4e-5, 0, 0),
+                       [W.Solid(W.SPHERE, (14.3, 12.6, 11.8), 4.4, velocity=(0.01, 0, 0))],
+                       W.BOUZIDI_QUAD, 0)
+    cyl = W.Problem("free_cylinder", W.D2Q9, 44, 40, 1, 0.7, W.BGK, W.FP64, (4e-5, 0, 0),
+                    [W.Solid(W.CYLINDER_Z, (20.3, 19.6, 0), 5.1, omega=(0, 0, 0.002))],
+                    W.IBM, 0)
+    return [_free(sphere, 1.5, (0.0, -4e-4, 2e-4)),
+            _free(cyl, 1.5, (0.0, -4e-4, 0.0), W.KEMPE),
+            _free(cyl.with_(name="free_cylinder_feng"), 2.0, (3e-4, -2e-4, 0.0), W.FENG)]
+
+
+def test_batch_with_free_solids_equals_alone(lbm):
+    """Free solids in a graph-captured batch: the fields, the centres and
+    the velocities equal those of the same lattices stepped alone."""
+    static = W.fixed_sphere(24, 3.1, seed=1, tau=0.7, g=2e-5, scheme=W.BOUZIDI_QUAD,
+                            precision=W.FP64)
+
+    def make():
+        lats = []
+        for p, rho, gravity in free_problems():
+            lt = lbm.Lattice.from_problem(p)
+            lt.set_solid_dynamics(0, rho, gravity)
+            lats.append(lt)
+        lats.append(lbm.Lattice.from_problem(static))
+        return lats
+
+    steps = 30
+    alone = make()
+    for lt in alone:
+        lt.step(steps)
+    mixed = make()
+    b = lbm.Batch(mixed, autotune=False)
+    b.step(steps)
+    assert b.info(0)[2] >= steps // 2 - 1          # replayed as graphs
+    for k, (a, m) in enumerate(zip(alone, mixed)):
+        ua, um = a.velocity(), m.velocity()
+        # the forces that move the free solids (and IBM's spreading) are FP64
+        # sums whose order across blocks varies from run to run
+        tol = 1e-13 if k < 3 else 0.0
+        assert rel_l2(um, ua) <= tol, k
+        assert m.info().steps == steps
+        if k < 3:
+            assert np.allclose(m.solid_centre(0), a.solid_centre(0), rtol=0, atol=1e-12)
+            (Ua, Oa), (Um, Om) = a.solid_velocity(0), m.solid_velocity(0)
+            assert np.allclose(Um, Ua, rtol=0, atol=1e-14 + 1e-11 * np.abs(Ua).max())
+            assert np.allclose(Om, Oa, rtol=0, atol=1e-14 + 1e-11 * np.abs(Oa).max())
+            assert np.linalg.norm(a.solid_centre(0) - np.array(free_problems()[k][0].solids[0].centre)) > 1e-3
+    b.close()
+    for lt in alone + mixed:
+        lt.close()

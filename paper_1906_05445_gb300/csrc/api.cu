@@ -175,12 +175,18 @@ struct lbm_ctx {
   cudaStream_t gst = nullptr;
   cudaEvent_t ev_geom = nullptr, ev_gfree = nullptr;
   // IBM
-  double *mk_dir = nullptr, *mk_dV = nullptr, *mk_F = nullptr;
+  double *mk_dir = nullptr, *mk_dV = nullptr, *mk_F = nullptr, *mk_dF = nullptr;
   uint8_t *mk_sid = nullptr;
   int4 *mk_base = nullptr;  // stencil table (rebuilt with the geometry)
   void *mk_wts = nullptr;
   bool markers_dirty = false;
   int nmark = 0;
+  int mk_start[kMaxSolids + 1] = {0};  // markers of solid k: mk_start[k] .. mk_start[k+1] - 1
+  // the forcing loop in one cluster per solid (see ibm.cu), taken with
+  // LBM_IBM_CLUSTER=1 where it fits the device (decided when the markers are
+  // built); off by default: it measured slower than the warp-per-marker
+  // kernels spread over every SM
+  bool ibm_cluster = false, ibm_cluster_on = false;
   void *u_band = nullptr, *f_ibm = nullptr;
   // forces
   double *hist = nullptr;
@@ -323,6 +329,7 @@ void resolve_timing(lbm_ctx *ctx) {
 
 bool any_free(const lbm_ctx *ctx);
 bool dev_motion(const lbm_ctx *ctx);
+bool ibm_cluster_args(const lbm_ctx *ctx, IbmClusterArgs &cl);
 
 // ---- kernel argument assembly
 SolidsDev solids_dev(const lbm_ctx *ctx, bool geometry_centres) {
@@ -811,10 +818,11 @@ lbm_status build_markers(lbm_ctx *ctx) {
   dfree(ctx, ctx->mk_dir);
   dfree(ctx, ctx->mk_dV);
   dfree(ctx, ctx->mk_F);
+  dfree(ctx, ctx->mk_dF);
   dfree(ctx, ctx->mk_sid);
   dfree(ctx, ctx->mk_base);
   dfree(ctx, ctx->mk_wts);
-  ctx->mk_dir = ctx->mk_dV = ctx->mk_F = nullptr;
+  ctx->mk_dir = ctx->mk_dV = ctx->mk_F = ctx->mk_dF = nullptr;
   ctx->mk_sid = nullptr;
   ctx->mk_base = nullptr;
   ctx->mk_wts = nullptr;
@@ -824,6 +832,7 @@ lbm_status build_markers(lbm_ctx *ctx) {
   std::vector<uint8_t> ms;
   const double dens = ctx->scheme.ibm_marker_density > 0 ? ctx->scheme.ibm_marker_density : 1.0;
   for (size_t k = 0; k < ctx->solids.size(); k++) {
+    ctx->mk_start[k] = (int)dx.size();
     const SolidHost &s = ctx->solids[k];
     const double rd = ctx->scheme.ibm_retraction;
     const double RL = s.d.fluid_inside ? s.d.radius + rd : s.d.radius - rd;
@@ -860,6 +869,7 @@ lbm_status build_markers(lbm_ctx *ctx) {
     }
   }
   const int n = (int)dx.size();
+  ctx->mk_start[ctx->solids.size()] = n;
   std::vector<double> dir(3 * (size_t)n);
   for (int m = 0; m < n; m++) {
     dir[m] = dx[m];
@@ -869,6 +879,7 @@ lbm_status build_markers(lbm_ctx *ctx) {
   TRY(dalloc(ctx, (void **)&ctx->mk_dir, sizeof(double) * 3 * n));
   TRY(dalloc(ctx, (void **)&ctx->mk_dV, sizeof(double) * n));
   TRY(dalloc(ctx, (void **)&ctx->mk_F, sizeof(double) * 3 * n));
+  TRY(dalloc(ctx, (void **)&ctx->mk_dF, sizeof(double) * 3 * n));
   TRY(dalloc(ctx, (void **)&ctx->mk_sid, n));
   TRY(dalloc(ctx, (void **)&ctx->mk_base, sizeof(int4) * n));
   TRY(dalloc(ctx, &ctx->mk_wts, ctx->tsz * (ctx->D == 3 ? 64 : 16) * (size_t)n));
@@ -943,6 +954,11 @@ lbm_status rebuild_full(lbm_ctx *ctx) {
   ctx->list_count = moving ? -1 : cnt[0];
   ctx->link_count = moving ? -1 : cnt[1];
   ibm_prepare(ctx);
+  {
+    IbmClusterArgs cl;
+    ctx->ibm_cluster = ctx->ibm_cluster_on && ibm_cluster_args(ctx, cl) &&
+                       ibm_cluster_fits(cl, ctx->d.precision);
+  }
   {
     std::vector<uint8_t> fl(ctx->N);
     CK(cudaMemcpyAsync(fl.data(), ctx->flags, ctx->N, cudaMemcpyDeviceToHost, ctx->st));
@@ -1081,6 +1097,65 @@ bool ibm_zeroes_record(const lbm_ctx *ctx) {
 
 // IBM: unforced velocity at the band, n_it interpolation/force iterations,
 // spreading, and the solid's force (into the given record slot).
+// whether [o1, o1 + w1) and [o2, o2 + w2) are disjoint on a periodic axis of n
+bool disjoint_mod(int o1, int w1, int o2, int w2, int n) {
+  if (w1 + w2 > n) return false;
+  const int d12 = ((o2 - o1) % n + n) % n, d21 = ((o1 - o2) % n + n) % n;
+  return d12 >= w1 && d21 >= w2;
+}
+
+// The cluster kernel's boxes: every stencil point of solid k's markers lies
+// within [floor(c - R_L) - 1, floor(c + R_L) + 2] per axis; the box is one
+// node wider on either side (a whole axis for a z-cylinder's rings or where
+// the box would reach round the lattice).
+// false where the kernel does not apply: no IBM solids, several solids whose
+// boxes may meet (their forcing loops would couple), or a free solid among
+// several (its box moves on the device).
+bool ibm_cluster_args(const lbm_ctx *ctx, IbmClusterArgs &cl) {
+  memset(&cl, 0, sizeof(cl));
+  const int ns = (int)ctx->solids.size();
+  if (ns < 1 || ctx->nmark == 0 || ctx->scheme.scheme != LBM_IBM_DIRECT) return false;
+  const bool dev = dev_motion(ctx);
+  if (dev && ns > 1) return false;
+  cl.ns = ns;
+  cl.dim = ctx->D;
+  cl.iters = std::max(1, ctx->scheme.ibm_iters);
+  cl.box_dev = dev ? 1 : 0;
+  const int n[3] = {ctx->d.nx, ctx->d.ny, ctx->D == 2 ? 1 : ctx->d.nz};
+  const int sax = ctx->D == 3 ? 2 : 1;
+  for (int k = 0; k <= ns; k++) cl.mk_start[k] = ctx->mk_start[k];
+  for (int k = 0; k < ns; k++) {
+    const SolidHost &h = ctx->solids[k];
+    const double rd = ctx->scheme.ibm_retraction;
+    const double RL = h.d.fluid_inside ? h.d.radius + rd : h.d.radius - rd;
+    IbmBox &B = cl.box[k];
+    // one node of slack on either side of the stencils' reach
+    B.ext = RL + 2.0;
+    for (int a = 0; a < 3; a++) {
+      const bool whole = a >= ctx->D || (a == 2 && h.d.kind == LBM_CYLINDER_Z);
+      const int w = (int)ceil(2.0 * RL) + 7;
+      if (whole || w >= n[a]) {
+        B.o[a] = 0;
+        B.w[a] = n[a];
+      } else {
+        B.o[a] = (int)floor(h.cg[a] - B.ext);
+        B.w[a] = w;
+      }
+    }
+    B.h = (B.w[sax] + kIbmClusterSize - 1) / kIbmClusterSize;
+    const int cnt = ctx->mk_start[k + 1] - ctx->mk_start[k];
+    B.mpc = (cnt + kIbmClusterSize - 1) / kIbmClusterSize;
+  }
+  for (int i = 0; i < ns; i++)
+    for (int j = i + 1; j < ns; j++) {
+      bool apart = false;
+      for (int a = 0; a < ctx->D && !apart; a++)
+        apart = disjoint_mod(cl.box[i].o[a], cl.box[i].w[a], cl.box[j].o[a], cl.box[j].w[a], n[a]);
+      if (!apart) return false;
+    }
+  return true;
+}
+
 void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStream_t s) {
   if (ctx->scheme.scheme != LBM_IBM_DIRECT || ctx->nmark == 0) return;
   Timed tm(ctx, TK_IBM, 0, s);
@@ -1092,6 +1167,12 @@ void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStr
   sweep(ctx, OP_BAND_VEL, a, s);
   IbmArgs ib = ibm_args(ctx, acc);
   const int iters = std::max(1, ctx->scheme.ibm_iters);
+  IbmClusterArgs cl;
+  if (ctx->ibm_cluster && ibm_cluster_args(ctx, cl)) {
+    launch_ibm_cluster(ib, cl, ctx->d.precision, s);
+    ctx->launches++;
+    return;
+  }
   if (iters == 1) {
     ib.first = 1;
     ib.reduce_force = 1;
@@ -1099,14 +1180,18 @@ void ibm_prepass(lbm_ctx *ctx, const void *src, bool local, double *acc, cudaStr
     ctx->launches++;
     return;
   }
-  for (int it = 0; it < iters; it++) {
-    ib.first = it == 0;
-    ib.use_f = it > 0;
+  // Eq. 9 iterations: the first is the fused pass; each later one
+  // interpolates u~ + f, adds rho0 (U^d - U) to the force, and spreads that
+  // increment onto f (the same sum as re-spreading the total force)
+  ib.first = 1;
+  ib.reduce_force = 0;
+  launch_ibm_fused(ib, ctx->d.precision, s);
+  ctx->launches++;
+  ib.dF = ctx->mk_dF;
+  for (int it = 1; it < iters; it++) {
+    ib.first = 0;
+    ib.use_f = 1;
     launch_ibm_interp(ib, ctx->d.precision, s);
-    if (it > 0) {
-      launch_zero_band(a, ctx->d.precision, s);
-      ctx->launches++;
-    }
     ib.reduce_force = it == iters - 1;
     launch_ibm_spread(ib, ctx->d.precision, s);
     ctx->launches += 2;
@@ -1528,6 +1613,7 @@ lbm_status lbm_create(lbm_ctx **out, const lbm_lattice_desc *desc, void *cuda_st
     if (const char *e = getenv("LBM_GEOM_PREFETCH")) ctx->geom_prefetch = atoi(e) != 0;
     if (const char *e = getenv("LBM_VEC_PACKED")) ctx->bulk_vec_packed = atoi(e);
     if (const char *e = getenv("LBM_IBM_LIST_THREAD")) ctx->ibm_list_thread = atoi(e) != 0;
+    if (const char *e = getenv("LBM_IBM_CLUSTER")) ctx->ibm_cluster_on = atoi(e) != 0;
     if (const char *e = getenv("LBM_IBB_LIST_THREAD")) ctx->ibb_list_thread = atoi(e) != 0;
     if (const char *e = getenv("LBM_MRT_GENERAL"))
       if (atoi(e) && ctx->coll_mode == CM_MRT_Q) ctx->coll_mode = CM_MRT;

@@ -217,14 +217,43 @@ struct IbmArgs {
   void *mk_wts;       // T [nmark][4^dim] delta weights of the stencil points
   int kernel;         // delta-function kernel (LBM_DELTA_*)
   const SolidsDev *solids_d;  // device copy of the solids (see KArgs)
+  double *dF;         // [3][nmark] the iteration's force increment, or null: the
+                      // interpolation stores it and the spreading adds it to the
+                      // force already spread (otherwise the total force is spread)
 };
+// The whole forcing loop of Sec. 2.1 (n_it iterations of interpolation,
+// direct force and spreading) for each solid in one thread-block cluster,
+// with the band fields of a box around the solid held in the cluster's
+// distributed shared memory (see ibm.cu).
+constexpr int kIbmClusterSize = 8;
+struct IbmBox {
+  int o[3];    // origin (unwrapped); recomputed from the device centre when box_dev
+  int w[3];    // widths (the lattice's on a full axis)
+  int h;       // planes per block along the slab axis (z in 3D, y in 2D)
+  int mpc;     // markers per block
+  double ext;  // floor(c - ext) is the origin when box_dev
+};
+struct IbmClusterArgs {
+  int ns;                       // solids, one cluster each
+  int mk_start[kMaxSolids + 1]; // markers of solid s: mk_start[s] .. mk_start[s+1] - 1
+  IbmBox box[kMaxSolids];
+  int iters;
+  int box_dev;
+  int dim;                      // 2 or 3: the slabs run along y or z
+};
+// Shared memory bytes per block of the cluster kernel for these boxes.
+size_t ibm_cluster_smem(const IbmClusterArgs &cl, int precision);
+// Whether clusters of these boxes can be placed on the device (sets the
+// kernel's shared-memory limit; not to be called during a stream capture).
+bool ibm_cluster_fits(const IbmClusterArgs &cl, int precision);
+void launch_ibm_cluster(const IbmArgs &a, const IbmClusterArgs &cl, int precision,
+                        cudaStream_t st);
 // stencil bases and weights of every marker (after each geometry change)
 void launch_ibm_prepare(const IbmArgs &a, int precision, cudaStream_t st);
 // interpolation, direct force and spreading in one pass (single iteration)
 void launch_ibm_fused(const IbmArgs &a, int precision, cudaStream_t st);
 void launch_ibm_interp(const IbmArgs &a, int precision, cudaStream_t st);
 void launch_ibm_spread(const IbmArgs &a, int precision, cudaStream_t st);
-void launch_zero_band(const KArgs &a, int precision, cudaStream_t st);
 
 // chunked upload of FP64 populations (transfer.cu)
 struct UploadArgs {

@@ -194,6 +194,21 @@ def pinned_bandwidth(device, nbytes=1 << 29):
     return out
 
 
+def stream_fork_join(main, streams):
+    """fork(): the other streams wait for the work queued on `main`;
+    join(): `main` waits for theirs."""
+    others = [s for s in streams if s is not main]
+
+    def fork():
+        for s in others:
+            s.wait_stream(main)
+
+    def join():
+        for s in others:
+            main.wait_stream(s)
+    return fork, join
+
+
 def dist_env():
     rank = int(os.environ.get("RANK", 0))
     world = int(os.environ.get("WORLD_SIZE", 1))
@@ -355,6 +370,12 @@ SERVE_CFG = dict(count=24, seed=11, rate_hz=40.0, min_2d=48, max_2d=160, min_3d=
 # a larger grid-convergence sweep, 32 lattices (edges 32..96), run on request
 BATCH_CFG_C4 = dict(count=32, r_min=4.0, r_max=12.0, tau=0.8, re_p=2.0, tol=1e-6,
                     check_every=500, max_steps=600000)
+# the whole grid-convergence set of 32 lattices R = 4..32 (edges 32..256,
+# 1.57e8 nodes): a fixed number of steps batched and one lattice at a time
+BATCH_CFG_FULL = dict(count=32, r_min=4.0, r_max=32.0, tau=0.6, re_p=5.0, steps=100)
+# a served stream reaching 512^2 / 96^3, run on request (--serve-config large)
+SERVE_CFG_LARGE = dict(count=16, seed=11, rate_hz=4.0, min_2d=128, max_2d=512, min_3d=48,
+                       max_3d=96, tau_range=(0.7, 1.0), tol=1e-5, check_every=200)
 
 
 def run_batch_leg(lbm, stream, c=None):
@@ -400,11 +421,55 @@ def run_batch_leg(lbm, stream, c=None):
                        "schemes": "even: bouzidi_quadratic, odd: ibm", "dtype": "f32"}}
 
 
-def run_serve_leg(stream):
+def run_batch_throughput(lbm, stream, device, c=None):
+    """The 32-lattice grid-convergence set at its full size, where the large
+    lattices make it bandwidth-bound: `steps` steps of every lattice as one
+    graph-replayed batch and one lattice after another, timed with CUDA
+    events.  Both do the same node updates, so the ratio of the two rates is
+    the ratio of solves/s over any number of steps."""
+    import torch
+    c = c or BATCH_CFG_FULL
+    ps = W.convergence_batch(c["count"], tau=c["tau"], re_p=c["re_p"], r_min=c["r_min"],
+                             r_max=c["r_max"])
+    units = sum(p.nodes for p in ps) * c["steps"]
+    lats = [lbm.Lattice.from_problem(p, stream=stream.cuda_stream) for p in ps]
+    for lt in lats:
+        lt.init_equilibrium()
+        lt.step(2)
+    e = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+    torch.cuda.synchronize(device)
+    e[0].record(stream)
+    for lt in lats:
+        lt.step(c["steps"])
+    e[1].record(stream)
+    torch.cuda.synchronize(device)
+    b = lbm.Batch(lats, stream=stream.cuda_stream, autotune=False)
+    b.step(2)
+    torch.cuda.synchronize(device)
+    e[2].record(stream)
+    b.step(c["steps"])
+    e[3].record(stream)
+    torch.cuda.synchronize(device)
+    b.close()
+    for lt in lats:
+        lt.close()
+    seq_s, bat_s = e[0].elapsed_time(e[1]) / 1e3, e[2].elapsed_time(e[3]) / 1e3
+    return {"metric": "batched MLUPS over the full grid-convergence set",
+            "value": units / bat_s / 1e6, "unit": UNIT, "sequential_value": units / seq_s / 1e6,
+            "speedup": seq_s / bat_s, "steps": c["steps"], "node_updates": units,
+            "config": {"lattices": len(ps), "edges": [ps[0].nx, ps[-1].nx],
+                       "radii": [ps[0].solids[0].radius, ps[-1].solids[0].radius],
+                       "nodes": sum(p.nodes for p in ps), "tau": c["tau"], "re_p": c["re_p"],
+                       "schemes": "even: bouzidi_quadratic, odd: ibm", "dtype": "f32",
+                       "reduction": "fixed steps, not to steady state: the largest lattices "
+                                    "relax over ~1e6 steps"}}
+
+
+def run_serve_leg(stream, c=None):
     """Poisson stream of mixed 2D Couette / 3D sphere solves (FP32, random
     tau and scheme): continuous batching vs one solve at a time."""
     from paper_1906_05445_gb300 import serve
-    c = SERVE_CFG
+    c = c or SERVE_CFG
     reqs = W.request_stream(count=c["count"], seed=c["seed"], rate_hz=c["rate_hz"],
                             min_2d=c["min_2d"], max_2d=c["max_2d"], min_3d=c["min_3d"],
                             max_3d=c["max_3d"], tau_range=c["tau_range"])
@@ -417,13 +482,15 @@ def run_serve_leg(stream):
             "config": {k: v for k, v in c.items()}}
 
 
-def storage_roofline(lbm, stream, device, precision, steps=ROOFLINE_STEPS):
+def storage_roofline(lbm, stream, device, precision, steps=ROOFLINE_STEPS, shared=False):
     """The two-lattice step with 16-bit storage: MLUPS over `steps` steps and
     the roofline of the bounce-back lattice's bulk sweep (76 B per node),
     every launch timed with CUDA events on its stream."""
     import torch
     problems = workload(precision)
-    lats = [lbm.Lattice.from_problem(p, stream=stream.cuda_stream) for p in problems]
+    lstreams = [stream if shared else torch.cuda.Stream(device) for _ in problems]
+    fork, join = stream_fork_join(stream, lstreams)
+    lats = [lbm.Lattice.from_problem(p, stream=s.cuda_stream) for p, s in zip(problems, lstreams)]
     for lt in lats:
         lt.init_equilibrium()
     for _ in range(5):
@@ -432,17 +499,17 @@ def storage_roofline(lbm, stream, device, precision, steps=ROOFLINE_STEPS):
     torch.cuda.synchronize(device)
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    fork()
     for _ in range(steps):
         for lt in lats:
             lt.step(1)
+    join()
     e1.record(stream)
     torch.cuda.synchronize(device)
     secs = e0.elapsed_time(e1) / 1e3
-    for lt in lats:
-        lt.set_timing(lbm.TIME_BULK, every=1)
+    lats[0].set_timing(lbm.TIME_BULK, every=1)
     for _ in range(steps):
-        for lt in lats:
-            lt.step(1)
+        lats[0].step(1)
     torch.cuda.synchronize(device)
     ms, nl, nodes = lats[0].kernel_time(lbm.TK_BULK)
     for lt in lats:
@@ -474,12 +541,19 @@ def run_ours(args, rank, world, local):
     precision = PRECISIONS[args.precision]
     problems = workload(precision, args.workload)
     stream = torch.cuda.current_stream(device)
-    lats = [lbm.Lattice.from_problem(p, stream=stream.cuda_stream) for p in problems]
+    # the lattices are independent: each steps on a stream of its own, so
+    # that one's boundary work, launch ramp and tail overlap the other's
+    # sweep (--lattice-streams shared: one after the other on one stream)
+    lstreams = [stream if args.lattice_streams == "shared" else torch.cuda.Stream(device)
+                for _ in problems]
+    fork, join = stream_fork_join(stream, lstreams)
+    lats = [lbm.Lattice.from_problem(p, stream=s.cuda_stream) for p, s in zip(problems, lstreams)]
     for lt in lats:
         lt.init_equilibrium()
     for _ in range(args.warmup):
         for lt in lats:
             lt.step(1)
+    torch.cuda.synchronize(device)
     # the timed region carries no kernel timing; the roofline's kernel (the
     # bulk sweep) is timed with CUDA events on its stream in a pass of its
     # own below, every launch (each pair of event records costs the step a
@@ -493,10 +567,14 @@ def run_ours(args, rank, world, local):
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
+    torch.cuda.nvtx.range_push("timed")  # lets a profiler take just these launches
+    fork()
     for _ in range(args.steps):
         for lt in lats:
             lt.step(1)
+    join()
     ev1.record(stream)
+    torch.cuda.nvtx.range_pop()
     torch.cuda.synchronize(device)
     barrier(world)
     clocks = sampler.stop()
@@ -507,12 +585,12 @@ def run_ours(args, rank, world, local):
     value = aggregate(units, max_secs, world)
 
     # dominant kernel: the bulk sweep of the bounce-back lattice, every
-    # launch of a pass of ROOFLINE_STEPS steps of the same two-lattice loop
-    for lt in lats:
-        lt.set_timing(lbm.TIME_BULK, every=1)
+    # launch of a pass of ROOFLINE_STEPS steps of that lattice alone (its
+    # boundary-node kernel beside it, as in the step; stepped alone, no other
+    # lattice's kernels share the HBM during the timed launch)
+    lats[0].set_timing(lbm.TIME_BULK, every=1)
     for _ in range(ROOFLINE_STEPS):
-        for lt in lats:
-            lt.step(1)
+        lats[0].step(1)
     torch.cuda.synchronize(device)
     ms, nl, nodes = lats[0].kernel_time(lbm.TK_BULK)
     bpn = BYTES_PER_NODE[precision]
@@ -556,13 +634,21 @@ def run_ours(args, rank, world, local):
 
     def e2e_pass():
         evs[0].record(stream)
-        for lt, hf in zip(lats, pinned_f):
+        # the uploads one after the other (two at once share the host link
+        # no faster and wrap each other's chunks)
+        prev = stream
+        for lt, hf, ls in zip(lats, pinned_f, lstreams):
+            ls.wait_stream(prev)
             lt.set_f_async(hf.numpy())
+            prev = ls
+        join()
         evs[1].record(stream)
+        fork()
         for k in range(e2e_steps):
             for i, lt in enumerate(lats):
                 lt.step(1)
                 lt.copy_force_torque_async(hFn[k, i])
+        join()
         evs[2].record(stream)
         for lt, u in zip(lats, hu):
             lt.velocity(out=u.numpy())  # straight into page-locked memory
@@ -610,12 +696,15 @@ def run_ours(args, rank, world, local):
     if rank == 0 and world == 1 and not args.no_lowp and args.workload == "fixed" and \
             precision == W.FP32:
         for name, prec in (("bf16", W.FP32_BF16), ("fp16", W.FP32_FP16)):
-            lowp[name] = storage_roofline(lbm, stream, device, prec)
-    batch = serve_leg = None
+            lowp[name] = storage_roofline(lbm, stream, device, prec,
+                                          shared=args.lattice_streams == "shared")
+    batch = serve_leg = batch_full = None
     if rank == 0 and world == 1 and not args.no_batch and args.workload == "fixed":
         batch = run_batch_leg(lbm, stream.cuda_stream,
                               BATCH_CFG_C4 if args.batch_config == "c4" else BATCH_CFG)
-        serve_leg = run_serve_leg(stream.cuda_stream)
+        batch_full = run_batch_throughput(lbm, stream, device)
+        serve_leg = run_serve_leg(stream.cuda_stream,
+                                  SERVE_CFG_LARGE if args.serve_config == "large" else SERVE_CFG)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
@@ -631,14 +720,22 @@ def run_ours(args, rank, world, local):
                              "bytes_per_node": bpn, "nodes_per_launch": nodes / max(nl, 1),
                              "launch_ms": ms / max(nl, 1), "timed_launches": int(nl),
                              "timed_sample": f"every bulk sweep of the bounce-back lattice in a "
-                                             f"{ROOFLINE_STEPS}-step pass of the same loop after "
-                                             f"the timed region",
+                                             f"{ROOFLINE_STEPS}-step pass of that lattice alone "
+                                             f"(its boundary-node kernel beside it) after the "
+                                             f"timed region",
                              "peak_kind": peak_kind + " hbm_gbs"},
                 "kernel_ms_per_step": kt,
+                "step_bandwidth": {"achieved": sum(p.nodes for p in problems) * bpn /
+                                   (max_secs / args.steps) / 1e9, "unit": "GB/s",
+                                   "frac": sum(p.nodes for p in problems) * bpn /
+                                   (max_secs / args.steps) / 1e9 / peak,
+                                   "what": "algorithmic bytes of every node update of both "
+                                           "lattices per step over the timed step time "
+                                           "(the lattices' sweeps overlap on their streams)"},
                 "roofline_bf16": lowp.get("bf16"), "roofline_fp16": lowp.get("fp16"),
                 "e2e": e2e, "cpu_baseline": cpu, "clocks": clocks,
                 "gpu_launches": int(launches) * world,
-                "batch": batch, "serve": serve_leg}
+                "batch": batch, "batch_full_set": batch_full, "serve": serve_leg}
         print(json.dumps(line), flush=True)
     for lt in lats:
         lt.close()
@@ -662,6 +759,11 @@ def main(argv=None):
                     help="batch leg: 8 lattices R 3..8 (default) or 32 lattices R 4..12")
     ap.add_argument("--no-batch", action="store_true",
                     help="skip the batched-solve and served-stream legs")
+    ap.add_argument("--serve-config", default="small", choices=["small", "large"],
+                    help="serve leg: 24 requests up to 160^2 / 48^3 (default) or 16 up to "
+                         "512^2 / 96^3")
+    ap.add_argument("--lattice-streams", default="own", choices=["own", "shared"],
+                    help="each lattice on a stream of its own (default) or all on one")
     ap.add_argument("--no-lowp", action="store_true",
                     help="skip the BF16 / FP16 storage roofline passes")
     args = ap.parse_args(argv)

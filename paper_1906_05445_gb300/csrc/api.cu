@@ -2294,7 +2294,7 @@ lbm_status lbm_get_velocity_noalloc(lbm_ctx *ctx, double *host_out, size_t n) {
                     ": use lbm_get_velocity");
   // rebuilding the geometry would allocate: the caller must have stepped or
   // queried the context since its last change
-  if (ctx->geom_dirty)
+  if (ctx->geom_dirty || (ctx->push_needed && dev_motion(ctx) && !ctx->sol_d))
     return fail(ctx, LBM_ERR_STATE,
                 "geometry changed since the last step: call lbm_step or lbm_sync first");
   int dev = -1;

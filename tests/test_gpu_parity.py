@@ -364,6 +364,32 @@ def test_checkpoint_split_run_equals_straight_run():
     assert np.allclose(c.force_torque(0)[0], a.force_torque(0)[0], rtol=1e-12, atol=1e-13)
 
 
+@pytest.mark.parametrize("scheme,inertia", [(W.BOUZIDI_QUAD, W.FENG), (W.IBM, W.KEMPE)])
+def test_checkpoint_of_a_free_solid(scheme, inertia):
+    """A free solid's state lives in device memory while it moves: a
+    checkpoint taken mid-run carries it (centre, velocities, the previous
+    step's velocities and Kempe's integrals), and the run continued from
+    it equals the straight run."""
+    p = _free_problem(3, scheme).with_(ibm_inertia=inertia)
+    gravity = (0.0, -4e-4, 2e-4)
+    a, b = make_gpu(p), make_gpu(p)
+    for g in (a, b):
+        g.set_solid_dynamics(0, 1.5, gravity)
+    a.step(30)
+    b.step(15)
+    blob = b.save()
+    c = make_gpu(p)
+    c.load(blob)
+    c.step(15)
+    assert rel_l2(c.velocity(), a.velocity()) < 1e-12
+    assert np.allclose(c.solid_centre(0), a.solid_centre(0), rtol=0, atol=1e-12)
+    (Ua, Oa), (Uc, Oc) = a.solid_velocity(0), c.solid_velocity(0)
+    assert np.allclose(Uc, Ua, rtol=0, atol=1e-14 + 1e-11 * np.abs(Ua).max())
+    assert np.allclose(Oc, Oa, rtol=0, atol=1e-14 + 1e-11 * np.abs(Oa).max())
+    for g in (a, b, c):
+        g.close()
+
+
 @pytest.mark.parametrize("prec", [W.FP32_BF16, W.FP32_FP16])
 def test_low_precision_storage_tracks_oracle(prec):
     """BF16 / FP16 storage with FP32 arithmetic: the error against the FP64

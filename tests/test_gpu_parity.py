@@ -233,17 +233,46 @@ def test_sphere_fp32(scheme):
     compare(g, o, FP32_U_TOL, tol_F=FP32_F_TOL)
 
 
-@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])
-def test_full_size_sphere_fp32(scheme):
-    """The 128^3 D3Q19 MRT sphere (R = 12, seeded offset) in the launch
-    configuration of the benchmark, a few steps from rest against the
-    oracle on every node."""
-    p = W.fixed_sphere(128, 12.0, seed=1906, scheme=scheme, precision=W.FP32,
-                       g=3.4e-5, steps=3)
-    g, o = make_gpu(p), make_oracle(p)
-    g.step(p.steps)
+def _full_size(scheme, precision):
+    # the benchmark's lattice, solid, tau and body force
+    return W.fixed_sphere(128, 12.0, seed=1906, scheme=scheme, precision=precision,
+                          g=3.4e-8, steps=20)
+
+
+def _oracle_fields(p):
+    """Velocity, drag and solid mask of the oracle after p.steps steps (a
+    picklable entry point for a process pool started with 'spawn')."""
+    o = make_oracle(p)
     o.step(p.steps)
-    compare(g, o, FP32_U_TOL, tol_F=FP32_F_TOL)
+    return o.velocity(), o.force_torque(0)[0], o.solid_mask()
+
+
+@pytest.fixture(scope="module")
+def full_size_oracle():
+    """The oracle's runs of the full-size sphere under both schemes, in two
+    processes started with 'spawn' (never forked from a process that holds
+    a CUDA context)."""
+    import multiprocessing as mp
+    schemes = (W.BOUZIDI_QUAD, W.IBM)
+    with mp.get_context("spawn").Pool(2) as pool:
+        res = pool.map(_oracle_fields, [_full_size(s, W.FP64) for s in schemes])
+    return dict(zip(schemes, res))
+
+
+@pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])
+def test_full_size_sphere_fp32(full_size_oracle, scheme):
+    """The 128^3 D3Q19 MRT sphere (R = 12, seeded offset) at the benchmark's
+    body force g = 3.4e-8 and tau = 0.6, in the launch configuration of the
+    benchmark, 20 steps from rest against the oracle on every node."""
+    p = _full_size(scheme, W.FP32)
+    u_o, F_o, mask = full_size_oracle[scheme]
+    g = make_gpu(p)
+    g.step(p.steps)
+    assert np.array_equal(g.solid_mask(), mask)
+    assert rel_l2(g.velocity(), u_o, mask) <= FP32_U_TOL
+    F_g = g.force_torque(0)[0]
+    assert np.linalg.norm(F_g - F_o) <= FP32_F_TOL * np.linalg.norm(F_o)
+    g.close()
 
 
 @pytest.mark.parametrize("scheme", [W.BOUZIDI_QUAD, W.IBM])

@@ -310,8 +310,12 @@ lbm_status lbm_get_force_torque(lbm_ctx *ctx, int solid_id, double F[3],
  * velocity.  Spheres have V = 4/3 pi R^3 and I = 2/5 m R^2; cylinders
  * V = pi R^2 (times nz in 3D) and I = 1/2 m R^2 about z, turning about z
  * only.  LBM_ERR_STATE without a bounce-back or IBM scheme;
- * LBM_ERR_UNSUPPORTED under LBM_ZHAO_YONG.  Each step of a lattice with a
- * free solid reads the force record back to the host (a wait per step). */
+ * LBM_ERR_UNSUPPORTED under LBM_ZHAO_YONG.  The solids' state then lives in
+ * device memory and a one-thread-per-solid kernel advances it at the end of
+ * every step, on the context's stream, with no read-back; the solid queries
+ * (velocity, centre, force) wait for that stream.  A solid that comes closer
+ * to a non-periodic face than lbm_set_domain allows is reported by the next
+ * lbm_sync as LBM_ERR_UNSUPPORTED. */
 lbm_status lbm_set_solid_dynamics(lbm_ctx *ctx, int solid_id, double density_ratio,
                                   const double gravity[3]);
 /* The solid's current velocity and angular velocity. */

@@ -48,7 +48,8 @@ typedef enum {
   LBM_ERR_CUDA = -3,        /* CUDA runtime error (message in last_error) */
   LBM_ERR_UNSUPPORTED = -4, /* valid but not implemented combination */
   LBM_ERR_STATE = -5,       /* call not valid in the current state */
-  LBM_ERR_TIMEOUT = -6,     /* a host-side wait ran out (lbm_server_wait); no kernel waits on a device flag */
+  LBM_ERR_TIMEOUT = -6,     /* a host-side wait ran out (lbm_server_wait), or a kernel's bounded
+                               wait for its own asynchronous copies gave up (lbm_sync) */
   LBM_ERR_DIVERGED = -7,    /* non-finite residual */
   LBM_ERR_CAPACITY = -8     /* a fixed-capacity device list overflowed */
 } lbm_status;
@@ -182,6 +183,9 @@ typedef struct {
   int64_t device_bytes;   /* device memory held */
   int32_t num_solids;
   int32_t precision;
+  int32_t bulk_kernel;    /* bulk sweep of the last single-lattice step: 0 one node
+                             per thread, 1 vectors of nodes per thread, 2 vectors fed
+                             by bulk copies of row segments; -1 before the first */
 } lbm_info;
 
 /* Create a lattice at rest (f = w_i, no solids, scheme NONE) on the current

@@ -51,6 +51,7 @@ void launch_sweep(SweepOp op, int lattice, int collision, int precision, const K
   default: launch_sweep_f16(op, lattice, collision, a, st); break;
   }
 }
+thread_local int g_bulk_kernel = BK_NODE;
 }  // namespace lbm
 
 using namespace lbm;
@@ -87,6 +88,7 @@ struct lbm_ctx {
   int list_block = 256;
   int cache_hints = 0;
   int bulk_mode = 1;
+  int bulk_kernel = -1;  // the bulk sweep kernel of the last step (BulkKernel), -1 none yet
   int bulk_vec_words = 0;
   int bulk_vec_packed = -1;
   int ibm_list_thread = 1;  // IBM band nodes: a thread per node in the boundary sweep
@@ -403,6 +405,7 @@ KArgs base_args(lbm_ctx *ctx) {
   a.list_link = ctx->list_link;
   a.list_cst = ctx->list_cst;
   a.counts = ctx->counts;
+  a.wait_err = ctx->counts + 5;
   a.list_cap = ctx->list_count >= 0 ? std::min(ctx->list_count, ctx->list_cap) : ctx->list_cap;
   a.links = ctx->links;
   a.f_ibm = ctx->f_ibm;
@@ -419,6 +422,7 @@ KArgs base_args(lbm_ctx *ctx) {
 
 void sweep(lbm_ctx *ctx, SweepOp op, const KArgs &a, cudaStream_t s) {
   launch_sweep(op, ctx->d.lattice, ctx->coll_mode, ctx->d.precision, a, s);
+  if (op == OP_BULK_SWEEP) ctx->bulk_kernel = g_bulk_kernel;
   ctx->launches++;
 }
 void sweep(lbm_ctx *ctx, SweepOp op, const KArgs &a) { sweep(ctx, op, a, ctx->st); }
@@ -2136,6 +2140,7 @@ lbm_status lbm_get_info(lbm_ctx *ctx, lbm_info *info) {
   info->device_bytes = (int64_t)ctx->dev_bytes;
   info->num_solids = (int)ctx->solids.size();
   info->precision = ctx->d.precision;
+  info->bulk_kernel = ctx->bulk_kernel;
   return LBM_OK;
 }
 
@@ -2333,6 +2338,9 @@ lbm_status lbm_sync(lbm_ctx *ctx) {
     return fail(ctx, LBM_ERR_UNSUPPORTED,
                 "a moving solid came too close to a non-periodic face (1.5 nodes from a wall or "
                 "stress-free face, R + 5 from an outflow face)");
+  if (cnt[5])
+    return fail(ctx, LBM_ERR_TIMEOUT,
+                "a bulk sweep gave up waiting (one second) for its asynchronous row copies");
   return LBM_OK;
 }
 

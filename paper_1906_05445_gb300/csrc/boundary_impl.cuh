@@ -6,6 +6,7 @@
 #pragma once
 
 #include "sweep_impl.cuh"
+#include "sweep_rows.cuh"
 #include "sweep_vec.cuh"
 
 namespace lbm {
@@ -925,6 +926,59 @@ bool launch_bulk_vec(const KArgs &a, int want, cudaStream_t st) {
   return launch_bulk_vec_w<LAT, CM, S, 2>(a, want, packed, st);
 }
 
+// The row-copy sweep (bulk_mode 2), built for the default vector shape of
+// the storage type only (2 words; node by node for FP32, packed pairs for
+// 16-bit storage).  The grid is the resident blocks of all SMs (queried per
+// device and shared-memory size), or fewer where the lattice has fewer
+// tiles.  Returns false where the lattice, its alignment or the requested
+// shape does not fit it.
+template <int LAT, int CM, typename S>
+bool launch_bulk_rows(const KArgs &a, cudaStream_t st) {
+  constexpr int W = 2;
+  constexpr int V = W * VecS<S>::per_word;
+  constexpr bool kPacked = sizeof(S) == 2;
+  const bool packed = a.bulk_vec_packed >= 0 ? a.bulk_vec_packed != 0 : kPacked;
+  if (a.bulk_vec_words == 4 || packed != kPacked || !a.wait_err) return false;
+  if (a.nx % (32 * V) != 0 || a.N / a.nx >= (1LL << 31) || (a.fs * (long long)sizeof(S)) % 16 != 0 ||
+      ((uintptr_t)a.src & 15) != 0 || ((uintptr_t)a.flags & 15) != 0)
+    return false;
+  // two blocks per SM
+  constexpr size_t kSmemLimit = 112 * 1024;
+  const RowTiles g = row_tiles<LAT, S, W>(a, kSmemLimit);
+  if (g.stage_bytes == 0) return false;
+  const size_t smem = 2 * (size_t)g.stage_bytes + 4 * sizeof(uint64_t);
+  auto kern = k_bulk_rows<LAT, CM, S, W, kPacked>;
+  constexpr int kMaxDev = 64;
+  struct Resident {
+    size_t smem;
+    int blocks;  // 0: not queried, -1: unusable
+  };
+  static Resident resident[kMaxDev];
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDev) return false;
+  Resident &r = resident[dev];
+  if (r.blocks == 0 || r.smem != smem) {
+    // the attribute calls are not stream work: allowed inside a capture
+    cudaStreamCaptureMode mode = cudaStreamCaptureModeRelaxed;
+    cudaThreadExchangeStreamCaptureMode(&mode);
+    int per_sm = 0, sms = 0;
+    const bool ok =
+        cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemLimit + 64) ==
+            cudaSuccess &&
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kRowBlock, smem) ==
+            cudaSuccess &&
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess;
+    cudaThreadExchangeStreamCaptureMode(&mode);
+    r.smem = smem;
+    r.blocks = ok && per_sm > 0 ? per_sm * sms : -1;
+  }
+  if (r.blocks < 0) return false;
+  const unsigned grid = (unsigned)std::min<long long>(r.blocks, g.ntiles);
+  if (grid == 0) return true;
+  kern<<<grid, kRowBlock, smem, st>>>(a, g);
+  return true;
+}
+
 template <int LAT, int CM, typename S, int W, bool PACKED>
 bool launch_group_w(const KArgs *as, int n, int want, cudaStream_t st) {
   constexpr int V = W * VecS<S>::per_word;
@@ -953,7 +1007,7 @@ bool launch_group_t(const KArgs *as, int n, cudaStream_t st) {
       if (as[k].bulk_mode != a0.bulk_mode || as[k].bulk_vec_words != a0.bulk_vec_words ||
           as[k].bulk_vec_packed != a0.bulk_vec_packed || as[k].bulk_block != a0.bulk_block)
         return false;
-    if (a0.bulk_mode != 1 || n < 1 || n > kMaxGroup) return false;
+    if (a0.bulk_mode < 1 || n < 1 || n > kMaxGroup) return false;
     // only the default vector shape of the storage type is built grouped (2
     // words; node by node for FP32, packed pairs for 16-bit storage): each
     // grouped variant inlines the update kMaxGroup times
@@ -986,8 +1040,12 @@ void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
   switch (op) {
   case OP_BULK_SWEEP:
     if constexpr (std::is_same<T, float>::value && CM != CM_MRT) {
-      if (a.bulk_mode == 1 && launch_bulk_vec<LAT, CM, S>(a, want, st)) break;
+      g_bulk_kernel = BK_ROWS;
+      if (a.bulk_mode == 2 && launch_bulk_rows<LAT, CM, S>(a, st)) break;
+      g_bulk_kernel = BK_VEC;
+      if (a.bulk_mode >= 1 && launch_bulk_vec<LAT, CM, S>(a, want, st)) break;
     }
+    g_bulk_kernel = BK_NODE;
     switch (a.cache_hints & 3) {
     case 1: k_bulk_sweep<LAT, CM, S, T, 1><<<div_up(a.N, want), want, 0, st>>>(a); break;
     case 2: k_bulk_sweep<LAT, CM, S, T, 2><<<div_up(a.N, want), want, 0, st>>>(a); break;

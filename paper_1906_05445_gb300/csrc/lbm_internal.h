@@ -85,11 +85,13 @@ struct KArgs {
   int list_block;    // threads per block of the boundary-node sweep (32, 64 or 128)
   int list_thread;   // boundary-node sweep: 1 = a thread per node (IBM band), 0 = a warp per node
   void *zy_pre;      // Eq. 16: T [Q][fs] pre-collision populations at the boundary nodes, or null
-  int bulk_mode;       // bulk sweep: 0 one node per thread, 1 vectors of nodes per thread
-                       // (where nx and the direction stride allow)
+  int bulk_mode;       // bulk sweep: 0 one node per thread, 1 vectors of nodes per thread,
+                       // 2 vectors fed by bulk copies of row segments (each where nx and
+                       // the direction stride allow, else the next simpler one)
   int bulk_vec_words;  // vector sweep: 32-bit words per thread and direction (2 or 4; 0 = 2)
   int bulk_vec_packed; // vector sweep: 1 packed FP32x2 collision of node pairs, 0 node by
                        // node, -1 by storage type
+  int *wait_err;       // set to 1 by a kernel whose wait for its asynchronous copies gave up
   // domain faces x-, x+, y-, y+, z-, z+ (LBM_FACE_*), their wall velocities,
   // the nodes next to a non-periodic face, and the outflow face's kept
   // populations and outward velocity (LT [Q + 1][out_area]; out_face -1: none)
@@ -160,6 +162,12 @@ bool launch_bulk_group(const KArgs *as, int n, int lattice, int collision, int p
 // sizes are chosen by the launcher; counts on the device bound list work.
 void launch_sweep(SweepOp op, int lattice, int collision, int precision,
                   const KArgs &a, cudaStream_t st);
+
+// The bulk sweep kernel the calling thread's last OP_BULK_SWEEP launch chose
+// (host side): 0 one node per thread, 1 vectors of nodes, 2 vectors fed by
+// row-segment copies.
+enum BulkKernel { BK_NODE = 0, BK_VEC = 1, BK_ROWS = 2 };
+extern thread_local int g_bulk_kernel;
 
 // geometry (geometry.cu)
 struct GeomBox {

@@ -280,26 +280,19 @@ template <int V> __device__ __forceinline__ void ld_flags(const uint8_t *p, uint
 }
 
 // ---------------------------------------------------------------- kernel
-// Thread t updates the vector of nodes [V t, V t + V).  A node is updated
-// when its flag byte has no bit but FL_NOG / FL_NEW; the other nodes of a
-// vector (boundary-list nodes, solid nodes) are loaded and computed but not
-// stored, since the boundary-node kernel writes them.  Every lane of the
-// warp calls this (threads past the end with t >= nt), for the shuffles.
+// The second half of a vector update: collide the V pulled nodes of a
+// thread (v, their flag bytes fl) and store the plain fluid ones at n0.  A
+// node is updated when its flag byte has no bit but FL_NOG / FL_NEW; the
+// other nodes of a vector (boundary-list nodes, solid nodes) are computed but
+// not stored, since the boundary-node kernel writes them.
 template <int LAT, int CM, typename S, int W, bool PACKED>
-__device__ __forceinline__ void bulk_vec_update(const KArgs &a, unsigned t, unsigned nt) {
+__device__ __forceinline__ void vec_collide_store(const KArgs &a, Words<W> (&v)[Lat<LAT>::Q],
+                                                  const uint32_t (&fl)[(W * VecS<S>::per_word + 3) / 4],
+                                                  unsigned n0, bool valid) {
   using L = Lat<LAT>;
   using VS = VecS<S>;
   constexpr int Q = L::Q, V = W * VS::per_word, NP = V / 2;
   static_assert(V % 2 == 0, "nodes are collided in pairs");
-  const bool valid = t < nt;
-  // threads past the end still take part in the lane shuffles (on node 0)
-  const unsigned n0 = valid ? t * V : 0u;
-  const unsigned yz = n0 / (unsigned)a.nx;
-  const int x0 = (int)(n0 - yz * (unsigned)a.nx);
-  const int z = (int)(yz / (unsigned)a.ny);
-  const int y = (int)(yz - (unsigned)z * (unsigned)a.ny);
-  uint32_t fl[(V + 3) / 4];
-  ld_flags<V>(a.flags + n0, fl);
   constexpr uint32_t kOther = (uint8_t)~(FL_NOG | FL_NEW);
   auto flag = [&](int k) { return (fl[k >> 2] >> (8 * (k & 3))) & 0xffu; };
   bool all = valid, any = false;
@@ -310,46 +303,6 @@ __device__ __forceinline__ void bulk_vec_update(const KArgs &a, unsigned t, unsi
     any = any || u;
   }
   any = any && valid;
-  const int nx = a.nx, ny = a.ny, nz = a.nz;
-  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
-  const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
-  // source rows (y - e_y, z - e_z)
-  const unsigned r[3][3] = {
-      {(unsigned)nx * (ym + (unsigned)ny * zm), (unsigned)nx * (y + (unsigned)ny * zm),
-       (unsigned)nx * (yp + (unsigned)ny * zm)},
-      {(unsigned)nx * (ym + (unsigned)ny * z), (unsigned)nx * (y + (unsigned)ny * z),
-       (unsigned)nx * (yp + (unsigned)ny * z)},
-      {(unsigned)nx * (ym + (unsigned)ny * zp), (unsigned)nx * (y + (unsigned)ny * zp),
-       (unsigned)nx * (yp + (unsigned)ny * zp)}};
-  const int lane = threadIdx.x & 31;
-  // the neighbour lane holds the adjacent vector of the same row
-  const bool lnb = lane != 0 && x0 != 0;
-  const bool rnb = lane != 31 && x0 + V != nx;
-  const int xl = x0 == 0 ? nx - 1 : x0 - 1, xr = x0 + V == nx ? 0 : x0 + V;
-  const S *src = (const S *)a.src;
-  Words<W> v[Q];
-  uint32_t edge[Q];
-  static_for<Q>([&](auto ic) {
-    constexpr int i = decltype(ic)::value;
-    const S *row = src + (long long)i * a.fs + r[1 - L::ez(i)][1 - L::ey(i)];
-    v[i] = ld_words<W>(row + x0);
-    edge[i] = 0u;
-    if constexpr (L::ex(i) == 1) {
-      if (!lnb) edge[i] = VS::left_word(row + xl);
-    } else if constexpr (L::ex(i) == -1) {
-      if (!rnb) edge[i] = VS::right_word(row + xr);
-    }
-  });
-  static_for<Q>([&](auto ic) {
-    constexpr int i = decltype(ic)::value;
-    if constexpr (L::ex(i) == 1) {
-      const uint32_t sw = __shfl_up_sync(0xffffffffu, v[i].w[W - 1], 1);
-      VS::shift_in_left(v[i], lnb ? sw : edge[i]);
-    } else if constexpr (L::ex(i) == -1) {
-      const uint32_t sw = __shfl_down_sync(0xffffffffu, v[i].w[0], 1);
-      VS::shift_in_right(v[i], rnb ? sw : edge[i]);
-    }
-  });
   const Coll<float> c = make_coll<LAT, float>(a);
   const float2 isc = bc2(a.inv_scale_f), sc = bc2(1.0f / a.inv_scale_f);
   const float gx = a.g_f[0], gy = a.g_f[1], gz = a.g_f[2];
@@ -401,6 +354,67 @@ __device__ __forceinline__ void bulk_vec_update(const KArgs &a, unsigned t, unsi
     }
   }
 }
+
+// Thread t updates the vector of nodes [V t, V t + V), pulling the shifted
+// rows straight from global memory.  Every lane of the warp calls this
+// (threads past the end with t >= nt), for the shuffles.
+template <int LAT, int CM, typename S, int W, bool PACKED>
+__device__ __forceinline__ void bulk_vec_update(const KArgs &a, unsigned t, unsigned nt) {
+  using L = Lat<LAT>;
+  using VS = VecS<S>;
+  constexpr int Q = L::Q, V = W * VS::per_word;
+  const bool valid = t < nt;
+  // threads past the end still take part in the lane shuffles (on node 0)
+  const unsigned n0 = valid ? t * V : 0u;
+  const unsigned yz = n0 / (unsigned)a.nx;
+  const int x0 = (int)(n0 - yz * (unsigned)a.nx);
+  const int z = (int)(yz / (unsigned)a.ny);
+  const int y = (int)(yz - (unsigned)z * (unsigned)a.ny);
+  uint32_t fl[(V + 3) / 4];
+  ld_flags<V>(a.flags + n0, fl);
+  const int nx = a.nx, ny = a.ny, nz = a.nz;
+  const int ym = y == 0 ? ny - 1 : y - 1, yp = y == ny - 1 ? 0 : y + 1;
+  const int zm = z == 0 ? nz - 1 : z - 1, zp = z == nz - 1 ? 0 : z + 1;
+  // source rows (y - e_y, z - e_z)
+  const unsigned r[3][3] = {
+      {(unsigned)nx * (ym + (unsigned)ny * zm), (unsigned)nx * (y + (unsigned)ny * zm),
+       (unsigned)nx * (yp + (unsigned)ny * zm)},
+      {(unsigned)nx * (ym + (unsigned)ny * z), (unsigned)nx * (y + (unsigned)ny * z),
+       (unsigned)nx * (yp + (unsigned)ny * z)},
+      {(unsigned)nx * (ym + (unsigned)ny * zp), (unsigned)nx * (y + (unsigned)ny * zp),
+       (unsigned)nx * (yp + (unsigned)ny * zp)}};
+  const int lane = threadIdx.x & 31;
+  // the neighbour lane holds the adjacent vector of the same row
+  const bool lnb = lane != 0 && x0 != 0;
+  const bool rnb = lane != 31 && x0 + V != nx;
+  const int xl = x0 == 0 ? nx - 1 : x0 - 1, xr = x0 + V == nx ? 0 : x0 + V;
+  const S *src = (const S *)a.src;
+  Words<W> v[Q];
+  uint32_t edge[Q];
+  static_for<Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    const S *row = src + (long long)i * a.fs + r[1 - L::ez(i)][1 - L::ey(i)];
+    v[i] = ld_words<W>(row + x0);
+    edge[i] = 0u;
+    if constexpr (L::ex(i) == 1) {
+      if (!lnb) edge[i] = VS::left_word(row + xl);
+    } else if constexpr (L::ex(i) == -1) {
+      if (!rnb) edge[i] = VS::right_word(row + xr);
+    }
+  });
+  static_for<Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    if constexpr (L::ex(i) == 1) {
+      const uint32_t sw = __shfl_up_sync(0xffffffffu, v[i].w[W - 1], 1);
+      VS::shift_in_left(v[i], lnb ? sw : edge[i]);
+    } else if constexpr (L::ex(i) == -1) {
+      const uint32_t sw = __shfl_down_sync(0xffffffffu, v[i].w[0], 1);
+      VS::shift_in_right(v[i], rnb ? sw : edge[i]);
+    }
+  });
+  vec_collide_store<LAT, CM, S, W, PACKED>(a, v, fl, n0, valid);
+}
+
 
 // One thread per vector.  (A persistent grid walking the lattice measured
 // slower: it holds more registers and leaves the boundary kernels less room;

@@ -83,7 +83,8 @@ class lbm_info(C.Structure):
                 ("list_nodes", C.c_int64), ("cut_links", C.c_int64),
                 ("markers", C.c_int64), ("steps", C.c_int64),
                 ("kernel_launches", C.c_int64), ("device_bytes", C.c_int64),
-                ("num_solids", C.c_int32), ("precision", C.c_int32)]
+                ("num_solids", C.c_int32), ("precision", C.c_int32),
+                ("bulk_kernel", C.c_int32)]
 
 
 def _load():

@@ -59,7 +59,7 @@ using namespace lbm;
 namespace {
 
 constexpr int kHistCap = 4096;          // force records kept (steps)
-constexpr double kFp16Scale = 1024.0;   // FP16 storage keeps (f - w) * 2^10
+constexpr double kFp16Scale = (double)(1 << kFp16ScaleLog2);  // FP16 storage keeps (f - w) * 2^10
 constexpr int kGeomMargin = 7;          // box margin around a moving solid
 
 struct SolidHost {

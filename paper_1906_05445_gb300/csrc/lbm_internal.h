@@ -37,6 +37,9 @@ struct LinkArrays {
   uint8_t *sid;
 };
 
+// FP16 storage keeps (f - w_i) * 2^kFp16ScaleLog2.
+constexpr int kFp16ScaleLog2 = 10;
+
 // Arguments of every sweep-like kernel (passed by value).
 struct KArgs {
   // lattice

@@ -73,13 +73,20 @@ __device__ __forceinline__ float2 qdot2(const float2 (&v)[3]) {
 //   f_j* = (1 - omega) f_j + omega (S - A) + (1 - omega/2)(SF - AF),
 // and the q-moment correction (omega - s_q) m_q M_q,i / |M_q|^2 with m_q the
 // q moments of Delta + Fbar/2, which only involve f_i - f_j - 2A + AF.
-template <int LAT, int CM>
+// With SL > 0 the populations and the force come in units of 2^-SL (FP16
+// storage's scaled deviations) and the results go out in them: everything
+// but the terms quadratic in u and F is linear, and those take their
+// constants times 2^-SL.  Every operation then gives 2^SL times its unscaled
+// result exactly (power-of-two scaling commutes with rounding), so the
+// stored values equal those of colliding the unscaled deviations.
+template <int LAT, int CM, int SL = 0>
 __device__ __forceinline__ void collide_x2(float2 (&f)[Lat<LAT>::Q], float2 Fx, float2 Fy,
                                            float2 Fz, const Coll<float> &c) {
   using L = Lat<LAT>;
   constexpr int Q = L::Q;
   static_assert(CM != CM_MRT, "general MRT rates run in the one-node kernel");
   constexpr float wa = (float)L::w(1), wb = (float)L::w(Q - 1);
+  constexpr float kInv = 1.0f / (float)(1 << SL);  // exact
   float2 drho = f[0];
   float2 jx = bc2(0.f), jy = bc2(0.f), jz = bc2(0.f);
   static_for<Q>([&](auto ic) {
@@ -101,14 +108,15 @@ __device__ __forceinline__ void collide_x2(float2 (&f)[Lat<LAT>::Q], float2 Fx, 
   const float2 ux = fma2(half, Fx, jx), uy = fma2(half, Fy, jy), uz = fma2(half, Fz, jz);
   const float2 uu = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
   const float2 uF = fma2(uz, Fz, fma2(uy, Fy, mul2(ux, Fx)));
-  const float2 base = fma2(bc2(-1.5f), uu, drho);
+  const float2 base = fma2(bc2(-1.5f * kInv), uu, drho);
   const float2 om = bc2(c.omega), omc = bc2(c.omc), cf = bc2(c.cforce);
   // w base and -3 w u.F for the two weight classes of the moving directions
   const float2 wbase_a = mul2(bc2(wa), base), wbase_b = mul2(bc2(wb), base);
-  const float2 wuF_a = mul2(bc2(-3.f * wa), uF), wuF_b = mul2(bc2(-3.f * wb), uF);
+  // (-3 w rounded to float) times 2^-SL
+  const float2 wuF_a = mul2(bc2(-3.f * wa * kInv), uF), wuF_b = mul2(bc2(-3.f * wb * kInv), uF);
   {
     constexpr float w0 = (float)L::w(0);
-    const float2 S = mul2(bc2(w0), base), SF = mul2(bc2(-3.f * w0), uF);
+    const float2 S = mul2(bc2(w0), base), SF = mul2(bc2(-3.f * w0 * kInv), uF);
     f[0] = fma2(omc, f[0], fma2(om, S, mul2(cf, SF)));
   }
   float2 mq[3] = {bc2(0.f), bc2(0.f), bc2(0.f)};
@@ -121,8 +129,8 @@ __device__ __forceinline__ void collide_x2(float2 (&f)[Lat<LAT>::Q], float2 Fx, 
       const float2 eu = edot2<LAT, i>(ux, uy, uz);
       const float2 eF = edot2<LAT, i>(Fx, Fy, Fz);
       const float2 A = mul2(bc2(w3), eu);
-      const float2 S = fma2(A, mul2(bc2(1.5f), eu), ca ? wbase_a : wbase_b);
-      const float2 SF = fma2(A, mul2(bc2(3.f), eF), ca ? wuF_a : wuF_b);
+      const float2 S = fma2(A, mul2(bc2(1.5f * kInv), eu), ca ? wbase_a : wbase_b);
+      const float2 SF = fma2(A, mul2(bc2(3.f * kInv), eF), ca ? wuF_a : wuF_b);
       const float2 AF = mul2(bc2(w3), eF);
       const float2 P = fma2(om, S, mul2(cf, SF));
       const float2 M = fma2(om, A, mul2(cf, AF));
@@ -190,6 +198,7 @@ __device__ __forceinline__ uint32_t join16(uint32_t a, uint32_t b) {
 template <typename S> struct VecS;
 template <> struct VecS<float> {
   static constexpr int per_word = 1;
+  static constexpr int kScaleLog2 = 0;  // stored values are the deviations
   // the end node fetched from outside the vector, as the word the shift
   // below expects
   __device__ static uint32_t left_word(const float *p) { return __float_as_uint(__ldg(p)); }
@@ -220,6 +229,7 @@ template <> struct VecS<float> {
 
 template <typename H> struct VecS16 {
   static constexpr int per_word = 2;
+  static constexpr int kScaleLog2 = 0;
   __device__ static uint32_t ld16(const H *p) {
     return (uint32_t)__ldg(reinterpret_cast<const unsigned short *>(p));
   }
@@ -253,16 +263,24 @@ template <> struct VecS<__nv_bfloat16> : VecS16<__nv_bfloat16> {
   }
 };
 
-// FP16 holds deviations times 2^k: get multiplies by inv_scale = 2^-k, put
-// by scale = 2^k (both exact)
+// FP16 holds deviations times 2^k (k = kFp16ScaleLog2): get multiplies by
+// inv_scale = 2^-k, put by scale = 2^k (both exact); get_scaled / put_scaled
+// keep the scaled units, for the packed collision that works in them
 template <> struct VecS<__half> : VecS16<__half> {
-  template <int W> __device__ static float2 get(const Words<W> &v, int p, float2 inv_scale) {
+  static constexpr int kScaleLog2 = kFp16ScaleLog2;
+  template <int W> __device__ static float2 get_scaled(const Words<W> &v, int p) {
     const uint32_t w = v.w[p];
-    return mul2(__half22float2(*reinterpret_cast<const __half2 *>(&w)), inv_scale);
+    return __half22float2(*reinterpret_cast<const __half2 *>(&w));
+  }
+  template <int W> __device__ static void put_scaled(Words<W> &v, int p, float2 f) {
+    const __half2 h = __float22half2_rn(f);
+    v.w[p] = *reinterpret_cast<const uint32_t *>(&h);
+  }
+  template <int W> __device__ static float2 get(const Words<W> &v, int p, float2 inv_scale) {
+    return mul2(get_scaled(v, p), inv_scale);
   }
   template <int W> __device__ static void put(Words<W> &v, int p, float2 f, float2 scale) {
-    const __half2 h = __float22half2_rn(mul2(f, scale));
-    v.w[p] = *reinterpret_cast<const uint32_t *>(&h);
+    put_scaled(v, p, mul2(f, scale));
   }
 };
 
@@ -304,20 +322,25 @@ __device__ __forceinline__ void vec_collide_store(const KArgs &a, Words<W> (&v)[
   }
   any = any && valid;
   const Coll<float> c = make_coll<LAT, float>(a);
+  // the packed collision of FP16 storage runs in its scaled units (the host
+  // sets a.inv_scale_f = 2^-SL for it); the rest unscale on load
+  constexpr int SL = PACKED ? VS::kScaleLog2 : 0;
   const float2 isc = bc2(a.inv_scale_f), sc = bc2(1.0f / a.inv_scale_f);
-  const float gx = a.g_f[0], gy = a.g_f[1], gz = a.g_f[2];
+  constexpr float kF = (float)(1 << SL);  // force in the same units (exact)
+  const float gx = a.g_f[0] * kF, gy = a.g_f[1] * kF, gz = a.g_f[2] * kF;
   static_for<NP>([&](auto pc) {
     constexpr int p = decltype(pc)::value;
     float2 f[Q];
     static_for<Q>([&](auto ic) {
       constexpr int i = decltype(ic)::value;
-      f[i] = VS::get(v[i], p, isc);
+      if constexpr (SL != 0) f[i] = VS::get_scaled(v[i], p);
+      else f[i] = VS::get(v[i], p, isc);
     });
     const float g0 = (flag(2 * p) & FL_NOG) ? 0.f : 1.f;
     const float g1 = (flag(2 * p + 1) & FL_NOG) ? 0.f : 1.f;
     if constexpr (PACKED) {
-      collide_x2<LAT, CM>(f, make_float2(g0 * gx, g1 * gx), make_float2(g0 * gy, g1 * gy),
-                          make_float2(g0 * gz, g1 * gz), c);
+      collide_x2<LAT, CM, SL>(f, make_float2(g0 * gx, g1 * gx), make_float2(g0 * gy, g1 * gy),
+                              make_float2(g0 * gz, g1 * gz), c);
     } else {
       float fa[Q], fb[Q];
       static_for<Q>([&](auto ic) {
@@ -334,7 +357,8 @@ __device__ __forceinline__ void vec_collide_store(const KArgs &a, Words<W> (&v)[
     }
     static_for<Q>([&](auto ic) {
       constexpr int i = decltype(ic)::value;
-      VS::put(v[i], p, f[i], sc);
+      if constexpr (SL != 0) VS::put_scaled(v[i], p, f[i]);
+      else VS::put(v[i], p, f[i], sc);
     });
   });
   S *dst = (S *)a.dst;

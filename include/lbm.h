@@ -290,6 +290,16 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, int check_every,
  * dissipation rate epsilon = 2 nu s_ij s_ij (Sec. 3.1) [nodes]. */
 lbm_status lbm_get_density(lbm_ctx *ctx, double *host_out, size_t n);
 lbm_status lbm_get_velocity(lbm_ctx *ctx, double *host_out, size_t n);
+/* The velocity field of lbm_get_velocity, copied to host_out without
+ * waiting: the query and its copy are enqueued on the context's stream after
+ * the work already there, and the call returns; lbm_sync waits for them.
+ * host_out (d * nodes doubles, as lbm_get_velocity) must stay valid and
+ * unread until then, and should be page-locked (e.g. cudaHostAlloc) for the
+ * copy to be asynchronous.  Later steps and queries of the context are
+ * ordered after the copy, so queries of several contexts on their own
+ * streams overlap.  The first query of a context allocates its staging
+ * buffer (and waits for the stream); errors as lbm_get_velocity. */
+lbm_status lbm_get_velocity_async(lbm_ctx *ctx, double *host_out, size_t n);
 lbm_status lbm_get_strain_rate(lbm_ctx *ctx, double *host_out, size_t n);
 lbm_status lbm_get_stress(lbm_ctx *ctx, double *host_out, size_t n);
 lbm_status lbm_get_dissipation(lbm_ctx *ctx, double *host_out, size_t n);

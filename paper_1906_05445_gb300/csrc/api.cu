@@ -1433,7 +1433,9 @@ void run_query(lbm_ctx *ctx, KArgs a) {
 
 enum QueryKind { Q_RHO, Q_U, Q_S, Q_STRESS, Q_F, Q_EPS };
 
-lbm_status query(lbm_ctx *ctx, QueryKind kind, double *host, size_t n) {
+// The field into host memory: enqueued on the context's stream, then (wait)
+// waited for.
+lbm_status query(lbm_ctx *ctx, QueryKind kind, double *host, size_t n, bool wait = true) {
   if (!ctx) return LBM_ERR_ARG;
   const int nc = ctx->D == 2 ? 3 : 6;
   size_t comps = (kind == Q_RHO || kind == Q_EPS) ? 1 : kind == Q_U ? ctx->D : kind == Q_F ? ctx->Q : nc;
@@ -1453,7 +1455,7 @@ lbm_status query(lbm_ctx *ctx, QueryKind kind, double *host, size_t n) {
   }
   run_query(ctx, a);
   CK(cudaMemcpyAsync(host, ctx->qbuf, need * sizeof(double), cudaMemcpyDeviceToHost, ctx->st));
-  CK(cudaStreamSynchronize(ctx->st));
+  if (wait) CK(cudaStreamSynchronize(ctx->st));
   CK(cudaGetLastError());
   return LBM_OK;
 }
@@ -1941,6 +1943,9 @@ lbm_status lbm_run_to_steady(lbm_ctx *ctx, double tol, int check_every, int max_
 
 lbm_status lbm_get_density(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_RHO, o, n); }
 lbm_status lbm_get_velocity(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_U, o, n); }
+lbm_status lbm_get_velocity_async(lbm_ctx *ctx, double *o, size_t n) {
+  return query(ctx, Q_U, o, n, false);
+}
 lbm_status lbm_get_strain_rate(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_S, o, n); }
 lbm_status lbm_get_stress(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_STRESS, o, n); }
 lbm_status lbm_get_dissipation(lbm_ctx *ctx, double *o, size_t n) { return query(ctx, Q_EPS, o, n); }

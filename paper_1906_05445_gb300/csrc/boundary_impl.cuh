@@ -125,6 +125,38 @@ __global__ void __launch_bounds__(512) k_bulk_query(const KArgs a) {
   write_fields<LAT, double>(a, n, f, gon * a.g[0], gon * a.g[1], gon * a.g[2]);
 }
 
+// Density and velocity only, for FP32 and 16-bit storage: the same moments
+// as write_fields (u = sum e_i d_i + F / 2, rho = 1 + sum d_i) summed in FP32
+// arithmetic over the stored values, written as FP64.  GB300's FP64 rate
+// makes the FP64 sums the query's bound; in FP32 they differ from them by
+// about the FP32 rounding of the sums (1e-7 of the largest term), well
+// inside the storage's own error.
+template <int LAT, typename S>
+__global__ void __launch_bounds__(512) k_bulk_query_u(const KArgs a) {
+  using L = Lat<LAT>;
+  constexpr int Q = L::Q, D = L::D;
+  const int x = blockIdx.x * blockDim.x + threadIdx.x;
+  const int y = blockIdx.y, z = blockIdx.z;
+  if (x >= a.nx) return;
+  const long long n = x + (long long)a.nx * (y + (long long)a.ny * z);
+  const uint8_t fl = a.flags[n];
+  if (fl & (uint8_t)~(FL_NOG | FL_NEW)) return;
+  float f[Q];
+  gather_pull<LAT, S, float>((const S *)a.src, a.fs, x, y, z, a.nx, a.ny, a.nz, a.inv_scale_f, f);
+  float drho = 0.f, j[3] = {0.f, 0.f, 0.f};
+  static_for<Q>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    drho += f[i];
+    if constexpr (L::ex(i) != 0) j[0] += L::ex(i) > 0 ? f[i] : -f[i];
+    if constexpr (L::ey(i) != 0) j[1] += L::ey(i) > 0 ? f[i] : -f[i];
+    if constexpr (L::ez(i) != 0) j[2] += L::ez(i) > 0 ? f[i] : -f[i];
+  });
+  const float gon = (fl & FL_NOG) ? 0.f : 1.f;
+  if (a.out_rho) a.out_rho[n] = 1.0 + (double)drho;
+  if (a.out_u)
+    for (int c = 0; c < D; c++) a.out_u[c * a.N + n] = (double)(j[c] + 0.5f * (gon * a.g_f[c]));
+}
+
 // Warp-sum of a double.
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -1054,6 +1086,12 @@ void launch_one(SweepOp op, const KArgs &a, cudaStream_t st) {
     }
     break;
   case OP_BULK_QUERY:
+    if constexpr (std::is_same<T, float>::value) {
+      if (!a.out_S && !a.out_stress && !a.out_eps && !a.out_f) {
+        k_bulk_query_u<LAT, S><<<gbulk, bx, 0, st>>>(a);
+        break;
+      }
+    }
     k_bulk_query<LAT, S><<<gbulk, bx, 0, st>>>(a);
     break;
   case OP_LIST_SWEEP:

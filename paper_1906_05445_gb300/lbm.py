@@ -109,6 +109,7 @@ def _load():
         "lbm_run_to_steady": (st, [vp, d, i, i, C.POINTER(i), dp]),
         "lbm_get_density": (st, [vp, dp, sz]),
         "lbm_get_velocity": (st, [vp, dp, sz]),
+        "lbm_get_velocity_async": (st, [vp, dp, sz]),
         "lbm_get_strain_rate": (st, [vp, dp, sz]),
         "lbm_get_stress": (st, [vp, dp, sz]),
         "lbm_get_dissipation": (st, [vp, dp, sz]),
@@ -160,8 +161,8 @@ globals().update({name: getattr(lib, name) for name in (
     "lbm_set_scheme", "lbm_init_equilibrium", "lbm_set_distributions",
     "lbm_set_distributions_async",
     "lbm_get_distributions", "lbm_step", "lbm_run_to_steady", "lbm_get_density",
-    "lbm_get_velocity", "lbm_get_strain_rate", "lbm_get_stress", "lbm_get_dissipation",
-    "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
+    "lbm_get_velocity", "lbm_get_velocity_async", "lbm_get_strain_rate", "lbm_get_stress",
+    "lbm_get_dissipation", "lbm_get_solid_mask", "lbm_get_force_torque", "lbm_get_force_history",
     "lbm_copy_force_torque_async", "lbm_set_solid_dynamics", "lbm_get_solid_velocity",
     "lbm_set_domain", "lbm_step_multi", "lbm_server_create", "lbm_server_submit",
     "lbm_server_poll", "lbm_server_wait", "lbm_server_velocity", "lbm_server_destroy",
@@ -307,6 +308,12 @@ class Lattice:
 
     def velocity(self, out=None):
         return self._field(lbm_get_velocity, self.d, out)
+
+    def velocity_async(self, out):
+        """Enqueue the velocity query and its copy into `out` (C-contiguous
+        float64, page-locked for an asynchronous copy) and return; `sync()`
+        waits for it."""
+        return self._field(lbm_get_velocity_async, self.d, out)
 
     def strain_rate(self):
         return self._field(lbm_get_strain_rate, 3 if self.d == 2 else 6)

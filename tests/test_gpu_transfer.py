@@ -1,8 +1,10 @@
-"""Uploads of full FP64 populations through the C ABI (lbm_set_distributions
-and lbm_set_distributions_async): the chunked copy through the staging ring
-stores exactly the rounding of f - w_i that the storage type defines, on a
-lattice large enough that every direction takes two chunks and the ring
-wraps, and the asynchronous form equals the synchronous one."""
+"""Host transfers through the C ABI.  Uploads of full FP64 populations
+(lbm_set_distributions and lbm_set_distributions_async): the chunked copy
+through the staging ring stores exactly the rounding of f - w_i that the
+storage type defines, on a lattice large enough that every direction takes
+two chunks and the ring wraps, and the asynchronous form equals the
+synchronous one.  The asynchronous velocity read-back
+(lbm_get_velocity_async) equals lbm_get_velocity."""
 import numpy as np
 import pytest
 
@@ -87,5 +89,37 @@ def test_async_upload_equals_sync_upload(precision):
     b.step(3)
     ua, ub = a.velocity(), b.velocity()
     assert np.array_equal(ua, ub)
+    a.close()
+    b.close()
+
+
+@pytest.mark.parametrize("precision", [W.FP64, W.FP32])
+def test_async_velocity_equals_velocity(precision):
+    """lbm_get_velocity_async into page-locked memory, followed at once by
+    more steps and a query of a second lattice (no wait in between), gives
+    the velocity lbm_get_velocity returns at the same state; lbm_sync waits
+    for it."""
+    import torch
+    p = big_problem(precision)
+    f0 = random_populations(p, seed=45, amplitude=0.02)
+    a, b = make_gpu(p), make_gpu(p)
+    for g in (a, b):
+        g.set_f(f0)
+        g.step(4)
+    want = a.velocity()
+    pin = [torch.empty(want.size, dtype=torch.float64, pin_memory=True).numpy()
+           for _ in range(2)]
+    a.velocity_async(pin[0])
+    b.velocity_async(pin[1])
+    a.step(3)  # ordered after the copy
+    a.sync()
+    b.sync()
+    assert np.array_equal(pin[0].reshape(want.shape), want)
+    assert np.array_equal(pin[1].reshape(want.shape), want)
+    # a plain (pageable) buffer works too
+    plain = np.empty(want.size)
+    b.velocity_async(plain)
+    b.sync()
+    assert np.array_equal(plain.reshape(want.shape), want)
     a.close()
     b.close()

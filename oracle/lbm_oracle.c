@@ -18,8 +18,9 @@
  *    printed second coefficient does not sum to one);
  *  - missing interpolation neighbours: quadratic -> linear -> Eq. 10;
  *  - refilling: equilibrium at the mean density of neighbours that were
- *    fluid before and after the move, at the local wall velocity.
- *    "parity unpinned": the paper gives no formula for this step.
+ *    fluid before and after the move, at the local wall velocity (the paper
+ *    gives no formula); pinned by the co-moving uniform flow, which it must
+ *    keep exact at any uniform density.
  *  - IBM markers: golden-angle (Fibonacci) points on the sphere of radius
  *    R - R_d (R + R_d for an enclosing wall), about `density` markers per
  *    unit area, dV = area * h / N.
@@ -799,7 +800,7 @@ static void ibm_forces(ora_sim *s) {
 
 /* Geometry at the current solid positions; nodes uncovered since the last
  * call are refilled (bounce-back schemes only, Sec. 3.2 mentions refilling,
- * formula is a reading).  "parity unpinned". */
+ * formula is a reading, pinned by the co-moving uniform flow). */
 static void update_geometry(ora_sim *s) {
   memcpy(s->inside_prev, s->inside, sizeof(int) * (size_t)s->N);
   compute_inside(s, s->inside);

@@ -17,9 +17,10 @@
  * streaming with interpolated bounce-back on cut links (Sec. 2.2) ->
  * momentum exchange (Eq. 17) -> prescribed motion of the solids.
  *
- * Parity status of every function is listed where it is defined; the one
- * part whose result is not pinned beyond consistency checks is the refilling
- * of uncovered nodes ("parity unpinned": the paper gives no formula).
+ * Parity status of every function is listed where it is defined.  The
+ * refilling of uncovered nodes is a reading (the paper gives no formula); it
+ * is pinned by the co-moving uniform flow, an exact fixed point that a
+ * refill at the wrong velocity or density, or none, breaks.
  */
 #ifndef LBM_ORACLE_H
 #define LBM_ORACLE_H

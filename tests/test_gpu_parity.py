@@ -183,6 +183,42 @@ def test_moving_sphere_ibb_refill_fp64(scheme):
     assert hist.shape[0] >= p.steps
 
 
+@pytest.mark.parametrize("precision,tol", [(W.FP64, 1e-13), (W.FP32, 2e-7)])
+@pytest.mark.parametrize("scheme", [W.BB, W.BOUZIDI_QUAD, W.YU_LIN, W.YU_QUAD])
+def test_moving_sphere_refill_keeps_comoving_flow_exact(scheme, precision, tol):
+    """The refilling pin of the oracle, on the GPU: a sphere translating at U
+    through fluid moving uniformly at U (density 1.05; the sphere's interior
+    at rest at density 1.3) is an exact fixed point, so after 60 steps, with
+    tens of nodes uncovered and refilled, the fluid is still at U and 1.05
+    (to the storage's rounding) and the momentum exchange vanishes."""
+    import oracle as O
+    U = (0.02, -0.011, 0.007)
+    p = W.Problem("comoving", W.D3Q19, 24, 18, 16, 0.8, W.MRT, precision, (0.0, 0.0, 0.0),
+                  [W.Solid(W.SPHERE, (8.2, 8.3, 7.9), 4.3, velocity=U)], scheme, 60)
+    e, w = O.lattice(W.D3Q19)
+
+    def feq(rho, u):
+        eu = e @ np.asarray(u, dtype=float)
+        f = w * (rho + 3 * eu + 4.5 * eu ** 2 - 1.5 * np.dot(u, u))
+        return np.broadcast_to(f.reshape(-1, 1, 1, 1), (19, 16, 18, 24)).copy()
+
+    g = make_gpu(p)
+    inside = g.solid_mask()
+    f = feq(1.05, U)
+    f[:, inside] = feq(1.3, (0.0, 0.0, 0.0))[:, inside]
+    g.set_f(f)
+    g.step(p.steps)
+    fluid = ~g.solid_mask()
+    assert (inside & fluid).sum() >= 10
+    u = g.velocity()
+    for c in range(3):
+        assert np.abs(u[c][fluid] - U[c]).max() < tol
+    assert np.abs(g.density()[fluid] - 1.05).max() < tol
+    F, _ = g.force_torque(0)
+    assert np.abs(F).max() < 1e4 * tol
+    g.close()
+
+
 def test_moving_sphere_ibm_fp64():
     p = W.translating_sphere(40, 24, 22, 5.2, seed=19, u=0.07, tau=0.7,
                              scheme=W.IBM, precision=W.FP64, steps=30)

@@ -2544,7 +2544,11 @@ lbm_status capture(lbm_batch *b) {
     cudaGraphDestroy(g);
     return LBM_OK;
   }
-  e = cudaGraphInstantiate(&b->exec, g, 0);
+  // the kernel nodes keep the priorities of the streams they were captured
+  // from (the auxiliary stream's boundary and IBM chains run ahead of the
+  // bulk sweeps, as when stepped directly); without this flag every node
+  // would run at the priority of the stream the graph is launched into
+  e = cudaGraphInstantiate(&b->exec, g, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) return bfail(b, LBM_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
   return LBM_OK;

@@ -63,6 +63,20 @@ __device__ __forceinline__ float2 qdot2(const float2 (&v)[3]) {
   return r;
 }
 
+// Sum over the pair leaders i of q_a,i 3 w_i e_i,b: the q moments of the
+// pairs' terms -2 A_i + AF_i (A_i = 3 w_i e_i.u, AF_i = 3 w_i e_i.F) are
+// sum_b K_ab (F_b - 2 u_b).
+template <int LAT> __host__ __device__ constexpr double qk(int a, int b) {
+  using L = Lat<LAT>;
+  double s = 0;
+  for (int i = 1; i < L::Q; i++)
+    if (L::opp(i) > i) {
+      const int e = b == 0 ? L::ex(i) : (b == 1 ? L::ey(i) : L::ez(i));
+      s += qrow<LAT>(a, i) * 3.0 * L::w(i) * e;
+    }
+  return s;
+}
+
 // Collide two nodes at once (lane x and lane y of every float2): BGK, or MRT
 // whose only non-BGK rates are those of the q moments.  Same algebra as
 // `collide`: feq and Fbar split into parts even and odd in e over each
@@ -72,7 +86,12 @@ __device__ __forceinline__ float2 qdot2(const float2 (&v)[3]) {
 //   f_i* = (1 - omega) f_i + omega (S + A) + (1 - omega/2)(SF + AF),
 //   f_j* = (1 - omega) f_j + omega (S - A) + (1 - omega/2)(SF - AF),
 // and the q-moment correction (omega - s_q) m_q M_q,i / |M_q|^2 with m_q the
-// q moments of Delta + Fbar/2, which only involve f_i - f_j - 2A + AF.
+// q moments of Delta + Fbar/2, i.e. of f_i - f_j - 2A + AF over the pairs.
+// Grouped for few operations:
+//   P = omega S + cforce SF = w B + A g,  B = omega (drho - 1.5 u^2) - 3 cforce u.F,
+//       g = 1.5 omega e.u + 3 cforce e.F,
+//   M = omega A + cforce AF = omega A + w (3 cforce e.F),
+//   m_q,a = sum_i q_a,i (f_i - f_j) + sum_b K_ab (F_b - 2 u_b)   (qk above).
 // With SL > 0 the populations and the force come in units of 2^-SL (FP16
 // storage's scaled deviations) and the results go out in them: everything
 // but the terms quadratic in u and F is linear, and those take their
@@ -87,8 +106,10 @@ __device__ __forceinline__ void collide_x2(float2 (&f)[Lat<LAT>::Q], float2 Fx, 
   static_assert(CM != CM_MRT, "general MRT rates run in the one-node kernel");
   constexpr float wa = (float)L::w(1), wb = (float)L::w(Q - 1);
   constexpr float kInv = 1.0f / (float)(1 << SL);  // exact
+  constexpr float kS = (float)(1 << SL);
   float2 drho = f[0];
   float2 jx = bc2(0.f), jy = bc2(0.f), jz = bc2(0.f);
+  float2 mq[3] = {bc2(0.f), bc2(0.f), bc2(0.f)};  // sum_i q_a,i (f_i - f_j)
   static_for<Q>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     if constexpr (i > 0 && L::opp(i) > i) {
@@ -102,6 +123,15 @@ __device__ __forceinline__ void collide_x2(float2 (&f)[Lat<LAT>::Q], float2 Fx, 
       if constexpr (L::ey(i) == -1) jy = sub2(jy, d);
       if constexpr (L::ez(i) == 1) jz = add2(jz, d);
       if constexpr (L::ez(i) == -1) jz = sub2(jz, d);
+      if constexpr (CM == CM_MRT_Q) {
+        static_for<L::D>([&](auto ac) {
+          constexpr int ax = decltype(ac)::value;
+          constexpr int q = qrow<LAT>(ax, i);
+          if constexpr (q == 1) mq[ax] = add2(mq[ax], d);
+          else if constexpr (q == -1) mq[ax] = sub2(mq[ax], d);
+          else if constexpr (q != 0) mq[ax] = fma2(bc2((float)q), d, mq[ax]);
+        });
+      }
     }
   });
   const float2 half = bc2(0.5f);
@@ -109,47 +139,46 @@ __device__ __forceinline__ void collide_x2(float2 (&f)[Lat<LAT>::Q], float2 Fx, 
   const float2 uu = fma2(uz, uz, fma2(uy, uy, mul2(ux, ux)));
   const float2 uF = fma2(uz, Fz, fma2(uy, Fy, mul2(ux, Fx)));
   const float2 base = fma2(bc2(-1.5f * kInv), uu, drho);
-  const float2 om = bc2(c.omega), omc = bc2(c.omc), cf = bc2(c.cforce);
-  // w base and -3 w u.F for the two weight classes of the moving directions
-  const float2 wbase_a = mul2(bc2(wa), base), wbase_b = mul2(bc2(wb), base);
-  // (-3 w rounded to float) times 2^-SL
-  const float2 wuF_a = mul2(bc2(-3.f * wa * kInv), uF), wuF_b = mul2(bc2(-3.f * wb * kInv), uF);
+  const float2 om = bc2(c.omega), omc = bc2(c.omc);
+  // the constants of the terms quadratic in u and F carry 2^-SL: 1.5 omega,
+  // 3 cforce (each the power-of-two multiple of its unscaled rounding)
+  const float om15 = c.omega * (1.5f * kInv), cf3 = c.cforce * (3.f * kInv);
+  const float2 B = fma2(bc2(-cf3), uF, mul2(om, base));
   {
     constexpr float w0 = (float)L::w(0);
-    const float2 S = mul2(bc2(w0), base), SF = mul2(bc2(-3.f * w0 * kInv), uF);
-    f[0] = fma2(omc, f[0], fma2(om, S, mul2(cf, SF)));
+    f[0] = fma2(omc, f[0], mul2(bc2(w0), B));
   }
-  float2 mq[3] = {bc2(0.f), bc2(0.f), bc2(0.f)};
+  const float2 Ba = mul2(bc2(wa), B), Bb = mul2(bc2(wb), B);
   static_for<Q>([&](auto ic) {
     constexpr int i = decltype(ic)::value;
     if constexpr (i > 0 && L::opp(i) > i) {
       constexpr int j = L::opp(i);
       constexpr bool ca = L::w(i) == L::w(1);
-      constexpr float w3 = (float)(3.0 * L::w(i));
+      constexpr float w = (float)L::w(i), w3 = (float)(3.0 * L::w(i));
       const float2 eu = edot2<LAT, i>(ux, uy, uz);
       const float2 eF = edot2<LAT, i>(Fx, Fy, Fz);
       const float2 A = mul2(bc2(w3), eu);
-      const float2 S = fma2(A, mul2(bc2(1.5f * kInv), eu), ca ? wbase_a : wbase_b);
-      const float2 SF = fma2(A, mul2(bc2(3.f * kInv), eF), ca ? wuF_a : wuF_b);
-      const float2 AF = mul2(bc2(w3), eF);
-      const float2 P = fma2(om, S, mul2(cf, SF));
-      const float2 M = fma2(om, A, mul2(cf, AF));
-      if constexpr (CM == CM_MRT_Q) {
-        // (f_i - f_j) recomputed rather than kept from the sums above
-        const float2 dd = add2(fma2(bc2(-2.f), A, sub2(f[i], f[j])), AF);
-        static_for<L::D>([&](auto ac) {
-          constexpr int ax = decltype(ac)::value;
-          constexpr int q = qrow<LAT>(ax, i);
-          if constexpr (q != 0) mq[ax] = fma2(bc2((float)q), dd, mq[ax]);
-        });
-      }
+      const float2 t = mul2(bc2(cf3), eF);     // 3 cforce e.F (times 2^-SL)
+      const float2 g = fma2(bc2(om15), eu, t);  // 1.5 omega e.u + 3 cforce e.F
+      const float2 P = fma2(A, g, ca ? Ba : Bb);
+      const float2 M = fma2(om, A, mul2(bc2(w * kS), t));
       f[i] = fma2(omc, f[i], add2(P, M));
       f[j] = fma2(omc, f[j], sub2(P, M));
     }
   });
   if constexpr (CM == CM_MRT_Q) {
-    // all q rows share one rate; the rows are odd in e, so the opposite
-    // direction of a pair gets the negative correction
+    // the pairs' -2 A + AF terms of the q moments, then the correction: all q
+    // rows share one rate; the rows are odd in e, so the opposite direction
+    // of a pair gets the negative correction
+    const float2 fu[3] = {fma2(bc2(-2.f), ux, Fx), fma2(bc2(-2.f), uy, Fy), fma2(bc2(-2.f), uz, Fz)};
+    static_for<L::D>([&](auto ac) {
+      constexpr int ax = decltype(ac)::value;
+      static_for<L::D>([&](auto bc) {
+        constexpr int b = decltype(bc)::value;
+        constexpr float K = (float)qk<LAT>(ax, b);
+        if constexpr (K != 0.f) mq[ax] = fma2(bc2(K), fu[b], mq[ax]);
+      });
+    });
     const float2 k = bc2(c.ds[4] * (float)(1.0 / mnorm<LAT>(4)));
     const float2 aq[3] = {mul2(k, mq[0]), mul2(k, mq[1]), mul2(k, mq[2])};
     static_for<Q>([&](auto ic) {

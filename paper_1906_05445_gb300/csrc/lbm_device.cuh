@@ -212,6 +212,20 @@ template <int LAT> __host__ __device__ constexpr int qrow(int a, int i) {
   return mrow<LAT>(4 + 2 * a, i);
 }
 
+// Sum over the pair leaders i of q_a,i 3 w_i e_i,b: the q moments of the
+// pairs' terms -2 A_i + AF_i (A_i = 3 w_i e_i.u, AF_i = 3 w_i e_i.F) are
+// sum_b K_ab (F_b - 2 u_b).
+template <int LAT> __host__ __device__ constexpr double qk(int a, int b) {
+  using L = Lat<LAT>;
+  double s = 0;
+  for (int i = 1; i < L::Q; i++)
+    if (L::opp(i) > i) {
+      const int e = b == 0 ? L::ex(i) : (b == 1 ? L::ey(i) : L::ez(i));
+      s += qrow<LAT>(a, i) * 3.0 * L::w(i) * e;
+    }
+  return s;
+}
+
 template <int LAT, int CM, typename T>
 __device__ __forceinline__ void collide(T (&f)[Lat<LAT>::Q], T Fx, T Fy, T Fz,
                                         const Coll<T> &c) {
@@ -236,28 +250,30 @@ __device__ __forceinline__ void collide(T (&f)[Lat<LAT>::Q], T Fx, T Fy, T Fz,
   const T om = c.omega, omc = c.omc, cf = c.cforce;
   if constexpr (CM != CM_MRT) {
     // BGK, or MRT whose only non-BGK moments are the q moments: update in
-    // place pair by pair; the odd q moments of Delta + Fbar/2 only need the
-    // differences f_i - f_ib - 2A + AF of each pair
+    // place pair by pair, grouped for few operations (as the packed pair
+    // collision): omega S + cforce SF = w B + A g with B = omega base -
+    // 3 cforce u.F and g = 1.5 omega e.u + 3 cforce e.F; omega A + cforce AF
+    // = omega A + w (3 cforce e.F); the q moments of Delta + Fbar/2 are
+    // sum_i q_a,i (f_i - f_ib) + K (F - 2u) (qk: the pairs' -2A + AF terms)
     T mq[3] = {0, 0, 0};
-    {
-      constexpr T w0 = (T)L::w(0);
-      const T S = w0 * base, SF = (T)(-3.0 * L::w(0)) * uF;
-      f[0] = omc * f[0] + om * S + cf * SF;
-    }
+    const T om15 = om * (T)1.5, cf3 = cf * (T)3;
+    const T B = om * base - cf3 * uF;
+    f[0] = omc * f[0] + (T)L::w(0) * B;
+    const T Ba = (T)L::w(1) * B, Bb = (T)L::w(Q - 1) * B;
     static_for<Q>([&](auto ic) {
       constexpr int i = decltype(ic)::value;
       if constexpr (i > 0 && L::opp(i) > i) {
         constexpr int j = L::opp(i);
         constexpr T w = (T)L::w(i);
+        constexpr bool ca = L::w(i) == L::w(1);
         const T eu = edot<LAT, i, T>(ux, uy, uz);
         const T eF = edot<LAT, i, T>(Fx, Fy, Fz);
-        const T S = w * (base + (T)4.5 * eu * eu);
         const T A = (T)(3.0 * L::w(i)) * eu;
-        const T SF = w * ((T)9 * eu * eF - (T)3 * uF);
-        const T AF = (T)(3.0 * L::w(i)) * eF;
-        const T P = om * S + cf * SF, M = om * A + cf * AF;
+        const T t = cf3 * eF;
+        const T P = A * (om15 * eu + t) + (ca ? Ba : Bb);
+        const T M = om * A + w * t;
         if constexpr (CM == CM_MRT_Q) {
-          const T d = f[i] - f[j] - (T)2 * A + AF;
+          const T d = f[i] - f[j];
           static_for<L::D>([&](auto ac) {
             constexpr int ax = decltype(ac)::value;
             constexpr int q = qrow<LAT>(ax, i);
@@ -269,6 +285,15 @@ __device__ __forceinline__ void collide(T (&f)[Lat<LAT>::Q], T Fx, T Fy, T Fz,
       }
     });
     if constexpr (CM == CM_MRT_Q) {
+      const T fu[3] = {Fx - (T)2 * ux, Fy - (T)2 * uy, Fz - (T)2 * uz};
+      static_for<L::D>([&](auto ac) {
+        constexpr int ax = decltype(ac)::value;
+        static_for<L::D>([&](auto bc) {
+          constexpr int b = decltype(bc)::value;
+          constexpr T K = (T)qk<LAT>(ax, b);
+          if constexpr (K != (T)0) mq[ax] += K * fu[b];
+        });
+      });
       // all q rows share one rate: a_a = (omega - s_q) m_q,a / |M_q|^2
       const T k = c.ds[4] * (T)(1.0 / mnorm<LAT>(4));
       T aq[3] = {k * mq[0], k * mq[1], k * mq[2]};

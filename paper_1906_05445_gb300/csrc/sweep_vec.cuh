@@ -63,20 +63,6 @@ __device__ __forceinline__ float2 qdot2(const float2 (&v)[3]) {
   return r;
 }
 
-// Sum over the pair leaders i of q_a,i 3 w_i e_i,b: the q moments of the
-// pairs' terms -2 A_i + AF_i (A_i = 3 w_i e_i.u, AF_i = 3 w_i e_i.F) are
-// sum_b K_ab (F_b - 2 u_b).
-template <int LAT> __host__ __device__ constexpr double qk(int a, int b) {
-  using L = Lat<LAT>;
-  double s = 0;
-  for (int i = 1; i < L::Q; i++)
-    if (L::opp(i) > i) {
-      const int e = b == 0 ? L::ex(i) : (b == 1 ? L::ey(i) : L::ez(i));
-      s += qrow<LAT>(a, i) * 3.0 * L::w(i) * e;
-    }
-  return s;
-}
-
 // Collide two nodes at once (lane x and lane y of every float2): BGK, or MRT
 // whose only non-BGK rates are those of the q moments.  Same algebra as
 // `collide`: feq and Fbar split into parts even and odd in e over each
@@ -475,7 +461,7 @@ __device__ __forceinline__ void bulk_vec_update(const KArgs &a, unsigned t, unsi
 // ring in shared memory.)  The 8-byte 16-bit kernels are held to 128
 // registers, 4 blocks of 128 per SM (130 unbounded: 3 blocks).
 template <int LAT, int CM, typename S, int W, bool PACKED>
-__global__ void __launch_bounds__(256, (sizeof(S) == 2 && W == 2) ? 2 : 0)
+__global__ void __launch_bounds__(256, (sizeof(S) == 2 && W == 2) ? 2 : ((sizeof(S) == 4 && W == 2 && !PACKED) ? 3 : 0))
     k_bulk_vec(const KArgs a) {
   constexpr int V = W * VecS<S>::per_word;
   bulk_vec_update<LAT, CM, S, W, PACKED>(a, blockIdx.x * blockDim.x + threadIdx.x,

@@ -459,9 +459,11 @@ __device__ __forceinline__ void bulk_vec_update(const KArgs &a, unsigned t, unsi
 // slower: it holds more registers and leaves the boundary kernels less room;
 // so did one that kept the next vector's loads in flight through a cp.async
 // ring in shared memory.)  The 8-byte 16-bit kernels are held to 128
-// registers, 4 blocks of 128 per SM (130 unbounded: 3 blocks).
+// registers, 4 blocks of 128 per SM (130 unbounded: 3 blocks); the FP32
+// node-by-node kernel to 64, 8 blocks of 128 per SM (88 unbounded: 5 blocks),
+// whose extra warps hide more of the boundary kernel's share of the SMs.
 template <int LAT, int CM, typename S, int W, bool PACKED>
-__global__ void __launch_bounds__(256, (sizeof(S) == 2 && W == 2) ? 2 : ((sizeof(S) == 4 && W == 2 && !PACKED) ? 3 : 0))
+__global__ void __launch_bounds__(256, (sizeof(S) == 2 && W == 2) ? 2 : ((sizeof(S) == 4 && W == 2 && !PACKED) ? 4 : 0))
     k_bulk_vec(const KArgs a) {
   constexpr int V = W * VecS<S>::per_word;
   bulk_vec_update<LAT, CM, S, W, PACKED>(a, blockIdx.x * blockDim.x + threadIdx.x,
